@@ -1,0 +1,346 @@
+"""Seeded synthetic MDP generators (inputs only; no MDP solution arithmetic).
+
+Every generator returns an ``MDPData``: the row-stacked transition matrix of
+Eq. 5 in CSR form (row index s*A + a holds P(s, ., a)) and the stage costs g
+as an S x A row-major array (g[s*A + a] = g(s, a)), plus the discount factor.
+
+Random draws come from Philox4x32-10 keyed by (seed, stream tag) with the
+counter set to (global row index, draw index), so any row can be regenerated
+alone (see ``regenerate_rows``).  The workloads mirror the shapes used in the
+paper's experiments (Sec. IV): random sparse MDPs with uniform columns
+(Sec. IV-A), a banded birth-death chain standing in for the SIS epidemic model
+(Sec. IV-B), a bilinear-interpolated pendulum grid (Sec. IV-C) and a
+deterministic maze (Sec. IV-D).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from .philox import stream
+
+# stream tags: one Philox key word per purpose so that draws never overlap
+TAG_COLS = 0x636F6C73  # "cols"
+TAG_VALS = 0x76616C73  # "vals"
+TAG_COST = 0x636F7374  # "cost"
+TAG_NOISE = 0x6E6F6973  # "nois"
+
+
+@dataclasses.dataclass
+class MDPData:
+    S: int
+    A: int
+    row_ptr: np.ndarray  # int64 [S*A + 1]
+    col: np.ndarray  # int32 [nnz]
+    val: np.ndarray  # float64 [nnz]
+    g: np.ndarray  # float64 [S*A]
+    gamma: float
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def row(self, s: int, a: int):
+        r = s * self.A + a
+        lo, hi = int(self.row_ptr[r]), int(self.row_ptr[r + 1])
+        return self.col[lo:hi], self.val[lo:hi]
+
+
+# --------------------------------------------------------------------------
+# value transforms
+# --------------------------------------------------------------------------
+
+def quantize_rows(w: np.ndarray, bits: int) -> np.ndarray:
+    """Round each row of nonnegative weights to multiples of 2**-bits summing to 1.
+
+    Largest-remainder rounding: each row is scaled to 2**bits units, floored,
+    and the missing units go to the entries with the largest remainders (ties
+    to the lower position).  The result is exactly representable in binary16
+    for bits <= 11 and in bfloat16 for bits <= 8, and every row sums to
+    exactly one in binary64.
+    """
+    unit = float(1 << bits)
+    w = np.asarray(w, dtype=np.float64)
+    x = w / w.sum(axis=1, keepdims=True) * unit
+    q = np.floor(x)
+    missing = (unit - q.sum(axis=1)).astype(np.int64)
+    rem = x - q
+    # stable order: larger remainder first, then lower position first
+    order = np.argsort(-rem, axis=1, kind="stable")
+    ranks = np.empty_like(order)
+    np.put_along_axis(ranks, order, np.arange(w.shape[1])[None, :].repeat(w.shape[0], 0), axis=1)
+    q += (ranks < missing[:, None]).astype(np.float64)
+    return q / unit
+
+
+def _dirichlet_weights(seed: int, rows: np.ndarray, k: int, conc: float) -> np.ndarray:
+    """Unnormalised Dirichlet(conc) weights for k entries of each given row.
+
+    conc == 1: Gamma(1) = -log(U) (exponential).
+    conc == 0.5: Gamma(1/2) = Z**2 / 2 with Z standard normal (Box-Muller).
+    """
+    j = np.arange(k, dtype=np.uint64)[None, :]
+    r = rows.astype(np.uint64)[:, None]
+    if conc == 1.0:
+        u = stream(seed, TAG_VALS, r, j)
+        return -np.log1p(-u)  # U in [0,1) -> 1-U in (0,1]
+    if conc == 0.5:
+        u1 = stream(seed, TAG_VALS, r, j, lane=0)
+        u2 = stream(seed, TAG_VALS, r, j, lane=1)
+        z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * math.pi * u2)
+        w = 0.5 * z * z
+        # a row of all-zero weights cannot be normalised: give it uniform mass
+        dead = w.sum(axis=1) <= 0.0
+        if np.any(dead):
+            w[dead] = 1.0
+        return w
+    raise ValueError("supported Dirichlet concentrations: 1.0, 0.5")
+
+
+def _distinct_columns(seed: int, rows: np.ndarray, k: int, S: int) -> np.ndarray:
+    """k distinct uniform columns in [0, S) per row, sorted ascending (Floyd's algorithm)."""
+    if k > S:
+        raise ValueError("k > S")
+    n = rows.shape[0]
+    chosen = np.empty((n, k), dtype=np.int64)
+    r = rows.astype(np.uint64)
+    for i in range(k):
+        jmax = S - k + i  # draw t uniformly in [0, jmax]
+        u = stream(seed, TAG_COLS, r, np.uint64(i))
+        t = np.minimum(np.floor(u * (jmax + 1)).astype(np.int64), jmax)
+        if i:
+            dup = (chosen[:, :i] == t[:, None]).any(axis=1)
+            t = np.where(dup, jmax, t)
+        chosen[:, i] = t
+    chosen.sort(axis=1)
+    return chosen
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def random_sparse(S: int, A: int, k: int, gamma: float, seed: int, conc: float = 1.0,
+                  quant_bits: int | None = None, chunk_rows: int = 1 << 20) -> MDPData:
+    """Random sparse MDP in the style of Sec. IV-A.
+
+    Each (s, a) row has k distinct columns drawn uniformly, probabilities
+    Dirichlet(conc) (optionally quantised to 2**-quant_bits, explicit zeros
+    kept so every row has exactly k entries), and costs g(s, a) ~ U[0, 1).
+    """
+    R = S * A
+    col = np.empty(R * k, dtype=np.int32)
+    val = np.empty(R * k, dtype=np.float64)
+    for r0 in range(0, R, chunk_rows):
+        r1 = min(R, r0 + chunk_rows)
+        rows = np.arange(r0, r1, dtype=np.int64)
+        c = _distinct_columns(seed, rows, k, S)
+        w = _dirichlet_weights(seed, rows, k, conc)
+        if quant_bits is None:
+            p = w / w.sum(axis=1, keepdims=True)
+        else:
+            p = quantize_rows(w, quant_bits)
+        col[r0 * k:r1 * k] = c.ravel()
+        val[r0 * k:r1 * k] = p.ravel()
+    g = stream(seed, TAG_COST, np.arange(R, dtype=np.uint64), np.uint64(0))
+    row_ptr = np.arange(R + 1, dtype=np.int64) * k
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"random_sparse(S={S},A={A},k={k})")
+
+
+def banded_birth_death(S: int = 1_000_000, A: int = 20, half_width: int = 16, gamma: float = 0.999,
+                       quant_bits: int | None = None, chunk_states: int = 1 << 16) -> MDPData:
+    """Banded birth-death chain standing in for the SIS model of Sec. IV-B.
+
+    State s is the infected count.  Row (s, a) is a band of 2h+1 contiguous
+    columns centred at c = clamp(s + drift(a), h, S-1-h) with drift(a) =
+    A//2 - a (higher intervention levels push the count down).  The band holds
+    the Binomial(2h, 1/2) pmf C(2h, j) / 2**(2h), exact in binary64 (or, with
+    quant_bits, rounded to 2**-quant_bits by largest remainder).  Cost
+    g(s, a) = s/S + 0.05 a.
+    """
+    h = half_width
+    w = 2 * h + 1
+    if S < w:
+        raise ValueError("S must be at least the band width")
+    pmf = np.array([math.comb(2 * h, j) for j in range(w)], dtype=np.float64) / float(2 ** (2 * h))
+    if quant_bits is not None:
+        pmf = quantize_rows(pmf[None, :], quant_bits)[0]
+    R = S * A
+    col = np.empty(R * w, dtype=np.int32)
+    val = np.empty(R * w, dtype=np.float64)
+    offs = np.arange(-h, h + 1, dtype=np.int64)
+    drift = (A // 2 - np.arange(A, dtype=np.int64))
+    for s0 in range(0, S, chunk_states):
+        s1 = min(S, s0 + chunk_states)
+        s = np.arange(s0, s1, dtype=np.int64)
+        c = np.clip(s[:, None] + drift[None, :], h, S - 1 - h)  # [ns, A]
+        cols = c[:, :, None] + offs[None, None, :]
+        lo, hi = s0 * A * w, s1 * A * w
+        col[lo:hi] = cols.ravel()
+        val[lo:hi] = np.broadcast_to(pmf, cols.shape).ravel()
+    s_all = np.repeat(np.arange(S, dtype=np.float64), A)
+    a_all = np.tile(np.arange(A, dtype=np.float64), S)
+    g = s_all / S + 0.05 * a_all
+    row_ptr = np.arange(R + 1, dtype=np.int64) * w
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"banded_birth_death(S={S},A={A},k={w})")
+
+
+def pendulum_grid(n_theta: int = 1000, n_omega: int = 1000, A: int = 9, gamma: float = 0.9999,
+                  seed: int = 3, Ts: float = 0.01, quant_bits: int | None = None,
+                  chunk_states: int = 1 << 16) -> MDPData:
+    """Inverted-pendulum grid MDP after Sec. IV-C (Eq. 8-10).
+
+    State s = i_theta * n_omega + i_omega on theta in [0, 2 pi) (periodic, step
+    2 pi / n_theta) and omega on linspace(-10, 10, n_omega); torques F on
+    linspace(-3, 3, A).  One forward-Euler step (theta' = theta + Ts omega,
+    omega' = omega + Ts (F - 9.80665 sin theta)) plus a Gaussian offset with
+    standard deviation half a grid step per dimension (drawn once per (s, a))
+    gives a continuous successor that is spread over its 4 surrounding grid
+    nodes by bilinear weights (omega clamped inside the grid so the 4 nodes are
+    distinct).  Cost g = 2 [(theta - pi)^2 + omega^2] + F^2.
+    """
+    S = n_theta * n_omega
+    R = S * A
+    dth = 2.0 * math.pi / n_theta
+    om = np.linspace(-10.0, 10.0, n_omega)
+    dom = om[1] - om[0]
+    forces = np.linspace(-3.0, 3.0, A)
+    col = np.empty(R * 4, dtype=np.int32)
+    val = np.empty(R * 4, dtype=np.float64)
+    g = np.empty(R, dtype=np.float64)
+    for s0 in range(0, S, chunk_states):
+        s1 = min(S, s0 + chunk_states)
+        s = np.arange(s0, s1, dtype=np.int64)
+        ith, iom = s // n_omega, s % n_omega
+        th = ith * dth
+        w_ = om[iom]
+        rows = (s[:, None] * A + np.arange(A)[None, :]).astype(np.uint64)  # [ns, A]
+        F = forces[None, :]
+        thn = th[:, None] + Ts * w_[:, None]
+        omn = w_[:, None] + Ts * (F - 9.80665 * np.sin(th)[:, None])
+        # Gaussian offsets via Box-Muller from one Philox block per row
+        u1 = stream(seed, TAG_NOISE, rows, np.uint64(0), lane=0)
+        u2 = stream(seed, TAG_NOISE, rows, np.uint64(0), lane=1)
+        rad = np.sqrt(-2.0 * np.log1p(-u1))
+        z1 = rad * np.cos(2.0 * math.pi * u2)
+        z2 = rad * np.sin(2.0 * math.pi * u2)
+        thn = thn + 0.5 * dth * z1
+        omn = omn + 0.5 * dom * z2
+        # theta: periodic cell index and fraction
+        xt = np.mod(thn, 2.0 * math.pi) / dth
+        i0 = np.floor(xt).astype(np.int64)
+        ft = xt - i0
+        i0 = np.mod(i0, n_theta)
+        i1 = np.mod(i0 + 1, n_theta)
+        # omega: clamp inside the grid
+        xo = np.clip((omn - om[0]) / dom, 0.0, n_omega - 1.0)
+        j0 = np.minimum(np.floor(xo).astype(np.int64), n_omega - 2)
+        fo = xo - j0
+        j1 = j0 + 1
+        cols = np.stack([i0 * n_omega + j0, i0 * n_omega + j1, i1 * n_omega + j0, i1 * n_omega + j1], axis=-1)
+        wts = np.stack([(1 - ft) * (1 - fo), (1 - ft) * fo, ft * (1 - fo), ft * fo], axis=-1)
+        order = np.argsort(cols, axis=-1, kind="stable")
+        cols = np.take_along_axis(cols, order, axis=-1)
+        wts = np.take_along_axis(wts, order, axis=-1)
+        wts = wts.reshape(-1, 4)
+        if quant_bits is not None:
+            wts = quantize_rows(wts, quant_bits)
+        else:
+            wts = wts / wts.sum(axis=1, keepdims=True)
+        lo, hi = s0 * A * 4, s1 * A * 4
+        col[lo:hi] = cols.ravel()
+        val[lo:hi] = wts.ravel()
+        gg = 2.0 * ((th[:, None] - math.pi) ** 2 + w_[:, None] ** 2) + F ** 2
+        g[s0 * A:s1 * A] = gg.ravel()
+    row_ptr = np.arange(R + 1, dtype=np.int64) * 4
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"pendulum_grid({n_theta}x{n_omega},A={A})")
+
+
+def maze(H: int, W: int, wall_frac: float = 0.2, seed: int = 7, gamma: float = 0.99,
+         goal_cost: float = -100.0, bump_cost: float = 1.0) -> tuple[MDPData, np.ndarray, int]:
+    """Deterministic grid maze after Sec. IV-D, with walls removed from the state space.
+
+    Cells are drawn as walls with probability wall_frac (the goal, the
+    bottom-right cell, is always free).  States are the free cells in
+    row-major order.  Actions 0..4 = stay, north, east, south, west.  A move
+    into a wall or off the grid leaves the agent in place at cost bump_cost;
+    other moves cost 0, and every action taken in the goal keeps the agent
+    there at cost goal_cost.  Returns (mdp, free-cell grid index of each
+    state, goal state index).
+    """
+    u = stream(seed, TAG_COLS, np.arange(H * W, dtype=np.uint64), np.uint64(0)).reshape(H, W)
+    wall = u < wall_frac
+    wall[H - 1, W - 1] = False
+    free_idx = np.flatnonzero(~wall.ravel())
+    state_of = -np.ones(H * W, dtype=np.int64)
+    state_of[free_idx] = np.arange(free_idx.size)
+    S, A = free_idx.size, 5
+    goal = int(state_of[(H - 1) * W + (W - 1)])
+    moves = [(0, 0), (-1, 0), (0, 1), (1, 0), (0, -1)]
+    col = np.empty(S * A, dtype=np.int32)
+    g = np.zeros(S * A, dtype=np.float64)
+    ys, xs = free_idx // W, free_idx % W
+    for a, (dy, dx) in enumerate(moves):
+        ny, nx = ys + dy, xs + dx
+        inside = (ny >= 0) & (ny < H) & (nx >= 0) & (nx < W)
+        tgt = np.where(inside, ny * W + nx, 0)
+        ok = inside & ~wall.ravel()[tgt]
+        nxt = np.where(ok, state_of[tgt], np.arange(S))
+        cost = np.where(ok | (a == 0), 0.0, bump_cost)
+        nxt[goal] = goal
+        cost[goal] = goal_cost
+        col[np.arange(S) * A + a] = nxt
+        g[np.arange(S) * A + a] = cost
+    val = np.ones(S * A, dtype=np.float64)
+    row_ptr = np.arange(S * A + 1, dtype=np.int64)
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"maze({H}x{W})"), free_idx, goal
+
+
+def random_value_vector(S: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """A seeded test vector V ~ scale * U[-1, 1) of length S."""
+    u = stream(seed, TAG_NOISE ^ 0x5A5A, np.arange(S, dtype=np.uint64), np.uint64(1))
+    return scale * (2.0 * u - 1.0)
+
+
+def regenerate_rows(kind: str, params: dict, rows: np.ndarray):
+    """Regenerate selected CSR rows of a workload without building the whole matrix.
+
+    Returns (cols [n, k] int64, vals [n, k] float64, g [n]) for the given
+    global row indices.  Supported kinds: "random_sparse", "banded_birth_death".
+    """
+    rows = np.asarray(rows, dtype=np.int64)
+    if kind == "random_sparse":
+        S, A, k, seed = params["S"], params["A"], params["k"], params["seed"]
+        conc, qb = params.get("conc", 1.0), params.get("quant_bits")
+        c = _distinct_columns(seed, rows, k, S)
+        w = _dirichlet_weights(seed, rows, k, conc)
+        p = w / w.sum(axis=1, keepdims=True) if qb is None else quantize_rows(w, qb)
+        g = stream(seed, TAG_COST, rows.astype(np.uint64), np.uint64(0))
+        return c, p, g
+    if kind == "banded_birth_death":
+        S, A = params["S"], params["A"]
+        h = params.get("half_width", 16)
+        qb = params.get("quant_bits")
+        w = 2 * h + 1
+        pmf = np.array([math.comb(2 * h, j) for j in range(w)], dtype=np.float64) / float(2 ** (2 * h))
+        if qb is not None:
+            pmf = quantize_rows(pmf[None, :], qb)[0]
+        s, a = rows // A, rows % A
+        c = np.clip(s + (A // 2 - a), h, S - 1 - h)
+        cols = c[:, None] + np.arange(-h, h + 1)[None, :]
+        return cols, np.broadcast_to(pmf, cols.shape).copy(), s / S + 0.05 * a
+    raise ValueError(kind)
+
+
+# named workloads (the shapes of the five benchmark configurations)
+def workload(name: str) -> MDPData:
+    if name == "random_s1000_a4_k8":
+        return random_sparse(1000, 4, 8, 0.9, seed=1, conc=1.0)
+    if name == "banded_s1e6_a20_k33":
+        return banded_birth_death(1_000_000, 20, 16, 0.999)
+    if name == "pendulum_1000x1000_a9":
+        return pendulum_grid(1000, 1000, 9, 0.9999, seed=3)
+    raise ValueError(name)

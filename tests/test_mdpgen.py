@@ -1,0 +1,83 @@
+"""Input generators: Philox known answers, row layout (Eq. 5), stochasticity, quantisation."""
+import math
+
+import numpy as np
+
+from mdpgen import (banded_birth_death, pendulum_grid, philox4x32, quantize_rows, random_sparse,
+                    regenerate_rows)
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors published with the Random123 library."""
+    cases = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, expect in cases:
+        assert tuple(int(x) for x in philox4x32(ctr, key)) == expect
+
+
+def _row_sums(m):
+    return np.add.reduceat(m.val, m.row_ptr[:-1])
+
+
+def test_random_sparse_shape_and_stochastic():
+    m = random_sparse(500, 4, 8, 0.9, seed=1)
+    assert m.row_ptr.shape == (2001,) and m.nnz == 16000
+    assert np.all(np.diff(m.row_ptr) == 8)
+    assert m.col.min() >= 0 and m.col.max() < 500
+    cols = m.col.reshape(-1, 8)
+    assert np.all(np.diff(cols, axis=1) > 0)  # distinct, ascending
+    assert np.all(m.val >= 0)
+    assert np.max(np.abs(_row_sums(m) - 1)) < 1e-15
+    assert np.all((m.g >= 0) & (m.g < 1))
+
+
+def test_quantised_rows_sum_exactly_to_one():
+    m = random_sparse(300, 3, 32, 0.99, seed=4, conc=0.5, quant_bits=11)
+    assert np.all(_row_sums(m) == 1.0)
+    assert np.all(m.val * 2048 == np.round(m.val * 2048))
+    q = quantize_rows(np.array([[1.0, 1.0, 1.0]]), 8)
+    assert q.sum() == 1.0 and sorted((q[0] * 256).tolist()) == [85, 85, 86]
+
+
+def test_banded_layout_row_is_state_times_A_plus_action():
+    """Row s*A + a holds P(s, ., a): the band sits at s + drift(a) (Eq. 5 layout)."""
+    S, A, h = 200, 6, 4
+    m = banded_birth_death(S, A, h, 0.999)
+    for s in (0, 57, 199):
+        for a in range(A):
+            cols, vals = m.row(s, a)
+            c = min(max(s + A // 2 - a, h), S - 1 - h)
+            assert cols.tolist() == list(range(c - h, c + h + 1))
+            assert vals.sum() == 1.0
+            assert math.isclose(vals[h], math.comb(2 * h, h) / 2 ** (2 * h))
+            assert m.g[s * A + a] == s / S + 0.05 * a
+
+
+def test_pendulum_rows():
+    m = pendulum_grid(30, 20, 5, 0.9999, seed=3)
+    assert m.S == 600 and m.nnz == 600 * 5 * 4
+    assert np.max(np.abs(_row_sums(m) - 1)) < 1e-14
+    cols = m.col.reshape(-1, 4)
+    assert np.all(np.diff(cols, axis=1) > 0)
+
+
+def test_regenerate_rows_matches_full_build():
+    m = random_sparse(700, 5, 6, 0.9, seed=9)
+    rows = np.array([0, 13, 3499])
+    c, p, g = regenerate_rows("random_sparse", dict(S=700, A=5, k=6, seed=9), rows)
+    for i, r in enumerate(rows):
+        lo, hi = m.row_ptr[r], m.row_ptr[r + 1]
+        assert np.array_equal(c[i], m.col[lo:hi])
+        assert np.array_equal(p[i], m.val[lo:hi])
+        assert g[i] == m.g[r]
+    b = banded_birth_death(300, 20, 16, 0.999)
+    rows = np.array([5, 2000, 5999])
+    c, p, g = regenerate_rows("banded_birth_death", dict(S=300, A=20), rows)
+    for i, r in enumerate(rows):
+        lo, hi = b.row_ptr[r], b.row_ptr[r + 1]
+        assert np.array_equal(c[i], b.col[lo:hi]) and np.array_equal(p[i], b.val[lo:hi])
+        assert g[i] == b.g[r]

@@ -1,0 +1,305 @@
+"""Pins for the FP64 oracle: closed forms, brute force, invariants and identities.
+
+Each check ties the oracle to something other than itself: a hand-derived
+solution, enumeration of all A**S policies with dense solves, a textbook BFS,
+or a property of the Bellman operator that holds for any MDP (Sec. II).
+"""
+import collections
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from mdpgen import maze, random_sparse, random_value_vector
+from oracle import mdp_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _args(m):
+    return (m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma)
+
+
+def _fixture_args(d):
+    return (d["S"], d["A"], np.array(d["row_ptr"]), np.array(d["col"]), np.array(d["val"]),
+            np.array(d["g"]), d["gamma"])
+
+
+# ---------------------------------------------------------------- golden closed forms
+
+@pytest.mark.parametrize("name", ["two_state.json", "three_state.json"])
+def test_golden_closed_form(name):
+    d = _load(name)
+    args = _fixture_args(d)
+    Vs, ps = np.array(d["V_star"]), np.array(d["pi_star"])
+    for inner in ("gmres", "richardson"):
+        r = O.ipi(*args, tol=1e-13, alpha=1e-3, inner=inner)
+        assert r.converged
+        np.testing.assert_allclose(r.V, Vs, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(r.pi, ps)
+    V, pi, _ = O.policy_iteration(*args)
+    np.testing.assert_allclose(V, Vs, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(pi, ps)
+    vi = O.value_iteration(*args, tol=1e-13)
+    np.testing.assert_allclose(vi.V, Vs, atol=1e-12)
+    Vb, opt, _ = O.brute_force(*args)
+    np.testing.assert_allclose(Vb, Vs, atol=1e-14)
+    assert tuple(ps) in opt
+    if "Q_star" in d:
+        P = O.stacked_matrix(d["S"], d["A"], args[2], args[3], args[4])
+        Q = O.q_values(P, args[5], d["gamma"], Vs, d["S"], d["A"])
+        np.testing.assert_allclose(Q, np.array(d["Q_star"]), atol=1e-15)
+
+
+def test_constant_cost_closed_form():
+    """g = c everywhere: V* = c / (1 - gamma), every action ties, pi* = 0 (lowest index)."""
+    m = random_sparse(40, 3, 5, 0.95, seed=11)
+    c = 0.37
+    g = np.full_like(m.g, c)
+    r = O.ipi(m.S, m.A, m.row_ptr, m.col, m.val, g, m.gamma, tol=1e-12, alpha=1e-3)
+    np.testing.assert_allclose(r.V, c / (1 - m.gamma), rtol=1e-12)
+    # exact ties: dyadic probabilities (rows sum to exactly 1), c = 1/4, gamma = 3/4, V = 1
+    q = random_sparse(40, 3, 5, 0.75, seed=11, quant_bits=11)
+    P = O.stacked_matrix(q.S, q.A, q.row_ptr, q.col, q.val)
+    TV, pi, res = O.bellman(P, np.full_like(q.g, 0.25), 0.75, np.ones(q.S), q.S, q.A)
+    assert res == 0.0 and np.all(TV == 1.0)
+    assert np.all(pi == 0)
+
+
+def test_single_action_uniform_closed_form():
+    """A = 1 with P = (1/S) 1 1^T: V = g + gamma mean(g) / (1 - gamma)."""
+    S, gamma = 17, 0.8
+    row_ptr = np.arange(S + 1) * S
+    col = np.tile(np.arange(S), S)
+    val = np.full(S * S, 1.0 / S)
+    g = np.linspace(-1.0, 2.0, S)
+    expect = g + gamma * g.mean() / (1 - gamma)
+    for inner in ("gmres", "richardson"):
+        r = O.ipi(S, 1, row_ptr, col, val, g, gamma, tol=1e-13, alpha=1e-4, inner=inner)
+        np.testing.assert_allclose(r.V, expect, atol=1e-12)
+
+
+def test_single_state_closed_form():
+    """S = 1: V* = min_a g(a) / (1 - gamma), pi* = first argmin."""
+    A, gamma = 6, 0.97
+    g = np.array([0.5, 0.2, 0.9, 0.2, 0.3, 1.0])
+    row_ptr = np.arange(A + 1)
+    r = O.ipi(1, A, row_ptr, np.zeros(A, dtype=np.int32), np.ones(A), g, gamma, tol=1e-12)
+    np.testing.assert_allclose(r.V, [0.2 / (1 - gamma)], rtol=1e-13)
+    assert r.pi[0] == 1
+
+
+def _bfs_distance(H, W, wall, goal_cell):
+    dist = np.full(H * W, -1, dtype=np.int64)
+    dist[goal_cell] = 0
+    q = collections.deque([goal_cell])
+    while q:
+        c = q.popleft()
+        y, x = divmod(c, W)
+        for dy, dx in ((-1, 0), (0, 1), (1, 0), (0, -1)):
+            ny, nx = y + dy, x + dx
+            if 0 <= ny < H and 0 <= nx < W:
+                n = ny * W + nx
+                if not wall[n] and dist[n] < 0:
+                    dist[n] = dist[c] + 1
+                    q.append(n)
+    return dist
+
+
+def test_maze_bfs_closed_form():
+    """Deterministic maze (Sec. IV-D): V*(s) = goal_cost * gamma**d(s) / (1 - gamma), d = BFS
+    distance to the goal; cells cut off from the goal stay put at cost 0 (V* = 0)."""
+    H, W = 9, 13
+    m, free_idx, goal = maze(H, W, wall_frac=0.25, seed=5, gamma=0.9)
+    wall = np.ones(H * W, dtype=bool)
+    wall[free_idx] = False
+    dist = _bfs_distance(H, W, wall, (H - 1) * W + (W - 1))[free_idx]
+    expect = np.where(dist >= 0, -100.0 * m.gamma ** np.maximum(dist, 0) / (1 - m.gamma), 0.0)
+    r = O.ipi(*_args(m), tol=1e-11, alpha=1e-4)
+    np.testing.assert_allclose(r.V, expect, atol=1e-8)
+    Vp, _, _ = O.policy_iteration(*_args(m))
+    np.testing.assert_allclose(Vp, expect, atol=1e-10)
+
+
+# ---------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_tiny(seed):
+    rng = np.random.default_rng(seed)
+    S, A = int(rng.integers(2, 6)), int(rng.integers(1, 4))
+    k = int(rng.integers(1, S + 1))
+    gamma = float(rng.choice([0.5, 0.9, 0.99]))
+    m = random_sparse(S, A, k, gamma, seed=100 + seed)
+    Vb, optimal, _ = O.brute_force(*_args(m))
+    scale = max(1.0, np.abs(Vb).max())
+    for inner in ("gmres", "richardson"):
+        r = O.ipi(*_args(m), tol=1e-12 * scale, alpha=1e-3, inner=inner)
+        assert r.converged
+        np.testing.assert_allclose(r.V, Vb, atol=1e-10 * scale)
+        assert tuple(r.pi) in optimal
+    Vp, pp, _ = O.policy_iteration(*_args(m))
+    np.testing.assert_allclose(Vp, Vb, atol=1e-11 * scale)
+    assert tuple(pp) in optimal
+
+
+# ---------------------------------------------------------------- invariants of T
+
+@pytest.fixture(scope="module")
+def mid_mdp():
+    return random_sparse(300, 5, 7, 0.93, seed=21)
+
+
+def test_contraction_monotone_shift(mid_mdp):
+    m = mid_mdp
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    V = random_value_vector(m.S, 1, 3.0)
+    Wv = random_value_vector(m.S, 2, 3.0)
+    TV, _, _ = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+    TW, _, _ = O.bellman(P, m.g, m.gamma, Wv, m.S, m.A)
+    assert np.max(np.abs(TV - TW)) <= m.gamma * np.max(np.abs(V - Wv)) * (1 + 1e-12)
+    # monotonicity: V <= V + |W| implies TV <= T(V + |W|)
+    TU, _, _ = O.bellman(P, m.g, m.gamma, V + np.abs(Wv), m.S, m.A)
+    assert np.all(TV <= TU + 1e-12)
+    # row-stochastic shift: T(V + c 1) = TV + gamma c 1
+    c = 1.75
+    TVc, pic, _ = O.bellman(P, m.g, m.gamma, V + c, m.S, m.A)
+    np.testing.assert_allclose(TVc, TV + m.gamma * c, atol=1e-12)
+
+
+def test_a_posteriori_bound_and_fixed_point(mid_mdp):
+    m = mid_mdp
+    Vs, ps, hist = O.policy_iteration(*_args(m))
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    TVs, pis, res = O.bellman(P, m.g, m.gamma, Vs, m.S, m.A)
+    assert res <= 1e-13 * max(1, np.abs(Vs).max())  # V* = T V* to the FP64 floor
+    np.testing.assert_array_equal(pis, ps)
+    for seed in range(3):
+        V = random_value_vector(m.S, 10 + seed, 5.0)
+        _, _, r = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+        assert np.max(np.abs(V - Vs)) <= r / (1 - m.gamma) * (1 + 1e-9)
+    # Howard PI decreases the cost monotonically
+    for a, b in zip(hist, hist[1:]):
+        assert np.all(b <= a + 1e-10)
+
+
+# ---------------------------------------------------------------- algorithm identities
+
+def test_richardson_one_step_is_value_iteration(mid_mdp):
+    """Table 2: Richardson with one step and omega = 1 is VI."""
+    m = mid_mdp
+    a = O.ipi(*_args(m), tol=1e-9, alpha=0.5, inner="richardson", max_inner=1, omega=1.0)
+    b = O.value_iteration(*_args(m), tol=1e-9)
+    assert a.outer_iters == b.outer_iters
+    np.testing.assert_allclose(a.V, b.V, atol=1e-11)
+    np.testing.assert_array_equal(a.pi, b.pi)
+
+
+def test_one_richardson_step_is_policy_operator(mid_mdp):
+    m = mid_mdp
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    V = random_value_vector(m.S, 3, 2.0)
+    TV, pi, _ = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    out = O.richardson(lambda x: O.apply_J(Ppi, m.gamma, x), gpi, V, 1.0, 0.0, 1)
+    assert out.iters == 1
+    np.testing.assert_allclose(out.x, TV, atol=1e-13)
+
+
+def test_unrestarted_gmres_is_exact_in_n_steps():
+    m = random_sparse(25, 3, 6, 0.97, seed=5)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    pi = np.arange(m.S) % m.A
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    exact = np.linalg.solve(np.eye(m.S) - m.gamma * Ppi.toarray(), gpi)
+    out = O.gmres(lambda x: O.apply_J(Ppi, m.gamma, x), gpi, np.zeros(m.S), m.S, 1e-300, m.S)
+    assert out.iters <= m.S
+    np.testing.assert_allclose(out.x, exact, atol=1e-12 * np.abs(exact).max())
+    # the reported residual is the true one
+    r = gpi - O.apply_J(Ppi, m.gamma, out.x)
+    assert abs(np.linalg.norm(r) - out.res2) <= 1e-15 * max(1, np.linalg.norm(gpi))
+
+
+def test_gmres_restarted_matches_dense(mid_mdp):
+    m = mid_mdp
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    pi = (np.arange(m.S) * 7) % m.A
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    exact = np.linalg.solve(np.eye(m.S) - m.gamma * Ppi.toarray(), gpi)
+    out = O.gmres(lambda x: O.apply_J(Ppi, m.gamma, x), gpi, np.zeros(m.S), 10, 1e-12, 10000)
+    assert out.res2 < 1e-12
+    np.testing.assert_allclose(out.x, exact, atol=1e-10)
+
+
+def test_beta_vi_and_opi_converge_to_optimum(mid_mdp):
+    """beta-VI (Richardson scale beta, one step) and OPI(W) (W steps) reach V* (Table 2)."""
+    m = mid_mdp
+    Vs, _, _ = O.policy_iteration(*_args(m))
+    b = O.ipi(*_args(m), tol=1e-10, alpha=0.5, inner="richardson", max_inner=1, omega=0.8)
+    w = O.ipi(*_args(m), tol=1e-10, alpha=1e-9, inner="richardson", max_inner=5)
+    for r in (b, w):
+        assert r.converged
+        assert np.max(np.abs(r.V - Vs)) <= 1e-10 / (1 - m.gamma)
+
+
+def test_bellman_states_matches_stacked(mid_mdp):
+    m = mid_mdp
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    V = random_value_vector(m.S, 4, 1.0)
+    TV, pi, _ = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+    states = np.array([0, 7, 299])
+    rows = (states[:, None] * m.A + np.arange(m.A)[None, :]).ravel()
+    k = 7
+    cols = np.stack([m.col[m.row_ptr[r]:m.row_ptr[r] + k] for r in rows])
+    vals = np.stack([m.val[m.row_ptr[r]:m.row_ptr[r] + k] for r in rows])
+    Q, tv, p = O.bellman_states(states, cols, vals, m.g[rows], m.gamma, V, m.A)
+    np.testing.assert_allclose(tv, TV[states], atol=1e-15)
+    np.testing.assert_array_equal(p, pi[states])
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _bellman_argmax_ties(P, g, gamma, V, S, A):
+    Q = O.q_values(P, g, gamma, V, S, A)
+    return Q.min(axis=1), (A - 1 - np.argmin(Q[:, ::-1], axis=1)).astype(np.int32), float(np.max(np.abs(V - Q.min(axis=1))))
+
+
+def _bellman_transposed(P, g, gamma, V, S, A):
+    Q = np.asarray(g).reshape(S, A) + gamma * (P @ V).reshape(A, S).T
+    return Q.min(axis=1), Q.argmin(axis=1).astype(np.int32), float(np.max(np.abs(V - Q.min(axis=1))))
+
+
+def _pins_hold():
+    """Run a subset of the pins; True when all pass."""
+    try:
+        test_golden_closed_form("two_state.json")
+        test_golden_closed_form("three_state.json")
+        test_constant_cost_closed_form()
+        test_single_state_closed_form()
+        for s in range(3):
+            test_brute_force_tiny(s)
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("mutant", ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign"])
+def test_planted_mistakes_are_caught(monkeypatch, mutant):
+    """Plausible mistakes planted in the oracle make at least one pin fail."""
+    assert _pins_hold()
+    if mutant == "argmax_ties":
+        monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
+    elif mutant == "gamma_one":
+        orig = O.bellman
+        monkeypatch.setattr(O, "bellman", lambda P, g, gamma, V, S, A: orig(P, g, min(1.0, gamma * 1.02), V, S, A))
+    elif mutant == "action_major_layout":
+        monkeypatch.setattr(O, "bellman", _bellman_transposed)
+    elif mutant == "inner_sign":
+        monkeypatch.setattr(O, "apply_J", lambda Ppi, gamma, x: x + gamma * (Ppi @ x))
+    assert not _pins_hold()
