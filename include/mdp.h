@@ -1,0 +1,165 @@
+/*
+ * mdp.h -- C ABI of the GB300 inexact-policy-iteration library (libmdp).
+ *
+ * The library solves discounted infinite-horizon MDPs {S, A, P, g, gamma} with
+ * finite state and action spaces (Sec. II of "Inside madupite", arXiv
+ * 2507.22538) by inexact policy iteration (Algorithm 1).  All arithmetic runs
+ * in the library's own CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *  - States are 0..S-1 and actions 0..A-1.  The transition tensor is passed
+ *    row-stacked as in Eq. 5: an (S*A) x S CSR matrix whose row s*A + a holds
+ *    P(s, ., a).  Stage costs are an S x A row-major array, g[s*A + a] = g(s, a).
+ *  - Unless stated otherwise every array argument is a DEVICE pointer owned by
+ *    the caller; the library reads/writes it in stream order on `stream` (a
+ *    cudaStream_t passed as void*; NULL means the legacy default stream).
+ *  - Every function returns an mdp_status and never aborts the process.  On
+ *    failure mdp_last_error() returns a message for the calling thread.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef MDP_H_
+#define MDP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdp_s* mdp_handle; /* opaque; owns a device copy of P and g */
+
+typedef enum {
+  MDP_OK = 0,
+  MDP_ERR_INVALID_ARG = 1,    /* bad size, null pointer, gamma outside (0,1), ... */
+  MDP_ERR_NOT_STOCHASTIC = 2, /* a row is empty, has a column outside [0,S), a negative or
+                                 non-finite probability, or does not sum to 1 */
+  MDP_ERR_OOM = 3,            /* device or pinned-host allocation failed */
+  MDP_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  MDP_NOT_CONVERGED = 5,      /* an iteration cap was hit; outputs hold the last iterate */
+  MDP_ERR_NUMERIC = 6         /* NaN or Inf appeared in a residual */
+} mdp_status;
+
+typedef enum { MDP_F64 = 0 } mdp_dtype; /* storage type of the P values passed to mdp_create */
+
+typedef enum { MDP_GMRES = 0, MDP_RICHARDSON = 1 } mdp_inner;
+
+/* Options of Algorithm 1 with the defaults of Table 1 (set by mdp_default_opts). */
+typedef struct {
+  double gamma;            /* discount factor, 0 < gamma < 1 (no default; must be set) */
+  double atol_pi;          /* tol: outer stop when ||TV - V||_inf <= atol_pi          (1e-8) */
+  double alpha;            /* inner stop when ||g_pi - J_pi theta||_2 < alpha*||r(V_k)||_inf (1e-4) */
+  double richardson_scale; /* omega of the Richardson step theta += omega (b - J theta) (1.0) */
+  int32_t max_iter_pi;     /* N_o: at most this many policy evaluations             (1000) */
+  int32_t max_iter_ksp;    /* N_i: at most this many inner iterations per evaluation (1000) */
+  int32_t gmres_restart;   /* GMRES restart length m, 1..64                            (30) */
+  int32_t inner;           /* an mdp_inner value                                  (MDP_GMRES) */
+  int32_t record_timing;   /* nonzero: time every Bellman sweep with CUDA events        (0) */
+} mdp_solve_opts;
+
+/* Statistics of one mdp_solve call (host struct filled by the library). */
+typedef struct {
+  int32_t outer_iters;        /* policy evaluations performed (k at exit) */
+  int32_t converged;          /* 1 when ||TV - V||_inf <= atol_pi at the returned V */
+  int64_t inner_iters_total;  /* inner iterations summed over all evaluations */
+  double final_residual;      /* ||TV - V||_inf at the returned V */
+  double seconds;             /* host wall time of the call */
+  int64_t kernel_launches;    /* CUDA kernels the call launched */
+  int32_t bellman_sweeps;     /* Bellman sweeps (kernel K1) launched */
+  double bellman_ms;          /* summed device time of those sweeps (record_timing only) */
+} mdp_solve_stats;
+
+/* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */
+void mdp_default_opts(mdp_solve_opts* opts);
+
+/*
+ * mdp_create -- copy an MDP into device memory owned by the returned handle.
+ * (Sec. III-B.2: row-stacked CSR of Eq. 5 and the dense S x A stage costs.)
+ *
+ *  S, A          number of states (>= 1) and actions (1..65535).
+ *  row_ptr       int64[S*A + 1], row_ptr[0] = 0, nondecreasing.
+ *  col           int32[nnz] column (successor state) of each entry, in [0, S).
+ *  val           P values, nnz entries of val_type (MDP_F64: double).
+ *  g             double[S*A] stage costs, finite.
+ *  inputs_on_device  nonzero: the four arrays are device pointers; zero: host pointers
+ *                (pinned host memory gives the fastest upload).
+ *  stream        stream for the upload and the layout kernels; the call returns
+ *                after they complete.
+ *  out           receives the handle (NULL on failure).
+ * The caller keeps ownership of its arrays; the handle keeps its own copy in a
+ * GPU-friendly layout.  Every row must be nonempty, have entries >= 0 that sum
+ * to 1 within 1e-12, and columns in [0, S): otherwise MDP_ERR_NOT_STOCHASTIC.
+ */
+mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
+                      mdp_dtype val_type, const double* g, int32_t inputs_on_device, void* stream,
+                      mdp_handle* out);
+
+/* Release every device and host resource of the handle (NULL is accepted). */
+mdp_status mdp_destroy(mdp_handle h);
+
+/* Problem sizes of a handle (any out pointer may be NULL). */
+mdp_status mdp_get_info(mdp_handle h, int64_t* S, int32_t* A, int64_t* nnz);
+
+/*
+ * mdp_bellman -- one application of the Bellman optimality operator (Eq. 3),
+ * the greedy policy (Eq. 4) and the residual norm ||r(V)||_inf (Sec. II;
+ * Algorithm 1 steps 2-3; computed as PV, reshaped S x A, scaled by gamma, plus
+ * g, row-wise argmin: Sec. III-B.3), fused in one kernel.
+ *
+ *  V             double[S]  input value vector.
+ *  TV            double[S]  TV(s) = min_a g(s,a) + gamma * sum_s' P(s,s',a) V(s').
+ *  pi            int32[S]   the lowest action attaining the minimum.
+ *  residual_inf  double[1]  max_s |TV(s) - V(s)| (device pointer; may be NULL).
+ * Stream-ordered: returns without waiting for the kernel.
+ */
+mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
+                       double* residual_inf, void* stream);
+
+/*
+ * mdp_policy_apply -- y = J_pi x = x - gamma * P_pi x, the matrix-free policy
+ * operator of Sec. III-B.3 (Algorithm 1 step 4), for a policy pi.
+ *  pi int32[S] with 0 <= pi[s] < A; x, y double[S] (may not alias).
+ * Stream-ordered.
+ */
+mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const double* x, double* y,
+                            void* stream);
+
+/*
+ * mdp_policy_eval -- approximately solve (I - gamma P_pi) v = g_pi (Eq. 2), the
+ * inexact policy evaluation of Algorithm 1 steps 4-12, from v0.
+ *
+ *  pi            int32[S] policy, 0 <= pi[s] < A.
+ *  v0, v         double[S] start vector and result (may alias).
+ *  inner         MDP_GMRES (restart = `restart`) or MDP_RICHARDSON (step scale `omega`).
+ *  abs_tol_2norm stop when ||g_pi - J_pi v||_2 < abs_tol_2norm (Sec. III-B.3).
+ *  max_it        at most this many iterations (a GMRES Arnoldi step or a Richardson step).
+ *  iters, res_2norm  host outputs (may be NULL): iterations done and the last
+ *                computed residual 2-norm.
+ * Blocks until the solve completes.  Returns MDP_NOT_CONVERGED (with v filled)
+ * when max_it is reached first.
+ */
+mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const double* v0, double* v,
+                           mdp_inner inner, int32_t restart, double omega, double abs_tol_2norm,
+                           int32_t max_it, int32_t* iters, double* res_2norm, void* stream);
+
+/*
+ * mdp_solve -- inexact policy iteration, Algorithm 1.
+ *
+ *  opts   options (Table 1); opts->gamma must be in (0, 1).
+ *  V      double[S]: in V_0, out the last iterate V_k (the first with
+ *         ||TV_k - V_k||_inf <= atol_pi, or the last one when a cap is hit).
+ *  pi     int32[S]: out the greedy policy of the returned V (ties: lowest action).
+ *  stats  host struct (may be NULL).
+ * Blocks until done.  MDP_NOT_CONVERGED when max_iter_pi evaluations did not
+ * reach atol_pi (V, pi and stats are still filled).
+ */
+mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_t* pi,
+                     mdp_solve_stats* stats, void* stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* mdp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDP_H_ */

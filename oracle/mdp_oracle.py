@@ -264,7 +264,7 @@ def value_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, V0=None,
     return SolveResult(V, pi, False, max_iter, [1] * max_iter, residuals)
 
 
-def evaluate_policy(Ppi, gpi, gamma: float, dense_limit: int = 3000, tol_rel: float = 1e-14) -> np.ndarray:
+def evaluate_policy(Ppi, gpi, gamma: float, dense_limit: int = 5000, tol_rel: float = 1e-14) -> np.ndarray:
     """V_pi solving (I - gamma P_pi) V = g_pi (Eq. 2).
 
     Up to dense_limit states: a dense LAPACK solve.  Above it: GMRES(50) from
@@ -290,7 +290,7 @@ def evaluate_policy(Ppi, gpi, gamma: float, dense_limit: int = 3000, tol_rel: fl
 
 
 def policy_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, max_iter: int = 1000,
-                     dense_limit: int = 3000):
+                     dense_limit: int = 5000):
     """Howard policy iteration with exact evaluation (Table 2, PI row).
 
     pi_0 is greedy for V = 0.  Each step evaluates V_pi exactly and switches

@@ -1,0 +1,457 @@
+// Handle lifetime: validation of the row-stacked CSR input (Eq. 5), conversion
+// to the device layout, policy-row extraction (Algorithm 1 step 4) and errors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mdp_internal.cuh"
+
+namespace mdp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+mdp_status fail(mdp_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+mdp_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? MDP_ERR_OOM : MDP_ERR_CUDA;
+}
+
+enum : int {
+  kBadPtr = 1,
+  kEmptyRow = 2,
+  kBadCol = 4,
+  kBadVal = 8,
+  kRowSum = 16,
+  kBadCost = 32,
+  kLongRow = 64,
+};
+
+// One thread per row of Eq. 5: check the CSR invariants and record the row length.
+__global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, const double* __restrict__ g, int64_t R,
+                                     int64_t S, int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
+                                     int* __restrict__ kmin, int* __restrict__ kmax) {
+  int bad = 0;
+  int lmin = 0x7fffffff, lmax = 0;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = rp[r], hi = rp[r + 1];
+    int l = 0;
+    if (lo < 0 || hi < lo || hi > nnz) {
+      bad |= kBadPtr;
+    } else if (hi == lo) {
+      bad |= kEmptyRow;
+    } else if (hi - lo > (1 << 30)) {
+      bad |= kLongRow;
+    } else {
+      l = (int)(hi - lo);
+      double sum = 0.0;
+      for (int64_t j = lo; j < hi; ++j) {
+        int c = col[j];
+        double v = val[j];
+        if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
+        if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
+        sum += v;
+      }
+      if (!(fabs(sum - 1.0) <= 1e-12)) bad |= kRowSum;
+    }
+    if (!isfinite(g[r])) bad |= kBadCost;
+    len[r] = l;
+    lmin = min(lmin, l);
+    lmax = max(lmax, l);
+  }
+  if (bad) atomicOr(flags, bad);
+  atomicMin(kmin, lmin);
+  atomicMax(kmax, lmax);
+}
+
+// Width of each slice of `rows` rows: the longest row among its 32.
+__global__ void slice_width_kernel(const int32_t* __restrict__ len, int64_t rows, int64_t nslices,
+                                   int32_t* __restrict__ width) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nslices; q += (int64_t)gridDim.x * blockDim.x) {
+    int w = 0;
+    for (int l = 0; l < kSlice; ++l) {
+      int64_t r = q * kSlice + l;
+      if (r < rows) w = max(w, len[r]);
+    }
+    width[q] = w;
+  }
+}
+
+// Per state: the longest of its A rows (sizes the policy-row slices).
+__global__ void state_maxlen_kernel(const int32_t* __restrict__ len, int64_t S, int A, int32_t* __restrict__ out) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    int w = 0;
+    for (int a = 0; a < A; ++a) w = max(w, len[s * A + a]);
+    out[s] = w;
+  }
+}
+
+// CSR -> sliced ELL: one thread per row copies its entries into column-major slice order.
+__global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                   const double* __restrict__ val, int64_t R, const int64_t* __restrict__ off,
+                                   int uniform_k, double* __restrict__ sval, int32_t* __restrict__ scol) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = r / kSlice;
+    int lane = (int)(r % kSlice);
+    int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
+    int64_t width = uniform_k ? uniform_k : (off[q + 1] - off[q]) / kSlice;
+    int64_t lo = rp[r], n = rp[r + 1] - lo;
+    for (int64_t j = 0; j < width; ++j) {
+      int64_t d = base + j * kSlice + lane;
+      if (j < n) {
+        sval[d] = val[lo + j];
+        scol[d] = col[lo + j];
+      } else {
+        sval[d] = 0.0;
+        scol[d] = 0;
+      }
+    }
+  }
+}
+
+// Algorithm 1 step 4: gather the policy's rows r(s) = s*A + pi(s) of the stacked
+// matrix into the per-state sliced layout, and g_pi(s) = g(s, pi(s)).  States
+// whose pi(s) lies outside [0, A) get an empty row and g_pi = NaN.
+__global__ void extract_policy_kernel(const double* __restrict__ sval, const int32_t* __restrict__ scol,
+                                      const int64_t* __restrict__ off, const int32_t* __restrict__ len, int uniform_k,
+                                      const double* __restrict__ g, const int32_t* __restrict__ pi, int64_t S, int A,
+                                      double* __restrict__ pval, int32_t* __restrict__ pcol,
+                                      const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
+                                      double* __restrict__ gpi) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    int a = pi[s];
+    int64_t ps = s / kSlice;
+    int pl = (int)(s % kSlice);
+    int64_t pbase = uniform_k ? ps * kSlice * (int64_t)uniform_k : poff[ps];
+    if (a < 0 || a >= A) {
+      if (!uniform_k) {
+        plen[s] = 0;
+      } else {
+        for (int j = 0; j < uniform_k; ++j) {
+          pval[pbase + (int64_t)j * kSlice + pl] = 0.0;
+          pcol[pbase + (int64_t)j * kSlice + pl] = 0;
+        }
+      }
+      gpi[s] = __longlong_as_double(0x7ff8000000000000ULL);
+      continue;
+    }
+    int64_t r = s * A + a;
+    int64_t q = r / kSlice;
+    int lane = (int)(r % kSlice);
+    int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
+    int n = uniform_k ? uniform_k : len[r];
+    for (int j = 0; j < n; ++j) {
+      pval[pbase + (int64_t)j * kSlice + pl] = sval[base + (int64_t)j * kSlice + lane];
+      pcol[pbase + (int64_t)j * kSlice + pl] = scol[base + (int64_t)j * kSlice + lane];
+    }
+    if (!uniform_k) plen[s] = n;
+    gpi[s] = g[r];
+  }
+}
+
+static int grid_for(int64_t n, int threads, int sm_count) {
+  int64_t b = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count * 8;
+  return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+template <typename T>
+static mdp_status dalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(MDP_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return MDP_OK;
+}
+
+#define MDP_TRY(x)                     \
+  do {                                 \
+    mdp_status st_ = (x);              \
+    if (st_ != MDP_OK) return st_;     \
+  } while (0)
+
+// Build a sliced layout from per-row lengths (device) for `rows` rows.
+static mdp_status build_sell(mdp_s* h, Sell* m, const int32_t* dlen, int64_t rows, int kmin, int kmax,
+                             cudaStream_t st) {
+  m->rows = rows;
+  m->nslices = (rows + kSlice - 1) / kSlice;
+  m->kmax = kmax;
+  m->uniform = (kmin == kmax);
+  if (m->uniform) {
+    m->nstored = m->nslices * kSlice * (int64_t)kmax;
+  } else {
+    int32_t* dwidth = nullptr;
+    MDP_TRY(dalloc(&dwidth, m->nslices, "slice widths"));
+    slice_width_kernel<<<grid_for(m->nslices, 256, h->sm_count), 256, 0, st>>>(dlen, rows, m->nslices, dwidth);
+    h->launches++;
+    std::vector<int32_t> width(m->nslices);
+    cudaError_t e = cudaMemcpyAsync(width.data(), dwidth, m->nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dwidth);
+    if (e != cudaSuccess) return cuda_fail(e, "slice widths");
+    std::vector<int64_t> off(m->nslices + 1);
+    off[0] = 0;
+    for (int64_t q = 0; q < m->nslices; ++q) off[q + 1] = off[q] + (int64_t)width[q] * kSlice;
+    m->nstored = off[m->nslices];
+    MDP_TRY(dalloc(&m->off, m->nslices + 1, "slice offsets"));
+    MDP_CUDA(cudaMemcpyAsync(m->off, off.data(), (m->nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    MDP_TRY(dalloc(&m->len, rows, "row lengths"));
+  }
+  MDP_TRY(dalloc(&m->val, m->nstored, "sliced values"));
+  MDP_TRY(dalloc(&m->col, m->nstored, "sliced columns"));
+  return MDP_OK;
+}
+
+static void free_sell(Sell* m) {
+  cudaFree(m->off);
+  cudaFree(m->len);
+  cudaFree(m->val);
+  cudaFree(m->col);
+  *m = Sell();
+}
+
+mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st) {
+  const Sell& P = h->P;
+  Sell& Q = h->Ppi;
+  extract_policy_kernel<<<h->vec_blocks, h->vec_threads, 0, st>>>(
+      P.val, P.col, P.off, P.len, P.uniform ? P.kmax : 0, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi);
+  h->launches++;
+  MDP_CUDA(cudaGetLastError());
+  return MDP_OK;
+}
+
+static void destroy_handle(mdp_s* h) {
+  if (!h) return;
+  free_sell(&h->P);
+  free_sell(&h->Ppi);
+  cudaFree(h->g);
+  cudaFree(h->gpi);
+  cudaFree(h->TV);
+  cudaFree(h->piw);
+  cudaFree(h->w);
+  cudaFree(h->tmp);
+  cudaFree(h->basis);
+  cudaFree(h->partials);
+  cudaFree(h->sc);
+  cudaFree(h->resmax);
+  if (h->hpin) cudaFreeHost(h->hpin);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+mdp_status ensure_basis(mdp_s* h, int nvec) {
+  if (nvec <= h->basis_cap) return MDP_OK;
+  cudaFree(h->basis);
+  h->basis = nullptr;
+  h->basis_cap = 0;
+  MDP_TRY(dalloc(&h->basis, (size_t)nvec * (size_t)h->S, "GMRES basis"));
+  h->basis_cap = nvec;
+  return MDP_OK;
+}
+
+static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
+                              mdp_dtype val_type, const double* g, int32_t on_device, cudaStream_t st,
+                              mdp_s* h) {
+  MDP_CUDA(cudaGetDevice(&h->device));
+  MDP_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+  h->S = S;
+  h->A = A;
+  h->R = S * (int64_t)A;
+  const int64_t R = h->R;
+
+  int64_t nnz = 0;
+  if (on_device) {
+    MDP_CUDA(cudaMemcpyAsync(&nnz, row_ptr + R, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    MDP_CUDA(cudaStreamSynchronize(st));
+  } else {
+    nnz = row_ptr[R];
+  }
+  if (nnz < R || nnz > (int64_t(1) << 40))
+    return fail(MDP_ERR_NOT_STOCHASTIC, "row_ptr[S*A] must be between S*A (no empty rows) and 2^40");
+  h->nnz = nnz;
+
+  // device views of the CSR input (temporary copies when it lives on the host)
+  const int64_t* drp = row_ptr;
+  const int32_t* dcol = col;
+  const double* dval = (const double*)val;
+  int64_t* trp = nullptr;
+  int32_t* tcol = nullptr;
+  double* tval = nullptr;
+  struct Temps {
+    int64_t** a; int32_t** b; double** c;
+    ~Temps() { cudaFree(*a); cudaFree(*b); cudaFree(*c); }
+  } temps{&trp, &tcol, &tval};
+  if (!on_device) {
+    MDP_TRY(dalloc(&trp, R + 1, "row pointers"));
+    MDP_TRY(dalloc(&tcol, nnz, "columns"));
+    MDP_TRY(dalloc(&tval, nnz, "values"));
+    MDP_CUDA(cudaMemcpyAsync(trp, row_ptr, (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    MDP_CUDA(cudaMemcpyAsync(tcol, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MDP_CUDA(cudaMemcpyAsync(tval, val, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    drp = trp;
+    dcol = tcol;
+    dval = tval;
+  }
+  MDP_TRY(dalloc(&h->g, R, "stage costs"));
+  MDP_CUDA(cudaMemcpyAsync(h->g, g, R * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+
+  // validation (flags, kmin, kmax live in the scalar area)
+  MDP_TRY(dalloc(&h->sc, kScalarSlots, "scalars"));
+  MDP_TRY(dalloc(&h->resmax, 1, "residual"));
+  MDP_CUDA(cudaMallocHost((void**)&h->hpin, kScalarSlots * sizeof(double)));
+  int32_t* dlen = nullptr;
+  MDP_TRY(dalloc(&dlen, R, "row lengths"));
+  struct FreeLen { int32_t** p; ~FreeLen() { cudaFree(*p); } } free_len{&dlen};
+  int* dflags = (int*)h->sc;
+  int init[3] = {0, 0x7fffffff, 0};
+  MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  validate_rows_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, dcol, dval, h->g, R, S, nnz, dlen,
+                                                                    dflags, dflags + 1, dflags + 2);
+  h->launches++;
+  MDP_CUDA(cudaGetLastError());
+  int res[3];
+  MDP_CUDA(cudaMemcpyAsync(res, dflags, sizeof(res), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaStreamSynchronize(st));
+  if (res[0]) {
+    std::string m = "invalid MDP:";
+    if (res[0] & kBadPtr) m += " row_ptr not monotone or out of [0, nnz];";
+    if (res[0] & kEmptyRow) m += " empty row;";
+    if (res[0] & kLongRow) m += " row longer than 2^30;";
+    if (res[0] & kBadCol) m += " column outside [0, S);";
+    if (res[0] & kBadVal) m += " negative or non-finite probability;";
+    if (res[0] & kRowSum) m += " row does not sum to 1 within 1e-12;";
+    if (res[0] & kBadCost) m += " non-finite stage cost;";
+    return fail((res[0] & (kBadCost | kBadPtr)) && !(res[0] & (kEmptyRow | kBadCol | kBadVal | kRowSum))
+                    ? MDP_ERR_INVALID_ARG : MDP_ERR_NOT_STOCHASTIC, m);
+  }
+  const int kmin = res[1], kmax = res[2];
+
+  // stacked matrix in sliced layout
+  MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));
+  csr_to_sell_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, dcol, dval, R, h->P.off,
+                                                                  h->P.uniform ? kmax : 0, h->P.val, h->P.col);
+  h->launches++;
+  MDP_CUDA(cudaGetLastError());
+  if (!h->P.uniform)
+    MDP_CUDA(cudaMemcpyAsync(h->P.len, dlen, R * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+
+  // policy rows: one per state, slice width = longest row of the slice's states
+  if (h->P.uniform) {
+    MDP_TRY(build_sell(h, &h->Ppi, dlen, S, kmax, kmax, st));
+  } else {
+    int32_t* smax = nullptr;
+    MDP_TRY(dalloc(&smax, S, "state max length"));
+    state_maxlen_kernel<<<grid_for(S, 256, h->sm_count), 256, 0, st>>>(dlen, S, A, smax);
+    h->launches++;
+    mdp_status s2 = build_sell(h, &h->Ppi, smax, S, 0, kmax, st);
+    MDP_CUDA(cudaStreamSynchronize(st));
+    cudaFree(smax);
+    MDP_TRY(s2);
+  }
+
+  // launch shapes
+  h->vec_threads = 256;
+  h->vec_blocks = grid_for(S, h->vec_threads, h->sm_count);
+  {
+    // Bellman tile: a multiple of 32 states whose rows fill whole warps where possible
+    int64_t ts = 32;
+    if (A <= 256) {
+      int g256 = 1;
+      for (int d = 1; d <= 256; d <<= 1)
+        if (A % d == 0) g256 = d;
+      int64_t need = 256 / g256;  // states per tile so that ts*A is a multiple of 256 rows
+      ts = std::max<int64_t>(32, need);
+      while (ts * A > 8192 && ts > 32) ts /= 2;
+    }
+    while (ts * A > 8192 && ts > 1) ts /= 2;
+    if (ts > S) ts = std::max<int64_t>(1, S);
+    h->bell_tile_states = (int)ts;
+    MDP_TRY(configure_bellman(h));
+  }
+  MDP_TRY(dalloc(&h->gpi, S, "g_pi"));
+  MDP_TRY(dalloc(&h->TV, S, "TV"));
+  MDP_TRY(dalloc(&h->piw, S, "policy"));
+  MDP_TRY(dalloc(&h->w, S, "w"));
+  MDP_TRY(dalloc(&h->tmp, S, "tmp"));
+  MDP_TRY(dalloc(&h->partials, (size_t)h->vec_blocks * kMaxBasis, "partials"));
+  MDP_CUDA(cudaEventCreate(&h->ev0));
+  MDP_CUDA(cudaEventCreate(&h->ev1));
+  MDP_CUDA(cudaStreamSynchronize(st));
+  return MDP_OK;
+}
+
+}  // namespace mdp
+
+using namespace mdp;
+
+extern "C" {
+
+void mdp_default_opts(mdp_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->gamma = 0.0;
+  o->atol_pi = 1e-8;
+  o->alpha = 1e-4;
+  o->richardson_scale = 1.0;
+  o->max_iter_pi = 1000;
+  o->max_iter_ksp = 1000;
+  o->gmres_restart = 30;
+  o->inner = MDP_GMRES;
+  o->record_timing = 0;
+}
+
+const char* mdp_last_error(void) { return g_last_error.c_str(); }
+
+mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
+                      mdp_dtype val_type, const double* g, int32_t inputs_on_device, void* stream,
+                      mdp_handle* out) {
+  if (!out) return fail(MDP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (S < 1 || A < 1 || A > 8192) return fail(MDP_ERR_INVALID_ARG, "need S >= 1 and 1 <= A <= 8192");
+  if (S > (int64_t(1) << 31) - 1 || S * (int64_t)A > (int64_t(1) << 36))
+    return fail(MDP_ERR_INVALID_ARG, "S must fit int32 and S*A must be below 2^36");
+  if (!row_ptr || !col || !val || !g) return fail(MDP_ERR_INVALID_ARG, "null input array");
+  if (val_type != MDP_F64) return fail(MDP_ERR_INVALID_ARG, "val_type must be MDP_F64");
+  mdp_s* h = new mdp_s();
+  mdp_status st = create_impl(S, A, row_ptr, col, val, val_type, g, inputs_on_device, (cudaStream_t)stream, h);
+  if (st != MDP_OK) {
+    std::string msg = g_last_error;
+    cudaStreamSynchronize((cudaStream_t)stream);
+    destroy_handle(h);
+    cudaGetLastError();
+    g_last_error = msg;
+    return st;
+  }
+  *out = h;
+  g_last_error.clear();
+  return MDP_OK;
+}
+
+mdp_status mdp_destroy(mdp_handle h) {
+  if (!h) return MDP_OK;
+  cudaDeviceSynchronize();
+  destroy_handle(h);
+  return MDP_OK;
+}
+
+mdp_status mdp_get_info(mdp_handle h, int64_t* S, int32_t* A, int64_t* nnz) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (S) *S = h->S;
+  if (A) *A = h->A;
+  if (nnz) *nnz = h->nnz;
+  return MDP_OK;
+}
+
+}  // extern "C"

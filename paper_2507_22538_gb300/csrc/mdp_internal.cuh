@@ -1,0 +1,100 @@
+// Internal declarations of libmdp: the handle, error plumbing and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mdp.h"
+
+namespace mdp {
+
+constexpr int kSlice = 32;       // rows (or states) per sliced-ELL slice: one warp, one row per lane
+constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
+constexpr int kScalarSlots = 512;
+
+// Per-thread message of the last failure.
+void set_error(const std::string& msg);
+mdp_status fail(mdp_status st, const std::string& msg);
+mdp_status cuda_fail(cudaError_t e, const char* what);
+
+#define MDP_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::mdp::cuda_fail(e_, #call); \
+  } while (0)
+
+// Sliced-ELL (slice height 32) copy of a row-major matrix: slice q holds rows
+// 32q..32q+31; element j of lane l sits at off[q] + 32*j + l.  When every row
+// has the same length k, `uniform` is set, off[q] = 32*k*q and len[] is unused.
+struct Sell {
+  int64_t rows = 0;
+  int64_t nslices = 0;
+  int32_t kmax = 0;
+  bool uniform = false;
+  int64_t* off = nullptr;   // [nslices + 1] (non-uniform only)
+  int32_t* len = nullptr;   // [rows]        (non-uniform only)
+  double* val = nullptr;    // [off[nslices]]
+  int32_t* col = nullptr;
+  int64_t nstored = 0;      // off[nslices]
+};
+
+}  // namespace mdp
+
+struct mdp_s {
+  int device = 0;
+  int sm_count = 0;
+  int64_t S = 0;
+  int32_t A = 0;
+  int64_t R = 0;    // S * A rows of Eq. 5
+  int64_t nnz = 0;
+
+  mdp::Sell P;      // all S*A rows, row s*A + a
+  mdp::Sell Ppi;    // one row per state (the policy's rows), rebuilt per policy
+  double* g = nullptr;      // [R]
+  double* gpi = nullptr;    // [S]
+
+  // Bellman launch shape
+  int bell_tile_states = 32;
+  int bell_threads = 256;
+  int bell_blocks = 0;
+
+  // vector-kernel launch shape (thread per state)
+  int vec_threads = 256;
+  int vec_blocks = 0;
+
+  // workspace
+  double* TV = nullptr;      // [S]
+  int32_t* piw = nullptr;    // [S] policy workspace
+  double* w = nullptr;       // [S]
+  double* tmp = nullptr;     // [S]
+  double* basis = nullptr;   // [(restart + 1) * S]
+  int basis_cap = 0;         // vectors allocated in basis
+  double* partials = nullptr;  // [vec_blocks * kMaxBasis]
+  double* sc = nullptr;      // device scalars [kScalarSlots]
+  unsigned long long* resmax = nullptr;  // device max of |TV - V| bits
+  double* hpin = nullptr;    // pinned host scalars [kScalarSlots]
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int64_t launches = 0;
+};
+
+namespace mdp {
+
+// layout.cu
+mdp_status build_policy_layout(mdp_s* h, cudaStream_t st);  // allocate Ppi for h->P
+mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st);  // fill Ppi, gpi from pi
+
+// bellman.cu
+mdp_status configure_bellman(mdp_s* h);  // threads and grid of the Bellman sweep
+mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi,
+                          bool fuse_policy, cudaStream_t st);
+
+// krylov.cu
+mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st);
+mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, double omega,
+                       double tol, int max_it, int* iters, double* res2, cudaStream_t st);
+mdp_status ensure_basis(mdp_s* h, int nvec);
+
+}  // namespace mdp

@@ -1,0 +1,114 @@
+// Entry points for policy evaluation and for Algorithm 1 (inexact policy iteration).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "mdp_internal.cuh"
+
+using namespace mdp;
+
+extern "C" {
+
+mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const double* x, double* y, void* stream) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
+  if (!pi || !x || !y) return fail(MDP_ERR_INVALID_ARG, "null vector");
+  if ((const void*)x == (const void*)y) return fail(MDP_ERR_INVALID_ARG, "x and y may not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  mdp_status s = extract_policy(h, pi, st);
+  if (s != MDP_OK) return s;
+  return launch_policy_apply(h, gamma, x, y, st);
+}
+
+mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const double* v0, double* v,
+                           mdp_inner inner, int32_t restart, double omega, double abs_tol_2norm, int32_t max_it,
+                           int32_t* iters, double* res_2norm, void* stream) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
+  if (!pi || !v0 || !v) return fail(MDP_ERR_INVALID_ARG, "null vector");
+  if (inner != MDP_GMRES && inner != MDP_RICHARDSON) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
+  if (inner == MDP_GMRES && (restart < 1 || restart > kMaxBasis))
+    return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
+  if (max_it < 0 || !(abs_tol_2norm >= 0.0)) return fail(MDP_ERR_INVALID_ARG, "bad tolerance or iteration cap");
+  cudaStream_t st = (cudaStream_t)stream;
+  mdp_status s = extract_policy(h, pi, st);
+  if (s != MDP_OK) return s;
+  if (v != v0) MDP_CUDA(cudaMemcpyAsync(v, v0, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  int it = 0;
+  double r2 = 0.0;
+  s = inner_solve(h, gamma, v, inner, restart, omega, abs_tol_2norm, max_it, &it, &r2, st);
+  MDP_CUDA(cudaStreamSynchronize(st));
+  if (iters) *iters = it;
+  if (res_2norm) *res_2norm = r2;
+  if (s != MDP_OK) return s;
+  if (!(r2 < abs_tol_2norm)) return fail(MDP_NOT_CONVERGED, "policy evaluation hit max_it");
+  return MDP_OK;
+}
+
+mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* stats,
+                     void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!h || !o) return fail(MDP_ERR_INVALID_ARG, "null handle or options");
+  if (!V || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
+  if (!(o->gamma > 0.0 && o->gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
+  if (!(o->atol_pi > 0.0) || !(o->alpha > 0.0 && o->alpha < 1.0))
+    return fail(MDP_ERR_INVALID_ARG, "need atol_pi > 0 and 0 < alpha < 1");
+  if (o->max_iter_pi < 0 || o->max_iter_ksp < 0) return fail(MDP_ERR_INVALID_ARG, "negative iteration cap");
+  if (o->inner != MDP_GMRES && o->inner != MDP_RICHARDSON) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
+  if (o->inner == MDP_GMRES && (o->gmres_restart < 1 || o->gmres_restart > kMaxBasis))
+    return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t launches0 = h->launches;
+  mdp_solve_stats local;
+  std::memset(&local, 0, sizeof(local));
+  mdp_status status = MDP_OK;
+  int k = 0;
+  for (;;) {
+    // Algorithm 1 steps 2-3 (and step 4's row gather, fused): TV, pi_{k+1}, ||r(V_k)||_inf
+    if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev0, st));
+    mdp_status s = launch_bellman(h, o->gamma, V, h->TV, pi, true, st);
+    if (s != MDP_OK) return s;
+    if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev1, st));
+    local.bellman_sweeps++;
+    MDP_CUDA(cudaMemcpyAsync(h->hpin, h->resmax, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MDP_CUDA(cudaStreamSynchronize(st));
+    const double res = h->hpin[0];
+    if (o->record_timing) {
+      float ms = 0.f;
+      MDP_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      local.bellman_ms += ms;
+    }
+    local.final_residual = res;
+    if (!std::isfinite(res)) {
+      status = fail(MDP_ERR_NUMERIC, "non-finite Bellman residual");
+      break;
+    }
+    if (res <= o->atol_pi) {
+      local.converged = 1;
+      break;
+    }
+    if (k >= o->max_iter_pi) {
+      status = fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
+      break;
+    }
+    // steps 4-12: theta_0 = V_k, solve J_pi theta = g_pi to ||.||_2 < alpha * ||r(V_k)||_inf
+    int it = 0;
+    double r2 = 0.0;
+    s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->richardson_scale, o->alpha * res,
+                    o->max_iter_ksp, &it, &r2, st);
+    if (s != MDP_OK) {
+      status = s;
+      break;
+    }
+    local.inner_iters_total += it;
+    ++k;
+  }
+  MDP_CUDA(cudaStreamSynchronize(st));
+  local.outer_iters = k;
+  local.kernel_launches = h->launches - launches0;
+  local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = local;
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libmdp (include/mdp.h): argument marshalling only.
+
+The functions keep the C names and return the C status codes; every
+computation runs in the library's CUDA kernels.  Arrays may be torch tensors
+(device or host) or numpy arrays (host); streams are torch.cuda.Stream
+objects, raw cudaStream_t integers, or None for the current torch stream.
+
+The library must be built first (``paper_2507_22538_gb300.build.build()``);
+loading fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdp.so")
+
+MDP_OK = 0
+MDP_ERR_INVALID_ARG = 1
+MDP_ERR_NOT_STOCHASTIC = 2
+MDP_ERR_OOM = 3
+MDP_ERR_CUDA = 4
+MDP_NOT_CONVERGED = 5
+MDP_ERR_NUMERIC = 6
+STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_INVALID_ARG", 2: "MDP_ERR_NOT_STOCHASTIC", 3: "MDP_ERR_OOM",
+                4: "MDP_ERR_CUDA", 5: "MDP_NOT_CONVERGED", 6: "MDP_ERR_NUMERIC"}
+
+MDP_F64 = 0
+MDP_GMRES = 0
+MDP_RICHARDSON = 1
+
+
+class mdp_solve_opts(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("atol_pi", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("richardson_scale", ctypes.c_double), ("max_iter_pi", ctypes.c_int32),
+                ("max_iter_ksp", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("inner", ctypes.c_int32),
+                ("record_timing", ctypes.c_int32)]
+
+
+class mdp_solve_stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("inner_iters_total", ctypes.c_int64), ("final_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "mdp_default_opts": (None, [ctypes.POINTER(mdp_solve_opts)]),
+    "mdp_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int32, _P,
+                                  ctypes.POINTER(_P)]),
+    "mdp_destroy": (ctypes.c_int, [_P]),
+    "mdp_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int64)]),
+    "mdp_bellman": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P, _P]),
+    "mdp_policy_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
+    "mdp_policy_eval": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, ctypes.c_int, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
+    "mdp_solve": (ctypes.c_int, [_P, ctypes.POINTER(mdp_solve_opts), _P, _P, ctypes.POINTER(mdp_solve_stats), _P]),
+    "mdp_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libmdp.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmdp.so is not built ({path}); run paper_2507_22538_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class MDPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {mdp_last_error()}")
+
+
+def check(status: int, where: str, allow=(MDP_OK,)):
+    if status not in allow:
+        raise MDPError(status, where)
+    return status
+
+
+# ---- the C entry points, same names ------------------------------------------------
+
+def mdp_default_opts() -> mdp_solve_opts:
+    o = mdp_solve_opts()
+    load().mdp_default_opts(ctypes.byref(o))
+    return o
+
+
+def mdp_last_error() -> str:
+    return load().mdp_last_error().decode()
+
+
+def mdp_create(S, A, row_ptr, col, val, g, inputs_on_device: bool, stream=None):
+    """Returns (status, handle)."""
+    h = _P()
+    st = load().mdp_create(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), MDP_F64, _ptr(g),
+                           1 if inputs_on_device else 0, _stream(stream), ctypes.byref(h))
+    return st, h
+
+
+def mdp_destroy(h) -> int:
+    return load().mdp_destroy(h)
+
+
+def mdp_get_info(h):
+    S, A, nnz = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    st = load().mdp_get_info(h, ctypes.byref(S), ctypes.byref(A), ctypes.byref(nnz))
+    return st, S.value, A.value, nnz.value
+
+
+def mdp_bellman(h, gamma, V, TV, pi, residual_inf=None, stream=None) -> int:
+    return load().mdp_bellman(h, float(gamma), _ptr(V), _ptr(TV), _ptr(pi), _ptr(residual_inf), _stream(stream))
+
+
+def mdp_policy_apply(h, gamma, pi, x, y, stream=None) -> int:
+    return load().mdp_policy_apply(h, float(gamma), _ptr(pi), _ptr(x), _ptr(y), _stream(stream))
+
+
+def mdp_policy_eval(h, gamma, pi, v0, v, inner=MDP_GMRES, restart=30, omega=1.0, abs_tol_2norm=1e-10,
+                    max_it=1000, stream=None):
+    """Returns (status, iterations, residual 2-norm)."""
+    it, res = ctypes.c_int32(), ctypes.c_double()
+    st = load().mdp_policy_eval(h, float(gamma), _ptr(pi), _ptr(v0), _ptr(v), int(inner), int(restart),
+                                float(omega), float(abs_tol_2norm), int(max_it), ctypes.byref(it),
+                                ctypes.byref(res), _stream(stream))
+    return st, it.value, res.value
+
+
+def mdp_solve(h, opts: mdp_solve_opts, V, pi, stream=None):
+    """Returns (status, mdp_solve_stats)."""
+    stats = mdp_solve_stats()
+    st = load().mdp_solve(h, ctypes.byref(opts), _ptr(V), _ptr(pi), ctypes.byref(stats), _stream(stream))
+    return st, stats
+
+
+# ---- a small convenience wrapper over torch device buffers --------------------------
+
+class MDP:
+    """Owns an mdp_handle; inputs are host numpy arrays or device torch tensors."""
+
+    def __init__(self, S, A, row_ptr, col, val, g, stream=None):
+        import torch
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+        st, self.h = mdp_create(S, A, row_ptr, col, val, g, on_dev, stream)
+        check(st, "mdp_create")
+        self.S, self.A = int(S), int(A)
+
+    @classmethod
+    def from_data(cls, m, stream=None):
+        return cls(m.S, m.A, m.row_ptr, m.col, m.val, m.g, stream)
+
+    def close(self):
+        if self.h:
+            mdp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def bellman(self, gamma, V, stream=None):
+        import torch
+        TV = torch.empty_like(V)
+        pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
+        res = torch.empty(1, dtype=torch.float64, device=V.device)
+        check(mdp_bellman(self.h, gamma, V, TV, pi, res, stream), "mdp_bellman")
+        return TV, pi, res
+
+    def policy_apply(self, gamma, pi, x, stream=None):
+        import torch
+        y = torch.empty_like(x)
+        check(mdp_policy_apply(self.h, gamma, pi, x, y, stream), "mdp_policy_apply")
+        return y
+
+    def policy_eval(self, gamma, pi, v0, inner=MDP_GMRES, restart=30, omega=1.0, tol=1e-10, max_it=1000,
+                    stream=None):
+        import torch
+        v = torch.empty_like(v0)
+        st, it, res = mdp_policy_eval(self.h, gamma, pi, v0, v, inner, restart, omega, tol, max_it, stream)
+        check(st, "mdp_policy_eval", allow=(MDP_OK, MDP_NOT_CONVERGED))
+        return v, it, res, st
+
+    def solve(self, gamma, V0=None, tol=1e-8, alpha=1e-4, inner=MDP_GMRES, restart=30, omega=1.0,
+              max_outer=1000, max_inner=1000, record_timing=False, stream=None, device="cuda"):
+        import torch
+        o = mdp_default_opts()
+        o.gamma, o.atol_pi, o.alpha, o.richardson_scale = gamma, tol, alpha, omega
+        o.max_iter_pi, o.max_iter_ksp, o.gmres_restart, o.inner = max_outer, max_inner, restart, inner
+        o.record_timing = 1 if record_timing else 0
+        V = torch.zeros(self.S, dtype=torch.float64, device=device) if V0 is None else V0.clone()
+        pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
+        st, stats = mdp_solve(self.h, o, V, pi, stream)
+        check(st, "mdp_solve", allow=(MDP_OK, MDP_NOT_CONVERGED))
+        return V, pi, stats, st

@@ -1,0 +1,146 @@
+"""Parity of the fused Bellman sweep (Eq. 3-4, Algorithm 1 steps 2-3) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+from mdpgen import MDPData, banded_birth_death, pendulum_grid, random_sparse, random_value_vector
+from oracle import mdp_oracle as O
+from tests._util import check_policy, q_tolerance, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(S, A, seed, kmax=40):
+    """Rows of random lengths 1..kmax (non-uniform layout path)."""
+    rng = np.random.default_rng(seed)
+    R = S * A
+    lens = rng.integers(1, kmax + 1, size=R)
+    lens[rng.integers(0, R, size=max(1, R // 50))] = kmax * 3  # a few long rows
+    lens = np.minimum(lens, S)
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = np.empty(row_ptr[-1], dtype=np.int32)
+    val = np.empty(row_ptr[-1])
+    for r in range(R):
+        c = np.sort(rng.choice(S, size=lens[r], replace=False))
+        w = rng.random(lens[r]) + 1e-3
+        col[row_ptr[r]:row_ptr[r + 1]] = c
+        val[row_ptr[r]:row_ptr[r + 1]] = w / w.sum()
+    g = rng.random(R) * 3 - 1
+    return MDPData(S, A, row_ptr, col, val, g, 0.95, f"ragged({S},{A})")
+
+
+CASES = [
+    ("c1_shape", lambda: random_sparse(1000, 4, 8, 0.9, seed=1)),
+    ("ragged_tail_states", lambda: random_sparse(1037, 3, 5, 0.97, seed=2)),
+    ("one_action", lambda: random_sparse(777, 1, 6, 0.9, seed=3)),
+    ("many_actions", lambda: random_sparse(300, 33, 7, 0.99, seed=4)),
+    ("long_rows", lambda: random_sparse(400, 5, 100, 0.9, seed=5)),
+    ("k1_deterministic", lambda: random_sparse(2000, 7, 1, 0.8, seed=6)),
+    ("single_state", lambda: random_sparse(1, 6, 1, 0.5, seed=7)),
+    ("tiny", lambda: random_sparse(3, 2, 2, 0.5, seed=8)),
+    ("banded", lambda: banded_birth_death(5000, 20, 16, 0.999)),
+    ("pendulum", lambda: pendulum_grid(60, 50, 9, 0.9999, seed=3)),
+    ("ragged_rows", lambda: _ragged(500, 6, 9)),
+    ("ragged_rows_big_A", lambda: _ragged(90, 300, 10, kmax=12)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_bellman_parity(name, make):
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = make()
+    d = to_device(m)
+    with mdp.MDP(m.S, m.A, d["row_ptr"], d["col"], d["val"], d["g"]) as M:
+        for seed in (1, 2):
+            V = random_value_vector(m.S, seed, scale=1.0 / (1 - m.gamma))
+            TV, pi, res = M.bellman(m.gamma, torch.from_numpy(V).cuda())
+            torch.cuda.synchronize()
+            P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+            Q = O.q_values(P, m.g, m.gamma, V, m.S, m.A)
+            TVo, pio, reso = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+            tol = q_tolerance(m, V)
+            np.testing.assert_allclose(TV.cpu().numpy(), TVo, rtol=0, atol=tol)
+            assert abs(res.item() - reso) <= tol
+            check_policy(pi.cpu().numpy(), Q, tol)
+
+
+def test_host_upload_matches_device_upload():
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(700, 5, 9, 0.9, seed=12)
+    V = torch.from_numpy(random_value_vector(m.S, 3, 10.0)).cuda()
+    with mdp.MDP.from_data(m) as Mh:
+        a = Mh.bellman(m.gamma, V)
+    d = to_device(m)
+    with mdp.MDP(m.S, m.A, d["row_ptr"], d["col"], d["val"], d["g"]) as Md:
+        b = Md.bellman(m.gamma, V)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)  # same layout, same kernel: bitwise equal
+
+
+def test_exact_ties_take_lowest_action():
+    """g = 1/4 everywhere, gamma = 3/4, dyadic probabilities, V = 1: every Q is exactly 1."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(1000, 9, 6, 0.75, seed=4, quant_bits=11)
+    with mdp.MDP(m.S, m.A, m.row_ptr, m.col, m.val, np.full_like(m.g, 0.25)) as M:
+        TV, pi, res = M.bellman(0.75, torch.ones(m.S, dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        assert torch.all(TV == 1.0) and torch.all(pi == 0) and res.item() == 0.0
+
+
+def test_nan_input_gives_nan_residual():
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(500, 4, 8, 0.9, seed=1)
+    with mdp.MDP.from_data(m) as M:
+        V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+        V[123] = float("nan")
+        TV, pi, res = M.bellman(0.9, V)
+        torch.cuda.synchronize()
+        assert torch.isnan(res).item()
+
+
+def test_deterministic_repeat():
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = banded_birth_death(3000, 20, 16, 0.999)
+    with mdp.MDP.from_data(m) as M:
+        V = torch.from_numpy(random_value_vector(m.S, 5, 100.0)).cuda()
+        a = M.bellman(m.gamma, V)
+        b = M.bellman(m.gamma, V)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("bad", ["row_sum", "column", "negative", "empty_row", "nan_cost", "gamma"])
+def test_invalid_inputs_are_rejected(bad):
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(50, 3, 4, 0.9, seed=2)
+    rp, col, val, g = m.row_ptr.copy(), m.col.copy(), m.val.copy(), m.g.copy()
+    expect = mdp.MDP_ERR_NOT_STOCHASTIC
+    if bad == "row_sum":
+        val[5] *= 1.01
+    elif bad == "column":
+        col[7] = 50
+    elif bad == "negative":
+        val[3] = -val[3]
+    elif bad == "empty_row":
+        rp[1] = 0  # row 0 empty (row 1 then holds two rows' entries)
+    elif bad == "nan_cost":
+        g[4] = np.nan
+        expect = mdp.MDP_ERR_INVALID_ARG
+    if bad == "gamma":
+        with mdp.MDP(m.S, m.A, rp, col, val, g) as M:
+            V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+            TV = torch.empty_like(V)
+            pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+            assert mdp.mdp_bellman(M.h, 1.0, V, TV, pi) == mdp.MDP_ERR_INVALID_ARG
+            assert mdp.mdp_bellman(M.h, 0.9, V, V, pi) == mdp.MDP_ERR_INVALID_ARG
+        return
+    st, h = mdp.mdp_create(m.S, m.A, rp, col, val, g, False, stream=0)
+    assert st == expect, (st, mdp.mdp_last_error())
+    assert not h.value

@@ -1,0 +1,66 @@
+"""Full-size banded birth-death workload (S = 1e6, A = 20, 33-wide bands, gamma = 0.999) in the
+launch configuration the benchmark times: GMRES(30), alpha = 0.01, tol = 1e-8.
+
+The oracle cannot solve it in test time, so the checks are properties that hold at
+any size, computed by the oracle from the GPU's answer: the Bellman residual at the
+returned V is within tol (so ||V - V*||_inf <= tol / (1 - gamma), Sec. II), the
+returned policy is greedy for V wherever the action gap is resolvable, and sampled
+states of one mdp_bellman call match the oracle's per-state Bellman values.
+"""
+import numpy as np
+import pytest
+
+from mdpgen import banded_birth_death, random_value_vector, regenerate_rows
+from oracle import mdp_oracle as O
+from tests._util import check_policy, q_tolerance
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+S, A, H, GAMMA = 1_000_000, 20, 16, 0.999
+
+
+@pytest.fixture(scope="module")
+def workload():
+    return banded_birth_death(S, A, H, GAMMA)
+
+
+def test_sampled_bellman_full_size(workload):
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = workload
+    V = random_value_vector(m.S, 11, 1000.0)
+    with mdp.MDP.from_data(m) as M:
+        TV, pi, res = M.bellman(m.gamma, torch.from_numpy(V).cuda())
+        torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    states = np.unique(np.concatenate([[0, 1, 16, m.S // 2, m.S - 18, m.S - 1], rng.integers(0, m.S, 2000)]))
+    rows = (states[:, None] * A + np.arange(A)[None, :]).ravel()
+    cols, vals, g = regenerate_rows("banded_birth_death", dict(S=S, A=A, half_width=H), rows)
+    Q, tv, _ = O.bellman_states(states, cols, vals, g, m.gamma, V, A)
+    tol = q_tolerance(m, V)
+    np.testing.assert_allclose(TV.cpu().numpy()[states], tv, rtol=0, atol=tol)
+    check_policy(pi.cpu().numpy()[states], Q, tol)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    _, _, reso = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+    assert abs(res.item() - reso) <= tol
+
+
+def test_solve_full_size(workload):
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = workload
+    tol = 1e-8
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol, alpha=0.01, restart=30)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.converged, stats.as_dict()
+    Vg, pg = V.cpu().numpy(), pi.cpu().numpy()
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+    TVo = Q.min(axis=1)
+    res = float(np.max(np.abs(TVo - Vg)))
+    rtol = q_tolerance(m, Vg)
+    assert res <= tol + rtol
+    # a-posteriori bound: ||V - V*||_inf <= res / (1 - gamma) <= 1e-8 ||V*||_inf
+    assert (tol + rtol) / (1 - m.gamma) <= 1e-8 * (float(np.max(np.abs(Vg))) - (tol + rtol) / (1 - m.gamma))
+    check_policy(pg, Q, rtol)

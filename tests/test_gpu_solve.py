@@ -1,0 +1,111 @@
+"""End-to-end parity of mdp_solve (Algorithm 1) with the oracle's optimal V* and pi*."""
+import numpy as np
+import pytest
+
+from mdpgen import banded_birth_death, maze, pendulum_grid, random_sparse
+from oracle import mdp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _args(m):
+    return (m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma)
+
+
+def _check_solution(m, V, pi, Vs, tol_outer):
+    """||V - V*||_inf <= 1e-8 ||V*||_inf, and pi equals the oracle's greedy policy
+    wherever the action gap at V* exceeds both 1e-9 and the certified band."""
+    err = float(np.max(np.abs(V - Vs)))
+    assert err <= 1e-8 * float(np.max(np.abs(Vs))), err
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vs, m.S, m.A)
+    gap = O.action_gaps(Q)
+    band = 2 * m.gamma * tol_outer / (1 - m.gamma) + 1e-9 * float(np.max(np.abs(Vs)))
+    sure = gap > max(1e-9, band)
+    assert np.array_equal(pi[sure], Q.argmin(axis=1)[sure])
+    literal = gap > 1e-9
+    return int(np.sum(pi[literal] != Q.argmin(axis=1)[literal]))
+
+
+SOLVE_CASES = [
+    ("c1_random_s1000_a4_k8", lambda: random_sparse(1000, 4, 8, 0.9, seed=1), 1e-3, 1e-10),
+    ("banded_s5000_a20_k33", lambda: banded_birth_death(5000, 20, 16, 0.999), 0.01, 1e-8),
+    ("pendulum_60x60_a9", lambda: pendulum_grid(60, 60, 9, 0.9999, seed=3), 1e-3, 1e-8),
+    ("random_s3000_a32_k32", lambda: random_sparse(3000, 32, 32, 0.99, seed=4, conc=0.5, quant_bits=11), 1e-4, 1e-8),
+    ("maze_40x40", lambda: maze(40, 40, 0.2, seed=7, gamma=0.99)[0], 1e-4, 1e-8),
+]
+
+
+@pytest.mark.parametrize("inner", ["gmres", "richardson"])
+@pytest.mark.parametrize("name,make,alpha,tol", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_solve_matches_oracle(name, make, alpha, tol, inner):
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = make()
+    if inner == "richardson" and m.gamma > 0.999:
+        pytest.skip("Richardson at gamma = 0.9999 needs ~1e5 sweeps; covered by GMRES")
+    Vs, ps, _ = O.policy_iteration(*_args(m))
+    # parity tolerance (reading C10): certify 1e-8 relative through the a-posteriori bound
+    tol_p = min(tol, 0.5e-8 * (1 - m.gamma) * float(np.max(np.abs(Vs))))
+    code = mdp.MDP_GMRES if inner == "gmres" else mdp.MDP_RICHARDSON
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol_p, alpha=alpha, inner=code, max_inner=1000 if inner == "gmres" else 50,
+                                   max_outer=100000)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.converged == 1, stats.as_dict()
+    assert stats.final_residual <= tol_p
+    _check_solution(m, V.cpu().numpy(), pi.cpu().numpy(), Vs, tol_p)
+
+
+def test_solve_outer_trace_matches_oracle_ipi():
+    """Same Algorithm 1 run on both sides: same number of evaluations, same final policy."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(1000, 4, 8, 0.9, seed=1)
+    ref = O.ipi(*_args(m), tol=1e-10, alpha=1e-3, inner="gmres", restart=30)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-10, alpha=1e-3)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK
+    assert stats.outer_iters == ref.outer_iters
+    assert abs(stats.inner_iters_total - sum(ref.inner_iters)) <= ref.outer_iters
+    np.testing.assert_allclose(V.cpu().numpy(), ref.V, rtol=0, atol=1e-9)
+    assert np.array_equal(pi.cpu().numpy(), ref.pi)
+
+
+def test_value_iteration_configuration():
+    """Richardson with one step per evaluation is VI (Table 2): same sweep count as the oracle's VI."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(800, 5, 6, 0.9, seed=3)
+    ref = O.value_iteration(*_args(m), tol=1e-9)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-9, alpha=0.5, inner=mdp.MDP_RICHARDSON, max_inner=1)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.outer_iters == ref.outer_iters
+    np.testing.assert_allclose(V.cpu().numpy(), ref.V, rtol=0, atol=1e-11)
+
+
+def test_outer_cap_returns_not_converged_with_iterate():
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(500, 4, 8, 0.99, seed=2)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-12, alpha=0.9, inner=mdp.MDP_RICHARDSON, max_inner=1,
+                                   max_outer=3)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_NOT_CONVERGED and stats.outer_iters == 3 and not stats.converged
+    ref = O.value_iteration(*_args(m), tol=0.0, max_iter=3)
+    np.testing.assert_allclose(V.cpu().numpy(), ref.V, rtol=0, atol=1e-12)
+
+
+def test_warm_start_resumes():
+    """V_0 is an input (Algorithm 1): restarting from a converged V takes zero evaluations."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(1000, 4, 8, 0.9, seed=1)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-10, alpha=1e-3)
+        V2, pi2, stats2, st2 = M.solve(m.gamma, V0=V, tol=1e-10, alpha=1e-3)
+        torch.cuda.synchronize()
+    assert stats2.outer_iters == 0 and torch.equal(V, V2) and torch.equal(pi, pi2)
