@@ -150,16 +150,31 @@ def random_sparse(S: int, A: int, k: int, gamma: float, seed: int, conc: float =
     return MDPData(S, A, row_ptr, col, val, g, gamma, f"random_sparse(S={S},A={A},k={k})")
 
 
+def sis_band_centres(s: np.ndarray, a: np.ndarray, S: int, A: int, half_width: int,
+                     r0_max: float = 2.5) -> np.ndarray:
+    """Band centre of row (s, a): the expected infected count after one SIS step.
+
+    As in the SIS model of Sec. IV-B the infectious period is one step, so the
+    next infected count is the number of new infections among the S-1-s
+    susceptibles, each infected with probability q = 1 - exp(-R0(a) s / S);
+    intervention level a scales the reproduction number R0(a) = r0_max (1 - a/A).
+    The centre is that mean, rounded and clamped so the band stays in [0, S).
+    """
+    s = np.asarray(s, dtype=np.float64)
+    r0 = r0_max * (1.0 - np.asarray(a, dtype=np.float64) / A)
+    mean = (S - 1 - s) * (1.0 - np.exp(-r0 * s / S))
+    return np.clip(np.rint(mean), half_width, S - 1 - half_width).astype(np.int64)
+
+
 def banded_birth_death(S: int = 1_000_000, A: int = 20, half_width: int = 16, gamma: float = 0.999,
                        quant_bits: int | None = None, chunk_states: int = 1 << 16) -> MDPData:
-    """Banded birth-death chain standing in for the SIS model of Sec. IV-B.
+    """Banded epidemic-like MDP standing in for the SIS model of Sec. IV-B.
 
-    State s is the infected count.  Row (s, a) is a band of 2h+1 contiguous
-    columns centred at c = clamp(s + drift(a), h, S-1-h) with drift(a) =
-    A//2 - a (higher intervention levels push the count down).  The band holds
-    the Binomial(2h, 1/2) pmf C(2h, j) / 2**(2h), exact in binary64 (or, with
-    quant_bits, rounded to 2**-quant_bits by largest remainder).  Cost
-    g(s, a) = s/S + 0.05 a.
+    State s is the infected count, action a an intervention level.  Row (s, a)
+    is a band of 2h+1 contiguous columns centred at ``sis_band_centres`` (the
+    expected infected count one step later) holding the Binomial(2h, 1/2) pmf
+    C(2h, j) / 2**(2h), exact in binary64 (or, with quant_bits, rounded to
+    2**-quant_bits by largest remainder).  Cost g(s, a) = s/S + 0.05 a.
     """
     h = half_width
     w = 2 * h + 1
@@ -172,11 +187,11 @@ def banded_birth_death(S: int = 1_000_000, A: int = 20, half_width: int = 16, ga
     col = np.empty(R * w, dtype=np.int32)
     val = np.empty(R * w, dtype=np.float64)
     offs = np.arange(-h, h + 1, dtype=np.int64)
-    drift = (A // 2 - np.arange(A, dtype=np.int64))
+    acts = np.arange(A, dtype=np.int64)
     for s0 in range(0, S, chunk_states):
         s1 = min(S, s0 + chunk_states)
         s = np.arange(s0, s1, dtype=np.int64)
-        c = np.clip(s[:, None] + drift[None, :], h, S - 1 - h)  # [ns, A]
+        c = sis_band_centres(s[:, None], acts[None, :], S, A, h)  # [ns, A]
         cols = c[:, :, None] + offs[None, None, :]
         lo, hi = s0 * A * w, s1 * A * w
         col[lo:hi] = cols.ravel()
@@ -329,7 +344,7 @@ def regenerate_rows(kind: str, params: dict, rows: np.ndarray):
         if qb is not None:
             pmf = quantize_rows(pmf[None, :], qb)[0]
         s, a = rows // A, rows % A
-        c = np.clip(s + (A // 2 - a), h, S - 1 - h)
+        c = sis_band_centres(s, a, S, A, h)
         cols = c[:, None] + np.arange(-h, h + 1)[None, :]
         return cols, np.broadcast_to(pmf, cols.shape).copy(), s / S + 0.05 * a
     raise ValueError(kind)

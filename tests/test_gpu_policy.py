@@ -85,10 +85,13 @@ def test_policy_eval_parity(name, make, inner):
         assert abs(it - ref.iters) <= 1, (it, ref.iters)
         np.testing.assert_allclose(v, ref.x, rtol=0, atol=2 * (tol + 64 * EPS * bn) / (1 - m.gamma))
     else:
-        # Richardson at gamma close to 1 may hit the cap on both sides: same count, same iterate
+        # the cap was hit on both sides (GMRES(30) stagnates on some random policies at
+        # gamma near 1; 200 Richardson steps are too few there)
         assert st == mdp.MDP_NOT_CONVERGED and it == maxit and ref.iters == maxit
-        scale = max(1.0, float(np.max(np.abs(ref.x))))
-        np.testing.assert_allclose(v, ref.x, rtol=0, atol=1e-9 * scale)
+        assert abs(res - true_res) <= 1e-6 * max(true_res, tol)
+        if inner == "richardson":  # same recurrence on both sides: same iterate
+            scale = max(1.0, float(np.max(np.abs(ref.x))))
+            np.testing.assert_allclose(v, ref.x, rtol=0, atol=1e-9 * scale)
 
 
 def test_richardson_one_step_is_policy_operator():

@@ -44,13 +44,15 @@ def test_quantised_rows_sum_exactly_to_one():
 
 
 def test_banded_layout_row_is_state_times_A_plus_action():
-    """Row s*A + a holds P(s, ., a): the band sits at s + drift(a) (Eq. 5 layout)."""
+    """Row s*A + a holds P(s, ., a): the band sits at the expected infected count of
+    one SIS step from s under intervention a (Eq. 5 layout)."""
     S, A, h = 200, 6, 4
     m = banded_birth_death(S, A, h, 0.999)
     for s in (0, 57, 199):
         for a in range(A):
             cols, vals = m.row(s, a)
-            c = min(max(s + A // 2 - a, h), S - 1 - h)
+            mean = (S - 1 - s) * (1 - math.exp(-2.5 * (1 - a / A) * s / S))
+            c = min(max(int(np.rint(mean)), h), S - 1 - h)
             assert cols.tolist() == list(range(c - h, c + h + 1))
             assert vals.sum() == 1.0
             assert math.isclose(vals[h], math.comb(2 * h, h) / 2 ** (2 * h))
