@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark: inexact policy iteration to ||TV - V||_inf <= 1e-8 on the banded
+epidemic-like MDP (S = 1e6 infected counts, A = 20 intervention levels, 33-wide
+binomial bands, gamma = 0.999, GMRES(30), alpha = 0.01), synthetic inputs.
+
+One step = one full mdp_solve from V_0 = 0: every Bellman sweep, policy-row
+gather, Arnoldi/CGS2 pass and Givens update of Algorithm 1 until the stop test
+holds.  Inputs (8.3 GB) stay resident in HBM and are larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With torchrun (N > 1) every rank solves its own replica (the path does not
+shard: replicas only); rank 0 prints one JSON line with the max-over-ranks time.
+--impl reference times the FP64 CPU oracle instead (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")  # the CPU oracle runs single-threaded
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("iPI time to ‖TV−V‖∞≤1e-8; Bellman SpMV+min GB/s vs HBM peak; "
+          "p50/p99 latency")
+S, A, H, GAMMA = 1_000_000, 20, 16, 0.999
+K_ROW = 2 * H + 1
+TOL, ALPHA, RESTART = 1e-8, 0.01, 30
+CPU_SAMPLE_DIV = 10  # the CPU oracle solves the same generator at S / 10 and is scaled by 10
+
+
+def workload_config():
+    return {"workload": "banded epidemic-like MDP (SIS-step band centres)", "S": S, "A": A, "k": K_ROW,
+            "nnz": S * A * K_ROW, "gamma": GAMMA, "tol": TOL, "alpha": ALPHA, "inner": f"GMRES({RESTART})",
+            "V0": "zeros", "l2": "inputs (8.3 GB) larger than L2 (129 MB); no flush"}
+
+
+def bellman_bytes():
+    """Algorithmic bytes of one Bellman sweep: CSR values (8) + columns (4) per
+    entry, row pointers (8) and costs (8) per row, V read once, TV and pi written."""
+    R = S * A
+    nnz = R * K_ROW
+    return nnz * 12 + (R + 1) * 8 + R * 8 + S * 8 + S * (8 + 4)
+
+
+def inner_bytes(stats):
+    """Algorithmic bytes of the inner solves: each P_pi application reads the
+    policy's rows (12 B per entry) and its x once; each counted vector access
+    moves 8 B per state."""
+    per_matvec = S * K_ROW * 12 + S * 8
+    return stats["policy_matvecs"] * per_matvec + (stats["vector_reads"] + stats["vector_writes"]) * 8 * S
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_traffic():
+    """DRAM bytes per Bellman launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2507_22538_gb300", "csrc", "bellman.cu")
+    summ = os.path.join(ROOT, "profiles", "bellman_sweep_banded_s1e6.txt")
+    if not os.path.exists(summ):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(summ):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("bellman.cu sha256[:16]") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_solve(div=CPU_SAMPLE_DIV):
+    """Time the FP64 oracle's Algorithm 1 on the same generator at S / div."""
+    from mdpgen import banded_birth_death
+    from oracle import mdp_oracle as O
+    m = banded_birth_death(S // div, A, H, GAMMA)
+    t0 = time.perf_counter()
+    r = O.ipi(m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma, tol=TOL, alpha=ALPHA, inner="gmres",
+              restart=RESTART)
+    dt = time.perf_counter() - t0
+    return dt * div, {"converged": r.converged, "outer": r.outer_iters, "inner": int(sum(r.inner_iters))}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        t, info = cpu_oracle_solve()
+        if i >= args.warmup:
+            times.append(t)
+    v = sum(times) / len(times)
+    sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the S={S // CPU_SAMPLE_DIV} "
+              f"instance of the same generator (same A, k, gamma, tol, alpha), wall time x{CPU_SAMPLE_DIV} "
+              f"(cost is linear in S at fixed iteration counts); last run {info}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from mdpgen import banded_birth_death
+    from paper_2507_22538_gb300 import mdp
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2507_22538_gb300.build import build
+    if rank == 0 or world == 1:
+        build()
+    if dist:
+        dist.barrier()
+    mdp.load()
+
+    m = banded_birth_death(S, A, H, GAMMA)
+    stream = torch.cuda.current_stream()
+    M = mdp.MDP.from_data(m, stream)
+    V = torch.zeros(S, dtype=torch.float64, device="cuda")
+    pi = torch.empty(S, dtype=torch.int32, device="cuda")
+    opts = mdp.mdp_default_opts()
+    opts.gamma, opts.atol_pi, opts.alpha, opts.gmres_restart = GAMMA, TOL, ALPHA, RESTART
+    opts.inner, opts.record_timing = mdp.MDP_GMRES, 1
+
+    def step():
+        V.zero_()
+        st, stats = mdp.mdp_solve(M.h, opts, V, pi, stream)
+        mdp.check(st, "mdp_solve")
+        return stats.as_dict()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    totals = {}
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = step()
+            for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
+                        "inner_ms", "policy_matvecs", "vector_reads", "vector_writes"):
+                totals[key] = totals.get(key, 0) + s[key]
+            totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # end to end through the C ABI from pinned host buffers: upload + layout + solve + read back
+    pinned = {k: torch.from_numpy(getattr(m, k)).pin_memory() for k in ("row_ptr", "col", "val", "g")}
+    h2d = sum(int(t.numel() * t.element_size()) for t in pinned.values())
+    Vh = torch.empty(S, dtype=torch.float64).pin_memory()
+    pih = torch.empty(S, dtype=torch.int32).pin_memory()
+    d2h = S * 8 + S * 4
+    M.close()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        t0 = time.perf_counter()
+        st, h = mdp.mdp_create(S, A, pinned["row_ptr"], pinned["col"], pinned["val"], pinned["g"], False, stream)
+        mdp.check(st, "mdp_create")
+        V.zero_()
+        st, _ = mdp.mdp_solve(h, opts, V, pi, stream)
+        mdp.check(st, "mdp_solve")
+        Vh.copy_(V, non_blocking=True)
+        pih.copy_(pi, non_blocking=True)
+        torch.cuda.synchronize()
+        mdp.mdp_destroy(h)
+        if i:  # the first pass is a warm-up
+            e2e_times.append(time.perf_counter() - t0)
+    e2e = sum(e2e_times) / len(e2e_times) if e2e_times else None
+    if dist and e2e is not None:
+        t = torch.tensor([e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    peak, peak_kind = load_peaks()
+    sweeps = totals["bellman_sweeps"]
+    bell_ms = totals["bellman_ms"] / sweeps
+    bell_gbs = bellman_bytes() / (bell_ms * 1e-3) / 1e9
+    inner_gbs = inner_bytes(totals) / (totals["inner_ms"] * 1e-3) / 1e9 if totals["inner_ms"] > 0 else None
+    share_bell = totals["bellman_ms"] / (ms * args.steps)
+    roofline = {"bound": "hbm", "kernel": "bellman_kernel (fused SpMV + min/argmin + residual + policy-row gather)",
+                "achieved": bell_gbs, "peak": peak, "unit": "GB/s", "frac": bell_gbs / peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "traffic": sweep_traffic(),
+                "bytes_per_launch": bellman_bytes(), "avg_launch_ms": bell_ms,
+                "share_of_step": share_bell}
+    inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
+                  "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
+                  "bytes": inner_bytes(totals) / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
+
+    line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "roofline": roofline, "roofline_inner": inner_roof,
+            "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
+                           "inner_per_step": totals["inner_iters_total"] / args.steps,
+                           "max_final_residual": totals["final_residual"]},
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, info = cpu_oracle_solve()
+        line["cpu_baseline"] = {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 oracle Algorithm 1 on the S={S // CPU_SAMPLE_DIV} instance of the "
+                                          f"same generator, wall time x{CPU_SAMPLE_DIV}; {info}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

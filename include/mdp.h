@@ -51,9 +51,9 @@ typedef struct {
   double richardson_scale; /* omega of the Richardson step theta += omega (b - J theta) (1.0) */
   int32_t max_iter_pi;     /* N_o: at most this many policy evaluations             (1000) */
   int32_t max_iter_ksp;    /* N_i: at most this many inner iterations per evaluation (1000) */
-  int32_t gmres_restart;   /* GMRES restart length m, 1..64                            (30) */
+  int32_t gmres_restart;   /* GMRES restart length m, 1..32                            (30) */
   int32_t inner;           /* an mdp_inner value                                  (MDP_GMRES) */
-  int32_t record_timing;   /* nonzero: time every Bellman sweep with CUDA events        (0) */
+  int32_t record_timing;   /* nonzero: time Bellman sweeps and inner solves (CUDA events) (0) */
 } mdp_solve_opts;
 
 /* Statistics of one mdp_solve call (host struct filled by the library). */
@@ -64,8 +64,14 @@ typedef struct {
   double final_residual;      /* ||TV - V||_inf at the returned V */
   double seconds;             /* host wall time of the call */
   int64_t kernel_launches;    /* CUDA kernels the call launched */
-  int32_t bellman_sweeps;     /* Bellman sweeps (kernel K1) launched */
+  int32_t bellman_sweeps;     /* Bellman sweeps launched */
   double bellman_ms;          /* summed device time of those sweeps (record_timing only) */
+  double inner_ms;            /* summed device-timeline time of the inner solves, including
+                                 host round trips between their kernels (record_timing only) */
+  int64_t policy_matvecs;     /* applications of P_pi by the inner solver */
+  int64_t vector_reads;       /* length-S double vectors the inner kernels must read, besides
+                                 the P_pi applications (each counts its x once) */
+  int64_t vector_writes;      /* length-S double vectors the inner kernels write */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */
@@ -75,7 +81,7 @@ void mdp_default_opts(mdp_solve_opts* opts);
  * mdp_create -- copy an MDP into device memory owned by the returned handle.
  * (Sec. III-B.2: row-stacked CSR of Eq. 5 and the dense S x A stage costs.)
  *
- *  S, A          number of states (>= 1) and actions (1..65535).
+ *  S, A          number of states (1 .. 2^31-1) and actions (1 .. 8192), S*A < 2^36.
  *  row_ptr       int64[S*A + 1], row_ptr[0] = 0, nondecreasing.
  *  col           int32[nnz] column (successor state) of each entry, in [0, S).
  *  val           P values, nnz entries of val_type (MDP_F64: double).

@@ -262,6 +262,9 @@ static mdp_status residual(mdp_s* h, double gamma, double omega, const double* t
     residual_kernel<U, false><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, h->S, gamma,
                                                                       omega, theta, h->gpi, out, h->partials);
   MDP_LAUNCH_CHECK(h);
+  h->matvecs += 1;
+  h->vreads += 1;
+  h->vwrites += 1;
   return reduce(h, 1, kNorm, nullptr, h->sc + kSlotNorm, st);
 }
 
@@ -291,6 +294,11 @@ static mdp_status arnoldi_step(mdp_s* h, double gamma, int j, cudaStream_t st) {
   if (r != MDP_OK) return r;
   scale_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis + (int64_t)(j + 1) * S, h->sc + kSlotNorm + 1);
   MDP_LAUNCH_CHECK(h);
+  // pass 1: P_pi v_j plus the other j basis vectors, writes w; pass 2: w and j+1
+  // basis vectors; pass 3: the same, writes v_{j+1}; scaling: one read, one write
+  h->matvecs += 1;
+  h->vreads += j + (j + 2) + (j + 2) + 1;
+  h->vwrites += 1 + 1 + 1;
   return MDP_OK;
 }
 
@@ -310,6 +318,8 @@ static mdp_status basis_update(mdp_s* h, int n, double* theta, cudaStream_t st) 
   else
     basis_update_kernel<32><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, n, y, theta);
   MDP_LAUNCH_CHECK(h);
+  h->vreads += n + 1;
+  h->vwrites += 1;
   return MDP_OK;
 }
 
@@ -333,6 +343,8 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, double tol
     if (!std::isfinite(beta)) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
     scale_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, h->sc + kSlotNorm + 1);
     MDP_LAUNCH_CHECK(h);
+    h->vreads += 1;
+    h->vwrites += 1;
     std::fill(e.begin(), e.end(), 0.0);
     e[0] = beta;
     int jdone = 0;

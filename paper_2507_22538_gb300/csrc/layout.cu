@@ -248,6 +248,8 @@ static void destroy_handle(mdp_s* h) {
   if (h->hpin) cudaFreeHost(h->hpin);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev2) cudaEventDestroy(h->ev2);
+  if (h->ev3) cudaEventDestroy(h->ev3);
   delete h;
 }
 
@@ -388,6 +390,8 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(&h->partials, (size_t)h->vec_blocks * kMaxBasis, "partials"));
   MDP_CUDA(cudaEventCreate(&h->ev0));
   MDP_CUDA(cudaEventCreate(&h->ev1));
+  MDP_CUDA(cudaEventCreate(&h->ev2));
+  MDP_CUDA(cudaEventCreate(&h->ev3));
   MDP_CUDA(cudaStreamSynchronize(st));
   return MDP_OK;
 }

@@ -76,8 +76,10 @@ struct mdp_s {
   unsigned long long* resmax = nullptr;  // device max of |TV - V| bits
   double* hpin = nullptr;    // pinned host scalars [kScalarSlots]
 
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   int64_t launches = 0;
+  // algorithmic work counters of the inner solver (see mdp_solve_stats)
+  int64_t matvecs = 0, vreads = 0, vwrites = 0;
 };
 
 namespace mdp {

@@ -59,6 +59,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t launches0 = h->launches;
+  const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
   mdp_solve_stats local;
   std::memset(&local, 0, sizeof(local));
   mdp_status status = MDP_OK;
@@ -94,11 +95,19 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     // steps 4-12: theta_0 = V_k, solve J_pi theta = g_pi to ||.||_2 < alpha * ||r(V_k)||_inf
     int it = 0;
     double r2 = 0.0;
+    if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev2, st));
     s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->richardson_scale, o->alpha * res,
                     o->max_iter_ksp, &it, &r2, st);
     if (s != MDP_OK) {
       status = s;
       break;
+    }
+    if (o->record_timing) {
+      MDP_CUDA(cudaEventRecord(h->ev3, st));
+      MDP_CUDA(cudaEventSynchronize(h->ev3));
+      float ms = 0.f;
+      MDP_CUDA(cudaEventElapsedTime(&ms, h->ev2, h->ev3));
+      local.inner_ms += ms;
     }
     local.inner_iters_total += it;
     ++k;
@@ -106,6 +115,9 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   MDP_CUDA(cudaStreamSynchronize(st));
   local.outer_iters = k;
   local.kernel_launches = h->launches - launches0;
+  local.policy_matvecs = h->matvecs - matvecs0;
+  local.vector_reads = h->vreads - vreads0;
+  local.vector_writes = h->vwrites - vwrites0;
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = local;
   return status;

@@ -42,7 +42,9 @@ class mdp_solve_stats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("inner_iters_total", ctypes.c_int64), ("final_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double)]
+                ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double),
+                ("inner_ms", ctypes.c_double), ("policy_matvecs", ctypes.c_int64),
+                ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -88,8 +88,9 @@ def test_policy_eval_parity(name, make, inner):
         # the cap was hit on both sides (GMRES(30) stagnates on some random policies at
         # gamma near 1; 200 Richardson steps are too few there)
         assert st == mdp.MDP_NOT_CONVERGED and it == maxit and ref.iters == maxit
-        assert abs(res - true_res) <= 1e-6 * max(true_res, tol)
-        if inner == "richardson":  # same recurrence on both sides: same iterate
+        if inner == "gmres":  # GMRES reports the true residual of the returned iterate
+            assert abs(res - true_res) <= 1e-6 * max(true_res, tol)
+        else:  # same recurrence on both sides: same iterate
             scale = max(1.0, float(np.max(np.abs(ref.x))))
             np.testing.assert_allclose(v, ref.x, rtol=0, atol=1e-9 * scale)
 
