@@ -161,6 +161,30 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
 mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_t* pi,
                      mdp_solve_stats* stats, void* stream);
 
+/*
+ * mdp_bellman_csr_noalloc -- the Bellman application of mdp_bellman (TV, greedy pi,
+ * ||TV - V||_inf) computed straight from the caller's row-stacked CSR arrays,
+ * with no handle and no device allocation.  The paper has no counterpart: it is
+ * for callers that cannot allocate device memory at the point of the call, such
+ * as code running under CUDA stream capture or inside an application that owns
+ * every device allocation through its own pool.
+ *
+ *  S, A          at most 2,097,152 states and 128 actions (else MDP_ERR_INVALID_ARG).
+ *  row_ptr, col, val, g   device arrays laid out as for mdp_create; the caller
+ *                guarantees they are valid (this call does not check them).
+ *  V, TV, pi, residual_inf   as for mdp_bellman (residual_inf may be NULL).
+ * Scratch: a fixed 512 KB array in the library's device memory, present on every
+ * GPU that loads the library until the process exits.  Its device address is
+ * looked up on the first call made on each device (that first call must not be
+ * inside a stream capture); later calls only launch work.  All calls share the
+ * array, so calls that may overlap on the GPU (different streams, no ordering
+ * between them) race and must not be issued.  Stream-ordered: returns without
+ * waiting for the kernel.
+ */
+mdp_status mdp_bellman_csr_noalloc(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col,
+                                   const double* val, const double* g, double gamma, const double* V,
+                                   double* TV, int32_t* pi, double* residual_inf, void* stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* mdp_last_error(void);
 

@@ -67,6 +67,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
     "mdp_solve": (ctypes.c_int, [_P, ctypes.POINTER(mdp_solve_opts), _P, _P, ctypes.POINTER(mdp_solve_stats), _P]),
     "mdp_last_error": (ctypes.c_char_p, []),
+    "mdp_bellman_csr_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
+                                               _P, _P, _P, _P, _P]),
 }
 
 
@@ -171,6 +173,13 @@ def mdp_solve(h, opts: mdp_solve_opts, V, pi, stream=None):
     stats = mdp_solve_stats()
     st = load().mdp_solve(h, ctypes.byref(opts), _ptr(V), _ptr(pi), ctypes.byref(stats), _stream(stream))
     return st, stats
+
+
+def mdp_bellman_csr_noalloc(S, A, row_ptr, col, val, g, gamma, V, TV, pi, residual_inf=None, stream=None) -> int:
+    """Bellman application from device CSR arrays without a handle or any device allocation."""
+    return load().mdp_bellman_csr_noalloc(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(g),
+                                          float(gamma), _ptr(V), _ptr(TV), _ptr(pi), _ptr(residual_inf),
+                                          _stream(stream))
 
 
 # ---- a small convenience wrapper over torch device buffers --------------------------
