@@ -183,6 +183,37 @@ def run_reference(args):
     return 0
 
 
+def run_bellman_only(args):
+    """Time mdp_bellman alone on the banded workload (any size), one JSON line."""
+    import torch
+
+    from mdpgen import banded_birth_death, random_value_vector
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.build import build
+    build()
+    m = banded_birth_death(args.states, A, H, GAMMA)
+    stream = torch.cuda.current_stream()
+    with mdp.MDP.from_data(m, stream) as M:
+        V = torch.from_numpy(random_value_vector(m.S, 1, 1000.0)).cuda()
+        TV = torch.empty_like(V)
+        pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            mdp.check(mdp.mdp_bellman(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.bellman_only):
+            mdp.check(mdp.mdp_bellman(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman")
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.bellman_only
+    R = m.S * A
+    nbytes = R * K_ROW * 12 + (R + 1) * 8 + R * 8 + m.S * 8 + m.S * 12
+    peak, _ = load_peaks()
+    print(json.dumps({"mode": "bellman_only", "S": m.S, "ms_per_sweep": ms, "bytes": nbytes,
+                      "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,9 +222,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
+                    help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
+    ap.add_argument("--states", type=int, default=S, help="with --bellman-only: number of states")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.bellman_only:
+        return run_bellman_only(args)
 
     import numpy as np
     import torch

@@ -43,6 +43,12 @@ typedef enum { MDP_F64 = 0 } mdp_dtype; /* storage type of the P values passed t
 
 typedef enum { MDP_GMRES = 0, MDP_RICHARDSON = 1 } mdp_inner;
 
+/* Gram-Schmidt refinement inside GMRES (the choices of PETSc's KSPGMRES, whose
+   default madupite inherits, Sec. III-B.3): classical Gram-Schmidt with no second
+   pass, a second pass when the projected norm drops below 1/sqrt(2) of the
+   original (Daniel-Gragg-Kaufman-Stewart test), or always two passes. */
+typedef enum { MDP_REFINE_NEVER = 0, MDP_REFINE_IFNEEDED = 1, MDP_REFINE_ALWAYS = 2 } mdp_refine;
+
 /* Options of Algorithm 1 with the defaults of Table 1 (set by mdp_default_opts). */
 typedef struct {
   double gamma;            /* discount factor, 0 < gamma < 1 (no default; must be set) */
@@ -54,6 +60,7 @@ typedef struct {
   int32_t gmres_restart;   /* GMRES restart length m, 1..32                            (30) */
   int32_t inner;           /* an mdp_inner value                                  (MDP_GMRES) */
   int32_t record_timing;   /* nonzero: time Bellman sweeps and inner solves (CUDA events) (0) */
+  int32_t gmres_refine;    /* an mdp_refine value                          (MDP_REFINE_NEVER) */
 } mdp_solve_opts;
 
 /* Statistics of one mdp_solve call (host struct filled by the library). */
@@ -137,7 +144,8 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
  *  v0, v         double[S] start vector and result (may alias).
  *  inner         MDP_GMRES (restart = `restart`) or MDP_RICHARDSON (step scale `omega`).
  *  abs_tol_2norm stop when ||g_pi - J_pi v||_2 < abs_tol_2norm (Sec. III-B.3).
- *  max_it        at most this many iterations (a GMRES Arnoldi step or a Richardson step).
+ *  max_it        at most this many iterations (a GMRES Arnoldi step or a Richardson step);
+ *                GMRES uses classical Gram-Schmidt without refinement (MDP_REFINE_NEVER).
  *  iters, res_2norm  host outputs (may be NULL): iterations done and the last
  *                computed residual 2-norm.
  * Blocks until the solve completes.  Returns MDP_NOT_CONVERGED (with v filled)

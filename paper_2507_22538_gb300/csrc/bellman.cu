@@ -1,8 +1,7 @@
 // Fused Bellman sweep (Eq. 3-4, Algorithm 1 steps 2-3, Sec. III-B.3):
 //   Q(s,a) = g(s,a) + gamma * sum_j P[s*A+a, j] V[col_j]   (the S*A-long PV, scaled, plus g)
 //   TV(s) = min_a Q(s,a), pi(s) = lowest minimising a, residual = max_s |TV(s) - V(s)|
-// and, optionally, the policy's rows copied into the per-state layout used by
-// the inner solver (Algorithm 1 step 4) while they are still in L2.
+// in one pass over the stacked matrix; Q is never written to memory.
 //
 // Layout: rows of the stacked matrix in 32-row slices, column-major inside a
 // slice, so lane l of a warp streams row 32q+l with fully coalesced loads of
@@ -16,14 +15,13 @@ __device__ __forceinline__ double nan_max(double a, double b) { return (b > a ||
 
 constexpr int kBellThreads = 256;
 
-template <bool UNIFORM, bool FUSE>
+template <bool UNIFORM>
 __global__ void __launch_bounds__(kBellThreads) bellman_kernel(
     const double* __restrict__ sval, const int32_t* __restrict__ scol, const int64_t* __restrict__ off,
     const int32_t* __restrict__ len, int k, const double* __restrict__ g, const double* __restrict__ V, int64_t S,
-    int A, int TS, double gamma, double* __restrict__ TV, int32_t* __restrict__ pi, double* __restrict__ gpi,
-    unsigned long long* __restrict__ resmax, double* __restrict__ pval, int32_t* __restrict__ pcol,
-    const int64_t* __restrict__ poff, int32_t* __restrict__ plen) {
-  extern __shared__ double q_s[];
+    int A, int TS, double gamma, double* __restrict__ TV, int32_t* __restrict__ pi,
+    unsigned long long* __restrict__ resmax) {
+  extern __shared__ double q_s[];  // TS * A values of Q
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   double dmax = 0.0;
@@ -77,20 +75,6 @@ __global__ void __launch_bounds__(kBellThreads) bellman_kernel(
       TV[s] = best;
       pi[s] = ba;
       dmax = nan_max(dmax, fabs(best - V[s]));
-      if (FUSE) {
-        const int64_t r = s * A + ba;
-        gpi[s] = g[r];
-        const int n = UNIFORM ? k : len[r];
-        const int64_t q = r / kSlice;
-        const int64_t base = (UNIFORM ? q * kSlice * (int64_t)k : off[q]) + (r % kSlice);
-        const int64_t ps = s / kSlice;
-        const int64_t pbase = (UNIFORM ? ps * kSlice * (int64_t)k : poff[ps]) + (s % kSlice);
-        for (int j = 0; j < n; ++j) {
-          pval[pbase + (int64_t)j * kSlice] = sval[base + (int64_t)j * kSlice];
-          pcol[pbase + (int64_t)j * kSlice] = scol[base + (int64_t)j * kSlice];
-        }
-        if (!UNIFORM) plen[s] = n;
-      }
     }
     __syncthreads();
   }
@@ -106,24 +90,19 @@ __global__ void __launch_bounds__(kBellThreads) bellman_kernel(
   }
 }
 
-template <bool U, bool F>
-static cudaError_t set_smem(size_t bytes) {
-  return cudaFuncSetAttribute(bellman_kernel<U, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+static size_t bellman_smem(const mdp_s* h) { return (size_t)h->bell_tile_states * h->A * sizeof(double); }
 
 mdp_status configure_bellman(mdp_s* h) {
-  const size_t smem = (size_t)h->bell_tile_states * h->A * sizeof(double);
+  const size_t smem = bellman_smem(h);
   if (smem > 48 * 1024) {
-    MDP_CUDA((set_smem<true, true>(smem)));
-    MDP_CUDA((set_smem<true, false>(smem)));
-    MDP_CUDA((set_smem<false, true>(smem)));
-    MDP_CUDA((set_smem<false, false>(smem)));
+    MDP_CUDA(cudaFuncSetAttribute(bellman_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MDP_CUDA(cudaFuncSetAttribute(bellman_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   int per_sm = 0;
   if (h->P.uniform)
-    MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<true, true>, kBellThreads, smem));
+    MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<true>, kBellThreads, smem));
   else
-    MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<false, true>, kBellThreads, smem));
+    MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<false>, kBellThreads, smem));
   if (per_sm < 1) return fail(MDP_ERR_INVALID_ARG, "Bellman tile does not fit on an SM (too many actions)");
   const int64_t ntiles = (h->S + h->bell_tile_states - 1) / h->bell_tile_states;
   h->bell_threads = kBellThreads;
@@ -131,23 +110,18 @@ mdp_status configure_bellman(mdp_s* h) {
   return MDP_OK;
 }
 
-mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi, bool fuse_policy,
-                          cudaStream_t st) {
+mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi, cudaStream_t st) {
   MDP_CUDA(cudaMemsetAsync(h->resmax, 0, sizeof(unsigned long long), st));
-  const size_t smem = (size_t)h->bell_tile_states * h->A * sizeof(double);
+  const size_t smem = bellman_smem(h);
   const Sell& P = h->P;
-  const Sell& Q = h->Ppi;
-  const int k = P.uniform ? P.kmax : 0;
-#define MDP_BELL(U, F)                                                                                       \
-  bellman_kernel<U, F><<<h->bell_blocks, kBellThreads, smem, st>>>(                                          \
-      P.val, P.col, P.off, P.len, k, h->g, V, h->S, h->A, h->bell_tile_states, gamma, TV, pi, h->gpi, h->resmax, \
-      Q.val, Q.col, Q.off, Q.len)
-  if (P.uniform) {
-    if (fuse_policy) MDP_BELL(true, true); else MDP_BELL(true, false);
-  } else {
-    if (fuse_policy) MDP_BELL(false, true); else MDP_BELL(false, false);
-  }
-#undef MDP_BELL
+  if (P.uniform)
+    bellman_kernel<true><<<h->bell_blocks, kBellThreads, smem, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, V,
+                                                                      h->S, h->A, h->bell_tile_states, gamma, TV, pi,
+                                                                      h->resmax);
+  else
+    bellman_kernel<false><<<h->bell_blocks, kBellThreads, smem, st>>>(P.val, P.col, P.off, P.len, 0, h->g, V, h->S,
+                                                                       h->A, h->bell_tile_states, gamma, TV, pi,
+                                                                       h->resmax);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   return MDP_OK;
@@ -164,7 +138,7 @@ extern "C" mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, d
   if (!V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
   if ((const void*)V == (const void*)TV) return fail(MDP_ERR_INVALID_ARG, "V and TV may not alias");
   cudaStream_t st = (cudaStream_t)stream;
-  mdp_status s = launch_bellman(h, gamma, V, TV, pi, false, st);
+  mdp_status s = launch_bellman(h, gamma, V, TV, pi, st);
   if (s != MDP_OK) return s;
   if (residual_inf)
     MDP_CUDA(cudaMemcpyAsync(residual_inf, h->resmax, sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -1,21 +1,57 @@
 // Inexact policy evaluation (Algorithm 1 steps 6-12): the matrix-free operator
 // J_pi x = x - gamma P_pi x (Sec. III-B.3) over the policy's rows, and the two
 // inner solvers, Richardson (theta += omega (g_pi - J_pi theta)) and restarted
-// GMRES(m) with classical Gram-Schmidt plus one re-orthogonalisation (CGS2).
+// GMRES(m) (Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.5).
+//
+// GMRES runs a whole restart cycle without the host: classical Gram-Schmidt
+// with a second pass only when the DGKS test asks for it (Daniel, Gragg,
+// Kaufman and Stewart, Math. Comp. 1976: re-orthogonalise when the norm after
+// projection falls below 1/sqrt(2) of the norm before), the Givens rotations,
+// the residual estimate and the stop test all on the device.  Each kernel
+// reduces its dot products in its last finishing block (fixed order, so
+// results are deterministic) and checks device flags on entry, so steps queued
+// after the stop test fired return at once.  The host waits once per cycle.
+//
+// Basis vectors are stored unnormalised (u_i) with scales sigma_i (v_i =
+// sigma_i u_i); the scales are folded into the projection coefficients, so no
+// pass rescales a vector.
 //
 // Every pass is one thread per state over the per-state sliced layout of P_pi
-// (lanes = consecutive states, so values, columns and vector entries load
-// coalesced; only x[col] is a gather).  Reductions are deterministic: each
-// block writes a partial per quantity, and a one-block kernel adds the
-// partials in a fixed order.
+// (lanes = consecutive states: values, columns and vector entries load
+// coalesced; only x[col] is a gather).
+#include <algorithm>
 #include <cmath>
-#include <vector>
+#include <cstring>
 
 #include "mdp_internal.cuh"
 
 namespace mdp {
 
 constexpr int kVecThreads = 256;
+
+// ---- device state of an inner solve -------------------------------------------------
+
+struct KrylovState {
+  double H[(kMaxBasis + 1) * kMaxBasis];  // H[i * kMaxBasis + j]: rotated Hessenberg (upper triangle = R)
+  double cs[kMaxBasis], sn[kMaxBasis];    // Givens rotations
+  double e[kMaxBasis + 1];                // rotated right-hand side beta e_1
+  double hc[kMaxBasis + 1];               // current column h_i = v_i . w
+  double coef[kMaxBasis + 1];             // projection coefficients on the stored u_i
+  double sigma[kMaxBasis + 1];            // v_i = sigma_i u_i
+  double wnorm, beta, estimate, res2, tol;
+  int it, maxit, m, jdone, flags, counter, result;  // result: Richardson buffer holding the answer
+};
+
+struct KrylovHeader {  // host copy of the int tail of KrylovState
+  int it, maxit, m, jdone, flags, counter, result;
+};
+
+enum : int {
+  kCycleStop = 1,  // this restart cycle is over
+  kSolveDone = 2,  // the whole inner solve is over
+  kReorth = 4,     // the current step needs its second Gram-Schmidt pass
+  kNumeric = 8,    // a non-finite norm appeared
+};
 
 // sum_j P_pi[s, j] x[col_j] for state s (lane l of slice s/32)
 template <bool UNIFORM>
@@ -29,44 +65,97 @@ __device__ __forceinline__ double policy_row_dot(const double* __restrict__ pval
   const int32_t* cp = pcol + base;
   double acc = 0.0;
   int j = 0;
-  for (; j + 4 <= n; j += 4) {
-    double v[4];
-    int c[4];
+  for (; j + 8 <= n; j += 8) {
+    double v[8];
+    int c[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       v[u] = vp[(int64_t)(j + u) * kSlice];
       c[u] = cp[(int64_t)(j + u) * kSlice];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc = fma(v[u], __ldg(x + c[u]), acc);
+    for (int u = 0; u < 8; ++u) acc = fma(v[u], __ldg(x + c[u]), acc);
   }
   for (; j < n; ++j) acc = fma(vp[(int64_t)j * kSlice], __ldg(x + cp[(int64_t)j * kSlice]), acc);
   return acc;
 }
 
-// Block sum of NV per-thread values; thread 0..NV-1 of the block then writes
-// partials[blockIdx.x * kMaxBasis + i].  Fixed shuffle tree, fixed warp order.
+// Block sums of NV per-thread values into partials[blockIdx.x][i]; the last block
+// to finish then adds the partials of all blocks in block order into out[i]
+// (shared memory) and returns true in all of its threads.  Deterministic for a
+// fixed grid.  The counter is left at zero for the next kernel.
 template <int NV>
-__device__ __forceinline__ void block_partials(double (&d)[NV], int nvalid, double* __restrict__ partials) {
+__device__ bool grid_sum(const double (&d)[NV], double* __restrict__ partials, int* counter, double* out) {
   __shared__ double red[kVecThreads / 32][NV];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    if (i < nvalid) {
-      double v = d[i];
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][i] = v;
-    }
+    double v = d[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
-  if (threadIdx.x < nvalid) {
+  if (threadIdx.x < NV) {
     double v = 0.0;
     for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * kMaxBasis + threadIdx.x] = v;
+    partials[(int64_t)blockIdx.x * kPartialStride + threadIdx.x] = v;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int i = warp; i < NV; i += kVecThreads / 32) {  // warp i adds column i over the blocks
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads (L2, bypassing L1)
+    int b = lane;
+    for (; b + 96 < (int)gridDim.x; b += 128) {
+      v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
+      v1 += __ldcg(partials + (int64_t)(b + 32) * kPartialStride + i);
+      v2 += __ldcg(partials + (int64_t)(b + 64) * kPartialStride + i);
+      v3 += __ldcg(partials + (int64_t)(b + 96) * kPartialStride + i);
+    }
+    for (; b < (int)gridDim.x; b += 32) v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
+    double v = (v0 + v1) + (v2 + v3);
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0;
+  return true;
 }
 
-// y = x - gamma P_pi x
+// Finish Arnoldi step j once beta = ||u_{j+1}|| is final (one thread).
+__device__ void finish_step(KrylovState* K, int j) {
+  double* H = K->H;
+  for (int i = 0; i <= j; ++i) H[i * kMaxBasis + j] = K->hc[i];
+  const double hn = K->beta;
+  H[(j + 1) * kMaxBasis + j] = hn;
+  for (int i = 0; i < j; ++i) {  // earlier rotations applied to column j
+    const double a = H[i * kMaxBasis + j], b = H[(i + 1) * kMaxBasis + j];
+    H[i * kMaxBasis + j] = K->cs[i] * a + K->sn[i] * b;
+    H[(i + 1) * kMaxBasis + j] = -K->sn[i] * a + K->cs[i] * b;
+  }
+  const double a = H[j * kMaxBasis + j], b = H[(j + 1) * kMaxBasis + j];
+  const double d = hypot(a, b);
+  K->cs[j] = a / d;
+  K->sn[j] = b / d;
+  H[j * kMaxBasis + j] = d;
+  H[(j + 1) * kMaxBasis + j] = 0.0;
+  K->e[j + 1] = -K->sn[j] * K->e[j];
+  K->e[j] = K->cs[j] * K->e[j];
+  K->estimate = fabs(K->e[j + 1]);
+  K->sigma[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+  K->it += 1;
+  K->jdone = j + 1;
+  if (!isfinite(hn) || !(d > 0.0) || !isfinite(d)) K->flags |= kNumeric | kCycleStop | kSolveDone;
+  if (K->estimate < K->tol || K->it >= K->maxit || hn == 0.0 || j + 1 == K->m) K->flags |= kCycleStop;
+}
+
+// ---- kernels ---------------------------------------------------------------------
+
+// y = x - gamma P_pi x (states whose policy entry was invalid carry g_pi = NaN and get NaN)
 template <bool U>
 __global__ void __launch_bounds__(kVecThreads) policy_apply_kernel(const double* __restrict__ pval,
                                                                     const int32_t* __restrict__ pcol,
@@ -77,347 +166,371 @@ __global__ void __launch_bounds__(kVecThreads) policy_apply_kernel(const double*
                                                                     double* __restrict__ y) {
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
     const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, x);
-    // states whose policy entry was invalid carry g_pi = NaN: poison their output
     const double gv = gpi[s];
     y[s] = (gv != gv) ? gv : x[s] - gamma * px;
   }
 }
 
-// r = b - J theta written to r_out; partial ||r||^2.  Richardson variant also
-// writes theta_out = theta + omega r.
-template <bool U, bool RICH>
-__global__ void __launch_bounds__(kVecThreads) residual_kernel(const double* __restrict__ pval,
-                                                                const int32_t* __restrict__ pcol,
-                                                                const int64_t* __restrict__ poff,
-                                                                const int32_t* __restrict__ plen, int k, int64_t S,
-                                                                double gamma, double omega,
-                                                                const double* __restrict__ theta,
-                                                                const double* __restrict__ b,
-                                                                double* __restrict__ out, double* __restrict__ partials) {
+// GMRES (re)start: u_0 = r = b - J theta and beta_0 = ||r||_2; prepares the next
+// cycle, or ends the solve when beta_0 < tol or the iteration cap is reached.
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* __restrict__ pval,
+                                                                   const int32_t* __restrict__ pcol,
+                                                                   const int64_t* __restrict__ poff,
+                                                                   const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                   double gamma, const double* __restrict__ theta,
+                                                                   const double* __restrict__ b,
+                                                                   double* __restrict__ u0, double* partials,
+                                                                   KrylovState* K) {
+  if (K->flags & kSolveDone) return;
   double d[1] = {0.0};
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
     const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, theta);
-    const double th = theta[s];
-    const double r = b[s] - (th - gamma * px);
+    const double r = b[s] - (theta[s] - gamma * px);
     d[0] = fma(r, r, d[0]);
-    out[s] = RICH ? fma(omega, r, th) : r;
+    u0[s] = r;
   }
-  block_partials<1>(d, 1, partials);
+  __shared__ double out[1];
+  if (grid_sum<1>(d, partials, &K->counter, out) && threadIdx.x == 0) {
+    const double beta = sqrt(out[0]);
+    K->res2 = beta;
+    K->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    K->e[0] = beta;
+    for (int i = 1; i <= kMaxBasis; ++i) K->e[i] = 0.0;
+    K->jdone = 0;
+    K->flags &= ~(kCycleStop | kReorth);
+    if (!isfinite(beta)) K->flags |= kNumeric | kSolveDone;
+    if (beta < K->tol || K->it >= K->maxit) K->flags |= kSolveDone;
+  }
 }
 
-// Arnoldi pass 1: w = J v_j, and partial dots v_i . w for i <= j.
+// Arnoldi pass A: w = J v_j; raw dots u_i . w (i <= j) and ||w||^2 (slot NB).
 template <bool U, int NB>
-__global__ void __launch_bounds__(kVecThreads) arnoldi_matvec_kernel(const double* __restrict__ pval,
-                                                                      const int32_t* __restrict__ pcol,
-                                                                      const int64_t* __restrict__ poff,
-                                                                      const int32_t* __restrict__ plen, int k,
-                                                                      int64_t S, double gamma,
-                                                                      const double* __restrict__ basis, int j,
-                                                                      double* __restrict__ w,
-                                                                      double* __restrict__ partials) {
-  double d[NB];
+__global__ void __launch_bounds__(kVecThreads) gm_pass_a_kernel(const double* __restrict__ pval,
+                                                                 const int32_t* __restrict__ pcol,
+                                                                 const int64_t* __restrict__ poff,
+                                                                 const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                 double gamma, const double* __restrict__ basis, int j,
+                                                                 double* __restrict__ w, double* partials,
+                                                                 KrylovState* K) {
+  if (K->flags & (kCycleStop | kSolveDone)) return;
+  const double sj = K->sigma[j];
+  double d[NB + 1];
 #pragma unroll
-  for (int i = 0; i < NB; ++i) d[i] = 0.0;
-  const double* vj = basis + (int64_t)j * S;
+  for (int i = 0; i <= NB; ++i) d[i] = 0.0;
+  const double* uj = basis + (int64_t)j * S;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, vj);
-    const double ws = vj[s] - gamma * px;
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
+    const double ws = sj * (uj[s] - gamma * px);
     w[s] = ws;
 #pragma unroll
     for (int i = 0; i < NB; ++i)
       if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
+    d[NB] = fma(ws, ws, d[NB]);
   }
-  block_partials<NB>(d, j + 1, partials);
+  __shared__ double out[NB + 1];
+  if (grid_sum<NB + 1>(d, partials, &K->counter, out) && threadIdx.x == 0) {
+    for (int i = 0; i <= j; ++i) {
+      const double h = K->sigma[i] * out[i];
+      K->hc[i] = h;
+      K->coef[i] = h * K->sigma[i];
+    }
+    K->wnorm = sqrt(out[NB]);
+  }
 }
 
-// Arnoldi pass 2 (re-orthogonalisation): w' = w - sum_i h_i v_i, partial dots v_i . w'.
-template <int NB>
-__global__ void __launch_bounds__(kVecThreads) cgs_correct_kernel(int64_t S, const double* __restrict__ basis, int j,
-                                                                   const double* __restrict__ h,
-                                                                   const double* __restrict__ w,
-                                                                   double* __restrict__ partials) {
-  __shared__ double hc[NB];
-  double d[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) d[i] = 0.0;
-  if (threadIdx.x < NB) hc[threadIdx.x] = (threadIdx.x <= j) ? h[threadIdx.x] : 0.0;
-  __syncthreads();
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    double ws = w[s];
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i <= j) ws = fma(-hc[i], basis[(int64_t)i * S + s], ws);
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i <= j) d[i] = fma(__ldca(basis + (int64_t)i * S + s), ws, d[i]);
-  }
-  block_partials<NB>(d, j + 1, partials);
-}
+// Arnoldi projection passes.  First pass (MODE = kPlain, kDgks or kAlways):
+// u_{j+1} = w - sum_i coef_i u_i and ||u_{j+1}||^2; kDgks and kAlways also form
+// the raw dots u_i . u_{j+1} that a second classical Gram-Schmidt pass needs.
+// The last block then finishes the step, or (kAlways; kDgks when the norm fell
+// below 1/sqrt(2) of ||w||) turns the dots into corrections and requests the
+// second pass (MODE = kSecond): u_{j+1} -= sum_i coef_i u_i, ||u_{j+1}||^2, finish.
+enum { kPlain = 0, kDgks = 1, kAlways = 2, kSecond = 3 };
 
-// Arnoldi pass 3: u = w - sum_i h_i v_i (h = first + second coefficients) into
-// basis slot j+1, partial ||u||^2.
-template <int NB>
-__global__ void __launch_bounds__(kVecThreads) cgs_final_kernel(int64_t S, double* __restrict__ basis, int j,
-                                                                 const double* __restrict__ h,
-                                                                 const double* __restrict__ w,
-                                                                 double* __restrict__ partials) {
-  __shared__ double hc[NB];
-  double d[1] = {0.0};
-  if (threadIdx.x < NB) hc[threadIdx.x] = (threadIdx.x <= j) ? h[threadIdx.x] : 0.0;
+template <int NB, int MODE>
+__global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, double* __restrict__ basis, int j,
+                                                                  const double* __restrict__ w, double* partials,
+                                                                  KrylovState* K) {
+  constexpr bool SECOND = (MODE == kSecond);
+  constexpr bool DOTS = (MODE == kDgks || MODE == kAlways);
+  if (K->flags & (kCycleStop | kSolveDone)) return;
+  if (SECOND && !(K->flags & kReorth)) return;
+  __shared__ double c[NB];
+  if (threadIdx.x < NB) c[threadIdx.x] = ((int)threadIdx.x <= j) ? K->coef[threadIdx.x] : 0.0;
   __syncthreads();
   double* u = basis + (int64_t)(j + 1) * S;
+  const double* src = SECOND ? u : w;
+  constexpr int NV = DOTS ? NB + 1 : 1;  // slot 0: ||u||^2; slots 1..j+1: dots
+  double d[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) d[i] = 0.0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    double ws = w[s];
+    double x = src[s];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
-      if (i <= j) ws = fma(-hc[i], basis[(int64_t)i * S + s], ws);
-    u[s] = ws;
-    d[0] = fma(ws, ws, d[0]);
+      if (i <= j) x = fma(-c[i], basis[(int64_t)i * S + s], x);
+    u[s] = x;
+    d[0] = fma(x, x, d[0]);
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i <= j) d[(i + 1) % NV] = fma(basis[(int64_t)i * S + s], x, d[(i + 1) % NV]);
+    }
   }
-  block_partials<1>(d, 1, partials);
+  __shared__ double out[NV];
+  if (grid_sum<NV>(d, partials, &K->counter, out) && threadIdx.x == 0) {
+    const double beta = sqrt(out[0]);
+    K->beta = beta;
+    const bool again = (MODE == kAlways && beta > 0.0) ||
+                       (MODE == kDgks && beta > 0.0 && beta < 0.70710678118654752 * K->wnorm);
+    if (again) {
+      for (int i = 0; i <= j; ++i) {
+        const double h2 = K->sigma[i] * out[(i + 1) % NV];
+        K->hc[i] += h2;
+        K->coef[i] = h2 * K->sigma[i];
+      }
+      K->flags |= kReorth;
+    } else {
+      K->flags &= ~kReorth;
+      finish_step(K, j);
+    }
+  }
 }
 
-// theta += sum_{i < n} y_i v_i
-template <int NB>
-__global__ void __launch_bounds__(kVecThreads) basis_update_kernel(int64_t S, const double* __restrict__ basis, int n,
-                                                                    const double* __restrict__ y,
-                                                                    double* __restrict__ theta) {
-  __shared__ double yc[NB];
-  if (threadIdx.x < NB) yc[threadIdx.x] = (threadIdx.x < n) ? y[threadIdx.x] : 0.0;
+// theta += sum_{i < jdone} y_i v_i, where every block solves R y = e by back substitution.
+__global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const double* __restrict__ basis,
+                                                                 double* __restrict__ theta, KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  __shared__ double c[kMaxBasis];
+  const int n = K->jdone;
+  if (threadIdx.x == 0) {
+    double y[kMaxBasis];
+    for (int i = n - 1; i >= 0; --i) {
+      double t = K->e[i];
+      for (int q = i + 1; q < n; ++q) t -= K->H[i * kMaxBasis + q] * y[q];
+      y[i] = t / K->H[i * kMaxBasis + i];
+    }
+    for (int i = 0; i < n; ++i) c[i] = y[i] * K->sigma[i];
+  }
   __syncthreads();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    double t = theta[s];
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i < n) t = fma(yc[i], basis[(int64_t)i * S + s], t);
-    theta[s] = t;
-  }
-}
-
-// v *= scale[0]
-__global__ void scale_kernel(int64_t S, double* __restrict__ v, const double* __restrict__ scale) {
-  const double c = scale[0];
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
-    v[s] *= c;
-}
-
-enum { kSum = 0, kAdd = 1, kNorm = 2 };
-
-// One block: dst[i] = (mode == kAdd ? src[i] : 0) + sum_b partials[b][i] for i < n,
-// or (kNorm) dst[0] = sqrt(sum), dst[1] = 1 / dst[0] (0 if dst[0] == 0).
-__global__ void reduce_partials_kernel(const double* __restrict__ partials, int nblk, int n, int mode,
-                                       const double* __restrict__ src, double* __restrict__ dst) {
-  __shared__ double red[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = 0; i < n; ++i) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partials[(int64_t)b * kMaxBasis + i];
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += red[w];
-      if (mode == kNorm) {
-        const double nr = sqrt(t);
-        dst[0] = nr;
-        dst[1] = nr > 0.0 ? 1.0 / nr : 0.0;
-      } else {
-        dst[i] = (mode == kAdd ? src[i] : 0.0) + t;
-      }
+    double t0 = theta[s], t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= n; i += 4) {
+      t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
+      t1 = fma(c[i + 1], basis[(int64_t)(i + 1) * S + s], t1);
+      t2 = fma(c[i + 2], basis[(int64_t)(i + 2) * S + s], t2);
+      t3 = fma(c[i + 3], basis[(int64_t)(i + 3) * S + s], t3);
     }
-    __syncthreads();
+    for (; i < n; ++i) t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
+    theta[s] = (t0 + t1) + (t2 + t3);
   }
 }
 
-// device scalar slots
-enum {
-  kSlotH1 = 0,      // first-pass coefficients [32]
-  kSlotH = 64,      // Hessenberg column j: h_0..h_j, then norm at [j+1]
-  kSlotNorm = 160,  // [0] = norm, [1] = 1/norm
-  kSlotY = 192,     // update coefficients [32]
-};
+// One Richardson step from buffer `in`: r = b - J in, out = in + omega r, ||r||_2.
+// The last block ends the solve when ||r|| < tol (the answer is then `in`) or
+// when the step cap is reached (the answer is `out`).
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __restrict__ pval,
+                                                                 const int32_t* __restrict__ pcol,
+                                                                 const int64_t* __restrict__ poff,
+                                                                 const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                 double gamma, double omega,
+                                                                 const double* __restrict__ in,
+                                                                 const double* __restrict__ b,
+                                                                 double* __restrict__ out, int in_index,
+                                                                 double* partials, KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  double d[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, in);
+    const double th = in[s];
+    const double r = b[s] - (th - gamma * px);
+    d[0] = fma(r, r, d[0]);
+    out[s] = fma(omega, r, th);
+  }
+  __shared__ double o[1];
+  if (grid_sum<1>(d, partials, &K->counter, o) && threadIdx.x == 0) {
+    const double rn = sqrt(o[0]);
+    K->res2 = rn;
+    if (!isfinite(rn)) {
+      K->flags |= kNumeric | kSolveDone;
+      K->result = in_index;
+    } else if (rn < K->tol) {
+      K->flags |= kSolveDone;
+      K->result = in_index;
+    } else {
+      K->it += 1;
+      K->result = 1 - in_index;
+      if (K->it >= K->maxit) K->flags |= kSolveDone;
+    }
+  }
+}
 
-#define MDP_LAUNCH_CHECK(h) \
-  do {                      \
-    (h)->launches++;        \
+// ---- host side -------------------------------------------------------------------
+
+#define MDP_LAUNCH_CHECK(h)       \
+  do {                            \
+    (h)->launches++;              \
     MDP_CUDA(cudaGetLastError()); \
   } while (0)
 
-static mdp_status reduce(mdp_s* h, int n, int mode, const double* src, double* dst, cudaStream_t st) {
-  reduce_partials_kernel<<<1, 256, 0, st>>>(h->partials, h->vec_blocks, n, mode, src, dst);
-  MDP_LAUNCH_CHECK(h);
+static KrylovState* kstate(mdp_s* h) { return (KrylovState*)h->kstate; }
+
+// Zero the device state and set tol, maxit and m (through the pinned scratch).
+static mdp_status init_state(mdp_s* h, double tol, int maxit, int m, cudaStream_t st) {
+  KrylovState* K = kstate(h);
+  MDP_CUDA(cudaMemsetAsync(K, 0, sizeof(KrylovState), st));
+  h->hkrylov[0] = tol;
+  KrylovHeader hd{0, maxit, m, 0, 0, 0, 0};
+  std::memcpy(h->hkrylov + 2, &hd, sizeof(hd));
+  MDP_CUDA(cudaMemcpyAsync(&K->tol, h->hkrylov, sizeof(double), cudaMemcpyHostToDevice, st));
+  MDP_CUDA(cudaMemcpyAsync(&K->it, h->hkrylov + 2, sizeof(hd), cudaMemcpyHostToDevice, st));
   return MDP_OK;
 }
 
-template <bool U>
-static mdp_status residual(mdp_s* h, double gamma, double omega, const double* theta, double* out, bool rich,
-                           cudaStream_t st) {
-  const Sell& Q = h->Ppi;
-  const int k = U ? Q.kmax : 0;
-  if (rich)
-    residual_kernel<U, true><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, h->S, gamma,
-                                                                     omega, theta, h->gpi, out, h->partials);
-  else
-    residual_kernel<U, false><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, h->S, gamma,
-                                                                      omega, theta, h->gpi, out, h->partials);
-  MDP_LAUNCH_CHECK(h);
-  h->matvecs += 1;
-  h->vreads += 1;
-  h->vwrites += 1;
-  return reduce(h, 1, kNorm, nullptr, h->sc + kSlotNorm, st);
-}
-
-static mdp_status read_scalars(mdp_s* h, int slot, int n, cudaStream_t st) {
-  MDP_CUDA(cudaMemcpyAsync(h->hpin + slot, h->sc + slot, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+static mdp_status read_header(mdp_s* h, KrylovHeader* out, double* res2, cudaStream_t st) {
+  KrylovState* K = kstate(h);
+  MDP_CUDA(cudaMemcpyAsync(h->hkrylov + 8, &K->it, sizeof(KrylovHeader), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaMemcpyAsync(h->hkrylov + 16, &K->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(out, h->hkrylov + 8, sizeof(KrylovHeader));
+  *res2 = h->hkrylov[16];
   return MDP_OK;
 }
 
 template <bool U, int NB>
-static mdp_status arnoldi_step(mdp_s* h, double gamma, int j, cudaStream_t st) {
+static mdp_status arnoldi_step(mdp_s* h, double gamma, int j, int refine, cudaStream_t st) {
   const Sell& Q = h->Ppi;
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
-  arnoldi_matvec_kernel<U, NB><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma,
-                                                                       h->basis, j, h->w, h->partials);
+  KrylovState* K = kstate(h);
+  gm_pass_a_kernel<U, NB><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma, h->basis,
+                                                                  j, h->w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
-  mdp_status r = reduce(h, j + 1, kSum, nullptr, h->sc + kSlotH1, st);
-  if (r != MDP_OK) return r;
-  cgs_correct_kernel<NB><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->sc + kSlotH1, h->w, h->partials);
-  MDP_LAUNCH_CHECK(h);
-  r = reduce(h, j + 1, kAdd, h->sc + kSlotH1, h->sc + kSlotH, st);
-  if (r != MDP_OK) return r;
-  cgs_final_kernel<NB><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->sc + kSlotH, h->w, h->partials);
-  MDP_LAUNCH_CHECK(h);
-  r = reduce(h, 1, kNorm, nullptr, h->sc + kSlotNorm, st);
-  if (r != MDP_OK) return r;
-  scale_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis + (int64_t)(j + 1) * S, h->sc + kSlotNorm + 1);
-  MDP_LAUNCH_CHECK(h);
-  // pass 1: P_pi v_j plus the other j basis vectors, writes w; pass 2: w and j+1
-  // basis vectors; pass 3: the same, writes v_{j+1}; scaling: one read, one write
-  h->matvecs += 1;
-  h->vreads += j + (j + 2) + (j + 2) + 1;
-  h->vwrites += 1 + 1 + 1;
-  return MDP_OK;
-}
-
-template <bool U>
-static mdp_status arnoldi_dispatch(mdp_s* h, double gamma, int j, cudaStream_t st) {
-  if (j + 1 <= 8) return arnoldi_step<U, 8>(h, gamma, j, st);
-  if (j + 1 <= 16) return arnoldi_step<U, 16>(h, gamma, j, st);
-  return arnoldi_step<U, 32>(h, gamma, j, st);
-}
-
-static mdp_status basis_update(mdp_s* h, int n, double* theta, cudaStream_t st) {
-  const double* y = h->sc + kSlotY;
-  if (n <= 8)
-    basis_update_kernel<8><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, n, y, theta);
-  else if (n <= 16)
-    basis_update_kernel<16><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, n, y, theta);
+  if (refine == MDP_REFINE_NEVER) {
+    gm_project_kernel<NB, kPlain><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+    MDP_LAUNCH_CHECK(h);
+    return MDP_OK;
+  }
+  if (refine == MDP_REFINE_IFNEEDED)
+    gm_project_kernel<NB, kDgks><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
   else
-    basis_update_kernel<32><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, n, y, theta);
+    gm_project_kernel<NB, kAlways><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
-  h->vreads += n + 1;
-  h->vwrites += 1;
+  gm_project_kernel<NB, kSecond><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+  MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
 
-// Restarted GMRES(m) on J_pi theta = g_pi (Saad, Sec. 6.5), CGS2 Arnoldi on the
-// device, Givens rotations and the triangular solve on the host (m <= 32).
 template <bool U>
-static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, double tol, int maxit, int* iters,
-                        double* res2, cudaStream_t st) {
+static mdp_status arnoldi_dispatch(mdp_s* h, double gamma, int j, int refine, cudaStream_t st) {
+  if (j + 1 <= 8) return arnoldi_step<U, 8>(h, gamma, j, refine, st);
+  if (j + 1 <= 16) return arnoldi_step<U, 16>(h, gamma, j, refine, st);
+  return arnoldi_step<U, 32>(h, gamma, j, refine, st);
+}
+
+template <bool U>
+static mdp_status gm_residual(mdp_s* h, double gamma, const double* theta, cudaStream_t st) {
+  const Sell& Q = h->Ppi;
+  gm_residual_kernel<U><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+                                                                gamma, theta, h->gpi, h->basis, h->partials,
+                                                                kstate(h));
+  MDP_LAUNCH_CHECK(h);
+  return MDP_OK;
+}
+
+// Algorithmic work of `steps` Arnoldi steps without re-orthogonalisation: pass A
+// reads P_pi with x = u_j, j more basis vectors and writes w; pass B reads w and
+// j+1 basis vectors and writes u_{j+1}.
+static void count_cycle(mdp_s* h, int steps) {
+  for (int j = 0; j < steps; ++j) {
+    h->matvecs += 1;
+    h->vreads += j + (j + 2);
+    h->vwrites += 2;
+  }
+  h->vreads += steps + 1;  // update: basis vectors and theta
+  h->vwrites += 1;
+  h->matvecs += 1;  // the residual that follows
+  h->vreads += 1;
+  h->vwrites += 1;
+}
+
+template <bool U>
+static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine, double tol, int maxit,
+                        int* iters, double* res2, cudaStream_t st) {
   mdp_status r = ensure_basis(h, m + 1);
   if (r != MDP_OK) return r;
-  const int64_t S = h->S;
-  int it = 0;
-  r = residual<U>(h, gamma, 1.0, theta, h->basis, false, st);
+  KrylovState* K = kstate(h);
+  r = init_state(h, tol, maxit, m, st);
   if (r != MDP_OK) return r;
-  r = read_scalars(h, kSlotNorm, 2, st);
+  r = gm_residual<U>(h, gamma, theta, st);
   if (r != MDP_OK) return r;
-  double beta = h->hpin[kSlotNorm];
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), e(m + 1), y(m);
-  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-  while (beta >= tol && it < maxit) {
-    if (!std::isfinite(beta)) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
-    scale_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, h->sc + kSlotNorm + 1);
+  h->matvecs += 1;
+  h->vreads += 1;
+  h->vwrites += 1;
+  KrylovHeader hd{};
+  double rn = 0.0;
+  int it_before = 0;
+  for (;;) {
+    r = read_header(h, &hd, &rn, st);
+    if (r != MDP_OK) return r;
+    if (hd.flags & kSolveDone) break;
+    if (hd.it > it_before) count_cycle(h, hd.it - it_before);
+    it_before = hd.it;
+    const int steps = std::min(m, maxit - hd.it);
+    for (int j = 0; j < steps; ++j) {
+      r = arnoldi_dispatch<U>(h, gamma, j, refine, st);
+      if (r != MDP_OK) return r;
+    }
+    gm_update_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, theta, K);
     MDP_LAUNCH_CHECK(h);
-    h->vreads += 1;
-    h->vwrites += 1;
-    std::fill(e.begin(), e.end(), 0.0);
-    e[0] = beta;
-    int jdone = 0;
-    for (int j = 0; j < m; ++j) {
-      r = arnoldi_dispatch<U>(h, gamma, j, st);
-      if (r != MDP_OK) return r;
-      // column j of H: h_0..h_j from slot H, h_{j+1} = norm
-      MDP_CUDA(cudaMemcpyAsync(h->hpin + kSlotH, h->sc + kSlotH, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      r = read_scalars(h, kSlotNorm, 1, st);
-      if (r != MDP_OK) return r;
-      for (int i = 0; i <= j; ++i) Hat(i, j) = h->hpin[kSlotH + i];
-      const double hn = h->hpin[kSlotNorm];
-      Hat(j + 1, j) = hn;
-      if (!std::isfinite(hn)) return fail(MDP_ERR_NUMERIC, "non-finite Arnoldi norm in GMRES");
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
-        Hat(i + 1, j) = -sn[i] * Hat(i, j) + cs[i] * Hat(i + 1, j);
-        Hat(i, j) = t;
-      }
-      const double d = std::hypot(Hat(j, j), Hat(j + 1, j));
-      cs[j] = Hat(j, j) / d;
-      sn[j] = Hat(j + 1, j) / d;
-      Hat(j, j) = d;
-      Hat(j + 1, j) = 0.0;
-      e[j + 1] = -sn[j] * e[j];
-      e[j] = cs[j] * e[j];
-      ++it;
-      jdone = j + 1;
-      if (std::fabs(e[j + 1]) < tol || it >= maxit || hn == 0.0) break;
-    }
-    for (int i = jdone - 1; i >= 0; --i) {
-      double t = e[i];
-      for (int c = i + 1; c < jdone; ++c) t -= Hat(i, c) * y[c];
-      y[i] = t / Hat(i, i);
-    }
-    for (int i = 0; i < jdone; ++i) h->hpin[kSlotY + i] = y[i];
-    MDP_CUDA(cudaMemcpyAsync(h->sc + kSlotY, h->hpin + kSlotY, jdone * sizeof(double), cudaMemcpyHostToDevice, st));
-    r = basis_update(h, jdone, theta, st);
+    r = gm_residual<U>(h, gamma, theta, st);
     if (r != MDP_OK) return r;
-    r = residual<U>(h, gamma, 1.0, theta, h->basis, false, st);
-    if (r != MDP_OK) return r;
-    r = read_scalars(h, kSlotNorm, 2, st);
-    if (r != MDP_OK) return r;
-    beta = h->hpin[kSlotNorm];
   }
-  if (!std::isfinite(beta)) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
-  *iters = it;
-  *res2 = beta;
+  if (hd.it > it_before) count_cycle(h, hd.it - it_before);
+  if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
+  *iters = hd.it;
+  *res2 = rn;
   return MDP_OK;
 }
 
 // Richardson: before each step r = g_pi - J theta; stop when ||r||_2 < tol, else
-// theta += omega r; at most maxit steps.
+// theta += omega r; at most maxit steps.  Steps are queued in batches and the
+// host waits once per batch; steps queued after the stop return at once.
 template <bool U>
 static mdp_status richardson(mdp_s* h, double gamma, double* theta, double omega, double tol, int maxit, int* iters,
                              double* res2, cudaStream_t st) {
-  double* a = theta;
-  double* b = h->tmp;
-  int it = 0;
+  KrylovState* K = kstate(h);
+  mdp_status r = init_state(h, tol, maxit, 0, st);
+  if (r != MDP_OK) return r;
+  double* buf[2] = {theta, h->tmp};
+  const Sell& Q = h->Ppi;
+  KrylovHeader hd{};
   double rn = INFINITY;
-  while (it < maxit) {
-    mdp_status r = residual<U>(h, gamma, omega, a, b, true, st);
-    if (r != MDP_OK) return r;
-    r = read_scalars(h, kSlotNorm, 1, st);
-    if (r != MDP_OK) return r;
-    rn = h->hpin[kSlotNorm];
-    if (!std::isfinite(rn)) return fail(MDP_ERR_NUMERIC, "non-finite residual in Richardson");
-    if (rn < tol) break;
-    std::swap(a, b);
-    ++it;
+  int issued = 0;
+  if (maxit > 0) {
+    for (;;) {
+      const int batch = std::min(maxit - issued, issued < 8 ? 2 : 16);
+      for (int b = 0; b < batch; ++b, ++issued) {
+        const int in = issued & 1;
+        rich_step_kernel<U><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+                                                                    gamma, omega, buf[in], h->gpi, buf[1 - in], in,
+                                                                    h->partials, K);
+        MDP_LAUNCH_CHECK(h);
+      }
+      r = read_header(h, &hd, &rn, st);
+      if (r != MDP_OK) return r;
+      if ((hd.flags & kSolveDone) || issued >= maxit) break;
+    }
+    const int worked = hd.it + ((hd.flags & kSolveDone) && hd.it < maxit ? 1 : 0);
+    h->matvecs += worked;
+    h->vreads += worked;
+    h->vwrites += worked;
+    if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in Richardson");
+    if (hd.result == 1) MDP_CUDA(cudaMemcpyAsync(theta, h->tmp, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  if (a != theta) MDP_CUDA(cudaMemcpyAsync(theta, a, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  *iters = it;
+  *iters = maxit > 0 ? hd.it : 0;
   *res2 = rn;
   return MDP_OK;
 }
@@ -434,14 +547,16 @@ mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* 
   return MDP_OK;
 }
 
-mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, double omega, double tol,
-                       int max_it, int* iters, double* res2, cudaStream_t st) {
+size_t krylov_state_bytes() { return sizeof(KrylovState); }
+
+mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, double omega,
+                       double tol, int max_it, int* iters, double* res2, cudaStream_t st) {
   *iters = 0;
   *res2 = 0.0;
   const bool U = h->Ppi.uniform;
   if (inner == MDP_GMRES)
-    return U ? gmres<true>(h, gamma, theta, restart, tol, max_it, iters, res2, st)
-             : gmres<false>(h, gamma, theta, restart, tol, max_it, iters, res2, st);
+    return U ? gmres<true>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st)
+             : gmres<false>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st);
   return U ? richardson<true>(h, gamma, theta, omega, tol, max_it, iters, res2, st)
            : richardson<false>(h, gamma, theta, omega, tol, max_it, iters, res2, st);
 }

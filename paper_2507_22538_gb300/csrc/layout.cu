@@ -117,42 +117,42 @@ __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t
 }
 
 // Algorithm 1 step 4: gather the policy's rows r(s) = s*A + pi(s) of the stacked
-// matrix into the per-state sliced layout, and g_pi(s) = g(s, pi(s)).  States
-// whose pi(s) lies outside [0, A) get an empty row and g_pi = NaN.
+// matrix into the per-state sliced layout, and g_pi(s) = g(s, pi(s)).  One thread
+// per (state, entry) with the state fastest, so each warp's writes are
+// contiguous and every load is independent.  States whose pi(s) lies outside
+// [0, A) get an empty row (zero values, column 0) and g_pi = NaN.
+template <bool UNIFORM>
 __global__ void extract_policy_kernel(const double* __restrict__ sval, const int32_t* __restrict__ scol,
-                                      const int64_t* __restrict__ off, const int32_t* __restrict__ len, int uniform_k,
+                                      const int64_t* __restrict__ off, const int32_t* __restrict__ len, int kmax,
                                       const double* __restrict__ g, const int32_t* __restrict__ pi, int64_t S, int A,
                                       double* __restrict__ pval, int32_t* __restrict__ pcol,
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    int a = pi[s];
-    int64_t ps = s / kSlice;
-    int pl = (int)(s % kSlice);
-    int64_t pbase = uniform_k ? ps * kSlice * (int64_t)uniform_k : poff[ps];
-    if (a < 0 || a >= A) {
-      if (!uniform_k) {
-        plen[s] = 0;
-      } else {
-        for (int j = 0; j < uniform_k; ++j) {
-          pval[pbase + (int64_t)j * kSlice + pl] = 0.0;
-          pcol[pbase + (int64_t)j * kSlice + pl] = 0;
-        }
-      }
-      gpi[s] = __longlong_as_double(0x7ff8000000000000ULL);
-      continue;
+  const int64_t work = S * (int64_t)kmax;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = w % S;
+    const int j = (int)(w / S);
+    const int a = pi[s];
+    const bool ok = (a >= 0 && a < A);
+    const int64_t r = s * A + (ok ? a : 0);
+    const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
+    if (j == 0) {
+      if (!UNIFORM) plen[s] = n;
+      gpi[s] = ok ? g[r] : __longlong_as_double(0x7ff8000000000000ULL);
     }
-    int64_t r = s * A + a;
-    int64_t q = r / kSlice;
-    int lane = (int)(r % kSlice);
-    int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
-    int n = uniform_k ? uniform_k : len[r];
-    for (int j = 0; j < n; ++j) {
-      pval[pbase + (int64_t)j * kSlice + pl] = sval[base + (int64_t)j * kSlice + lane];
-      pcol[pbase + (int64_t)j * kSlice + pl] = scol[base + (int64_t)j * kSlice + lane];
+    const int64_t ps = s / kSlice;
+    const int64_t pmax = UNIFORM ? kmax : (poff[ps + 1] - poff[ps]) / kSlice;
+    if (j >= pmax) continue;
+    const int64_t dst = (UNIFORM ? ps * kSlice * (int64_t)kmax : poff[ps]) + (s % kSlice) + (int64_t)j * kSlice;
+    if (j < n) {
+      const int64_t q = r / kSlice;
+      const int64_t src = (UNIFORM ? q * kSlice * (int64_t)kmax : off[q]) + (r % kSlice) + (int64_t)j * kSlice;
+      pval[dst] = sval[src];
+      pcol[dst] = scol[src];
+    } else if (UNIFORM) {
+      pval[dst] = 0.0;
+      pcol[dst] = 0;
     }
-    if (!uniform_k) plen[s] = n;
-    gpi[s] = g[r];
   }
 }
 
@@ -224,8 +224,14 @@ static void free_sell(Sell* m) {
 mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st) {
   const Sell& P = h->P;
   Sell& Q = h->Ppi;
-  extract_policy_kernel<<<h->vec_blocks, h->vec_threads, 0, st>>>(
-      P.val, P.col, P.off, P.len, P.uniform ? P.kmax : 0, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi);
+  const int64_t work = h->S * (int64_t)P.kmax;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->sm_count * 16));
+  if (P.uniform)
+    extract_policy_kernel<true><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
+                                                         Q.val, Q.col, Q.off, Q.len, h->gpi);
+  else
+    extract_policy_kernel<false><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
+                                                          Q.val, Q.col, Q.off, Q.len, h->gpi);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   return MDP_OK;
@@ -246,6 +252,8 @@ static void destroy_handle(mdp_s* h) {
   cudaFree(h->sc);
   cudaFree(h->resmax);
   if (h->hpin) cudaFreeHost(h->hpin);
+  if (h->hkrylov) cudaFreeHost(h->hkrylov);
+  cudaFree(h->kstate);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
@@ -365,7 +373,9 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
 
   // launch shapes
   h->vec_threads = 256;
-  h->vec_blocks = grid_for(S, h->vec_threads, h->sm_count);
+  // vector passes: up to 4 blocks per SM (whole grid resident even at 128 registers
+  // per thread), few enough that the last block's reduction of the partials is short
+  h->vec_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, (int64_t)h->sm_count * 4));
   {
     // Bellman tile: a multiple of 32 states whose rows fill whole warps where possible
     int64_t ts = 32;
@@ -387,7 +397,16 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(&h->piw, S, "policy"));
   MDP_TRY(dalloc(&h->w, S, "w"));
   MDP_TRY(dalloc(&h->tmp, S, "tmp"));
-  MDP_TRY(dalloc(&h->partials, (size_t)h->vec_blocks * kMaxBasis, "partials"));
+  MDP_TRY(dalloc(&h->partials, (size_t)h->vec_blocks * kPartialStride, "partials"));
+  {
+    cudaError_t e = cudaMalloc(&h->kstate, krylov_state_bytes());
+    if (e != cudaSuccess) {
+      h->kstate = nullptr;
+      cudaGetLastError();
+      return fail(MDP_ERR_OOM, "device allocation failed: solver state");
+    }
+  }
+  MDP_CUDA(cudaMallocHost((void**)&h->hkrylov, 32 * sizeof(double)));
   MDP_CUDA(cudaEventCreate(&h->ev0));
   MDP_CUDA(cudaEventCreate(&h->ev1));
   MDP_CUDA(cudaEventCreate(&h->ev2));
@@ -414,6 +433,7 @@ void mdp_default_opts(mdp_solve_opts* o) {
   o->gmres_restart = 30;
   o->inner = MDP_GMRES;
   o->record_timing = 0;
+  o->gmres_refine = MDP_REFINE_NEVER;
 }
 
 const char* mdp_last_error(void) { return g_last_error.c_str(); }

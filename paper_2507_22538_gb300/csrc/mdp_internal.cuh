@@ -12,6 +12,7 @@ namespace mdp {
 
 constexpr int kSlice = 32;       // rows (or states) per sliced-ELL slice: one warp, one row per lane
 constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
+constexpr int kPartialStride = 40;  // per-block partial sums (up to kMaxBasis + 1 values)
 constexpr int kScalarSlots = 512;
 
 // Per-thread message of the last failure.
@@ -71,7 +72,9 @@ struct mdp_s {
   double* tmp = nullptr;     // [S]
   double* basis = nullptr;   // [(restart + 1) * S]
   int basis_cap = 0;         // vectors allocated in basis
-  double* partials = nullptr;  // [vec_blocks * kMaxBasis]
+  double* partials = nullptr;  // [vec_blocks * kPartialStride]
+  void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
+  double* hkrylov = nullptr;   // pinned host scratch for that state [32]
   double* sc = nullptr;      // device scalars [kScalarSlots]
   unsigned long long* resmax = nullptr;  // device max of |TV - V| bits
   double* hpin = nullptr;    // pinned host scalars [kScalarSlots]
@@ -85,18 +88,17 @@ struct mdp_s {
 namespace mdp {
 
 // layout.cu
-mdp_status build_policy_layout(mdp_s* h, cudaStream_t st);  // allocate Ppi for h->P
 mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st);  // fill Ppi, gpi from pi
 
 // bellman.cu
 mdp_status configure_bellman(mdp_s* h);  // threads and grid of the Bellman sweep
-mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi,
-                          bool fuse_policy, cudaStream_t st);
+mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi, cudaStream_t st);
 
 // krylov.cu
 mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st);
-mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, double omega,
+mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, double omega,
                        double tol, int max_it, int* iters, double* res2, cudaStream_t st);
 mdp_status ensure_basis(mdp_s* h, int nvec);
+size_t krylov_state_bytes();
 
 }  // namespace mdp

@@ -36,7 +36,7 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
   if (v != v0) MDP_CUDA(cudaMemcpyAsync(v, v0, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
   int it = 0;
   double r2 = 0.0;
-  s = inner_solve(h, gamma, v, inner, restart, omega, abs_tol_2norm, max_it, &it, &r2, st);
+  s = inner_solve(h, gamma, v, inner, restart, MDP_REFINE_NEVER, omega, abs_tol_2norm, max_it, &it, &r2, st);
   MDP_CUDA(cudaStreamSynchronize(st));
   if (iters) *iters = it;
   if (res_2norm) *res_2norm = r2;
@@ -57,6 +57,8 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   if (o->inner != MDP_GMRES && o->inner != MDP_RICHARDSON) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
   if (o->inner == MDP_GMRES && (o->gmres_restart < 1 || o->gmres_restart > kMaxBasis))
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
+  if (o->gmres_refine < MDP_REFINE_NEVER || o->gmres_refine > MDP_REFINE_ALWAYS)
+    return fail(MDP_ERR_INVALID_ARG, "unknown gmres_refine");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
@@ -65,9 +67,9 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   mdp_status status = MDP_OK;
   int k = 0;
   for (;;) {
-    // Algorithm 1 steps 2-3 (and step 4's row gather, fused): TV, pi_{k+1}, ||r(V_k)||_inf
+    // Algorithm 1 steps 2-3: TV, pi_{k+1} and ||r(V_k)||_inf in one sweep
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev0, st));
-    mdp_status s = launch_bellman(h, o->gamma, V, h->TV, pi, true, st);
+    mdp_status s = launch_bellman(h, o->gamma, V, h->TV, pi, st);
     if (s != MDP_OK) return s;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev1, st));
     local.bellman_sweeps++;
@@ -92,12 +94,18 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
       status = fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
       break;
     }
-    // steps 4-12: theta_0 = V_k, solve J_pi theta = g_pi to ||.||_2 < alpha * ||r(V_k)||_inf
+    // step 4: the policy's rows P_pi and costs g_pi, gathered into the per-state layout
+    s = extract_policy(h, pi, st);
+    if (s != MDP_OK) {
+      status = s;
+      break;
+    }
+    // steps 5-12: theta_0 = V_k, solve J_pi theta = g_pi to ||.||_2 < alpha * ||r(V_k)||_inf
     int it = 0;
     double r2 = 0.0;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev2, st));
-    s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->richardson_scale, o->alpha * res,
-                    o->max_iter_ksp, &it, &r2, st);
+    s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->gmres_refine, o->richardson_scale,
+                    o->alpha * res, o->max_iter_ksp, &it, &r2, st);
     if (s != MDP_OK) {
       status = s;
       break;

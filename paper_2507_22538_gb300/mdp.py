@@ -29,13 +29,16 @@ STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_INVALID_ARG", 2: "MDP_ERR_NOT_STOCHASTI
 MDP_F64 = 0
 MDP_GMRES = 0
 MDP_RICHARDSON = 1
+MDP_REFINE_NEVER = 0
+MDP_REFINE_IFNEEDED = 1
+MDP_REFINE_ALWAYS = 2
 
 
 class mdp_solve_opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("atol_pi", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("richardson_scale", ctypes.c_double), ("max_iter_pi", ctypes.c_int32),
                 ("max_iter_ksp", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("record_timing", ctypes.c_int32)]
+                ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):
@@ -238,12 +241,14 @@ class MDP:
         return v, it, res, st
 
     def solve(self, gamma, V0=None, tol=1e-8, alpha=1e-4, inner=MDP_GMRES, restart=30, omega=1.0,
-              max_outer=1000, max_inner=1000, record_timing=False, stream=None, device="cuda"):
+              max_outer=1000, max_inner=1000, record_timing=False, refine=MDP_REFINE_NEVER, stream=None,
+              device="cuda"):
         import torch
         o = mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.richardson_scale = gamma, tol, alpha, omega
         o.max_iter_pi, o.max_iter_ksp, o.gmres_restart, o.inner = max_outer, max_inner, restart, inner
         o.record_timing = 1 if record_timing else 0
+        o.gmres_refine = refine
         V = torch.zeros(self.S, dtype=torch.float64, device=device) if V0 is None else V0.clone()
         pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
         st, stats = mdp_solve(self.h, o, V, pi, stream)

@@ -130,3 +130,23 @@ def test_warm_start_resumes():
         V2, pi2, stats2, st2 = M.solve(m.gamma, V0=V, tol=1e-10, alpha=1e-3)
         torch.cuda.synchronize()
     assert stats2.outer_iters == 0 and torch.equal(V, V2) and torch.equal(pi, pi2)
+
+
+@pytest.mark.parametrize("refine", [0, 1, 2], ids=["never", "ifneeded", "always"])
+def test_gram_schmidt_refinement_modes(refine):
+    """All three Gram-Schmidt refinement choices reach the oracle-certified V."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    from tests._util import check_policy, q_tolerance
+    for m, alpha in ((random_sparse(1000, 4, 8, 0.9, seed=1), 1e-3), (banded_birth_death(5000, 20, 16, 0.999), 0.01)):
+        tol = 0.5e-8 * (1 - m.gamma) * float(np.max(np.abs(O.ipi(*_args(m), tol=1e-8, alpha=alpha).V)))
+        with mdp.MDP.from_data(m) as M:
+            V, pi, stats, st = M.solve(m.gamma, tol=tol, alpha=alpha, refine=refine, max_outer=300)
+            torch.cuda.synchronize()
+        assert st == mdp.MDP_OK, stats.as_dict()
+        Vg = V.cpu().numpy()
+        P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+        Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+        qt = q_tolerance(m, Vg)
+        assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol + qt
+        check_policy(pi.cpu().numpy(), Q, qt)
