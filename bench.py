@@ -214,6 +214,40 @@ def run_bellman_only(args):
     return 0
 
 
+def run_inner_only(args):
+    """Time a fixed number of GMRES(30) iterations of mdp_policy_eval on the policy
+    'always action 0' of the banded workload, built as a one-action MDP (0.4 GB)."""
+    import numpy as np
+    import torch
+
+    from mdpgen import MDPData, banded_birth_death
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.build import build
+    build()
+    full = banded_birth_death(args.states, A, H, GAMMA)
+    rows = np.arange(args.states, dtype=np.int64) * A  # row (s, 0)
+    k = K_ROW
+    col = full.col.reshape(-1, k)[rows].ravel()
+    val = full.val.reshape(-1, k)[rows].ravel()
+    m = MDPData(args.states, 1, np.arange(args.states + 1, dtype=np.int64) * k, col, val, full.g[rows], GAMMA)
+    del full
+    stream = torch.cuda.current_stream()
+    with mdp.MDP.from_data(m, stream) as M:
+        pi = torch.zeros(m.S, dtype=torch.int32, device="cuda")
+        v0 = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+        v = torch.empty_like(v0)
+        mdp.mdp_policy_eval(M.h, GAMMA, pi, v0, v, mdp.MDP_GMRES, RESTART, 1.0, 0.0, 30, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, it, res = mdp.mdp_policy_eval(M.h, GAMMA, pi, v0, v, mdp.MDP_GMRES, RESTART, 1.0, 0.0, args.inner_only,
+                                          stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    print(json.dumps({"mode": "inner_only", "S": m.S, "iterations": it, "ms_per_iteration": dt * 1e3 / max(it, 1),
+                      "residual": res}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,12 +258,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
                     help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
-    ap.add_argument("--states", type=int, default=S, help="with --bellman-only: number of states")
+    ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only: number of states")
+    ap.add_argument("--inner-only", type=int, default=0, metavar="ITERS",
+                    help="profiling aid: ITERS GMRES(30) iterations of mdp_policy_eval on the rows of action 0 "
+                         "of the workload (a one-action MDP; no bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.bellman_only:
         return run_bellman_only(args)
+    if args.inner_only:
+        return run_inner_only(args)
 
     import numpy as np
     import torch

@@ -80,26 +80,55 @@ __device__ __forceinline__ double policy_row_dot(const double* __restrict__ pval
   return acc;
 }
 
-// Block sums of NV per-thread values into partials[blockIdx.x][i]; the last block
-// to finish then adds the partials of all blocks in block order into out[i]
-// (shared memory) and returns true in all of its threads.  Deterministic for a
-// fixed grid.  The counter is left at zero for the next kernel.
-template <int NV>
-__device__ bool grid_sum(const double (&d)[NV], double* __restrict__ partials, int* counter, double* out) {
-  __shared__ double red[kVecThreads / 32][NV];
+// Warp reduce-scatter of N values per lane (N a power of two, N <= 32): each
+// butterfly level halves the values a lane carries (it keeps one half, adds the
+// partner's copy of that half), so the warp spends about N additions per lane
+// instead of 5 N for N separate shuffle trees; the last levels, once a lane
+// carries one value, are plain butterflies.  Returns the warp sum of value
+// index (lane >> (5 - log2 N)) in every lane.
+template <int N>
+__device__ __forceinline__ double warp_reduce_scatter(double (&d)[N]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int half = N / 2, o = 16; half >= 1; half /= 2, o /= 2) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double keep = upper ? d[i + half] : d[i];
+      const double send = upper ? d[i] : d[i + half];
+      d[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double v = d[0];
+  constexpr int kSplitLevels = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
+#pragma unroll
+  for (int o = 16 >> kSplitLevels; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sums of NV per-thread values (NV a power of two) plus one extra value into
+// partials[blockIdx.x][0 .. NV] (the extra one at index NV when HAS_EXTRA); the
+// last block to finish then adds the partials of all blocks in block order into
+// out[] (shared memory) and returns true in all of its threads.  Deterministic
+// for a fixed grid.  The counter is left at zero for the next kernel.
+template <int NV, bool HAS_EXTRA>
+__device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ partials, int* counter, double* out) {
+  constexpr int NT = NV + (HAS_EXTRA ? 1 : 0);
+  constexpr int kLog = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : (NV >= 2) ? 1 : 0;
+  __shared__ double red[kVecThreads / 32][NT];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double v = d[i];
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][i] = v;
+  const double v = warp_reduce_scatter<NV>(d);
+  if ((lane & ((1 << (5 - kLog)) - 1)) == 0) red[warp][lane >> (5 - kLog)] = v;
+  if (HAS_EXTRA) {
+    for (int o = 16; o; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o);
+    if (lane == 0) red[warp][NT - 1] = extra;
   }
   __syncthreads();
-  if (threadIdx.x < NV) {
-    double v = 0.0;
-    for (int w = 0; w < kVecThreads / 32; ++w) v += red[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * kPartialStride + threadIdx.x] = v;
+  if (threadIdx.x < NT) {
+    double t = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) t += red[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * kPartialStride + threadIdx.x] = t;
   }
   __threadfence();
   __syncthreads();
@@ -107,8 +136,8 @@ __device__ bool grid_sum(const double (&d)[NV], double* __restrict__ partials, i
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  for (int i = warp; i < NV; i += kVecThreads / 32) {  // warp i adds column i over the blocks
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;  // independent loads (L2, bypassing L1)
+  for (int i = warp; i < NT; i += kVecThreads / 32) {  // warp i adds column i over the blocks
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;       // independent loads (L2, bypassing L1)
     int b = lane;
     for (; b + 96 < (int)gridDim.x; b += 128) {
       v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
@@ -117,9 +146,9 @@ __device__ bool grid_sum(const double (&d)[NV], double* __restrict__ partials, i
       v3 += __ldcg(partials + (int64_t)(b + 96) * kPartialStride + i);
     }
     for (; b < (int)gridDim.x; b += 32) v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
-    double v = (v0 + v1) + (v2 + v3);
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) out[i] = v;
+    double t = (v0 + v1) + (v2 + v3);
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) out[i] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0;
@@ -191,7 +220,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
     u0[s] = r;
   }
   __shared__ double out[1];
-  if (grid_sum<1>(d, partials, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(d, 0.0, partials, &K->counter, out) && threadIdx.x == 0) {
     const double beta = sqrt(out[0]);
     K->res2 = beta;
     K->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -204,32 +233,46 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
   }
 }
 
-// Arnoldi pass A: w = J v_j; raw dots u_i . w (i <= j) and ||w||^2 (slot NB).
-template <bool U, int NB>
-__global__ void __launch_bounds__(kVecThreads) gm_pass_a_kernel(const double* __restrict__ pval,
+// Arnoldi step, part 1: w = J v_j = sigma_j (u_j - gamma P_pi u_j).  A lean
+// kernel (no reductions, few registers) so that enough warps are resident to
+// keep the row and gather loads of P_pi in flight.
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const double* __restrict__ pval,
                                                                  const int32_t* __restrict__ pcol,
                                                                  const int64_t* __restrict__ poff,
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
                                                                  double gamma, const double* __restrict__ basis, int j,
-                                                                 double* __restrict__ w, double* partials,
-                                                                 KrylovState* K) {
+                                                                 double* __restrict__ w, const KrylovState* K) {
   if (K->flags & (kCycleStop | kSolveDone)) return;
   const double sj = K->sigma[j];
-  double d[NB + 1];
-#pragma unroll
-  for (int i = 0; i <= NB; ++i) d[i] = 0.0;
   const double* uj = basis + (int64_t)j * S;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
     const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
-    const double ws = sj * (uj[s] - gamma * px);
-    w[s] = ws;
+    w[s] = sj * (uj[s] - gamma * px);
+  }
+}
+
+// Arnoldi step, part 2: raw dots u_i . w (i <= j) and ||w||^2; the last block
+// turns them into the Hessenberg column h_i = v_i . w and the projection
+// coefficients.
+template <int NB>
+__global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const double* __restrict__ basis, int j,
+                                                               const double* __restrict__ w, double* partials,
+                                                               KrylovState* K) {
+  if (K->flags & (kCycleStop | kSolveDone)) return;
+  double d[NB];
+  double ww = 0.0;
+#pragma unroll
+  for (int i = 0; i < NB; ++i) d[i] = 0.0;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double ws = w[s];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
       if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
-    d[NB] = fma(ws, ws, d[NB]);
+    ww = fma(ws, ws, ww);
   }
   __shared__ double out[NB + 1];
-  if (grid_sum<NB + 1>(d, partials, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<NB, true>(d, ww, partials, &K->counter, out) && threadIdx.x == 0) {
     for (int i = 0; i <= j; ++i) {
       const double h = K->sigma[i] * out[i];
       K->hc[i] = h;
@@ -260,8 +303,9 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, doub
   __syncthreads();
   double* u = basis + (int64_t)(j + 1) * S;
   const double* src = SECOND ? u : w;
-  constexpr int NV = DOTS ? NB + 1 : 1;  // slot 0: ||u||^2; slots 1..j+1: dots
+  constexpr int NV = DOTS ? NB : 1;  // dots u_i . u_{j+1} (first pass with dots); ||u||^2 goes last
   double d[NV];
+  double uu = 0.0;
 #pragma unroll
   for (int i = 0; i < NV; ++i) d[i] = 0.0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
@@ -270,22 +314,29 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, doub
     for (int i = 0; i < NB; ++i)
       if (i <= j) x = fma(-c[i], basis[(int64_t)i * S + s], x);
     u[s] = x;
-    d[0] = fma(x, x, d[0]);
+    uu = fma(x, x, uu);
     if (DOTS) {
 #pragma unroll
       for (int i = 0; i < NB; ++i)
-        if (i <= j) d[(i + 1) % NV] = fma(basis[(int64_t)i * S + s], x, d[(i + 1) % NV]);
+        if (i <= j) d[i % NV] = fma(basis[(int64_t)i * S + s], x, d[i % NV]);
     }
   }
-  __shared__ double out[NV];
-  if (grid_sum<NV>(d, partials, &K->counter, out) && threadIdx.x == 0) {
-    const double beta = sqrt(out[0]);
+  __shared__ double out[NV + 1];
+  bool last;
+  if (DOTS)
+    last = grid_sum<NV, true>(d, uu, partials, &K->counter, out);
+  else {
+    double n1[1] = {uu};
+    last = grid_sum<1, false>(n1, 0.0, partials, &K->counter, out);
+  }
+  if (last && threadIdx.x == 0) {
+    const double beta = sqrt(out[DOTS ? NV : 0]);
     K->beta = beta;
     const bool again = (MODE == kAlways && beta > 0.0) ||
                        (MODE == kDgks && beta > 0.0 && beta < 0.70710678118654752 * K->wnorm);
     if (again) {
       for (int i = 0; i <= j; ++i) {
-        const double h2 = K->sigma[i] * out[(i + 1) % NV];
+        const double h2 = K->sigma[i] * out[i % NV];
         K->hc[i] += h2;
         K->coef[i] = h2 * K->sigma[i];
       }
@@ -350,7 +401,7 @@ __global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __
     out[s] = fma(omega, r, th);
   }
   __shared__ double o[1];
-  if (grid_sum<1>(d, partials, &K->counter, o) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(d, 0.0, partials, &K->counter, o) && threadIdx.x == 0) {
     const double rn = sqrt(o[0]);
     K->res2 = rn;
     if (!isfinite(rn)) {
@@ -405,11 +456,13 @@ static mdp_status arnoldi_step(mdp_s* h, double gamma, int j, int refine, cudaSt
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
-  gm_pass_a_kernel<U, NB><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma, h->basis,
-                                                                  j, h->w, h->partials, K);
+  gm_matvec_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma, h->basis, j,
+                                                             h->w, K);
+  MDP_LAUNCH_CHECK(h);
+  gm_dots_kernel<NB><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
-    gm_project_kernel<NB, kPlain><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+    gm_project_kernel<NB, kPlain><<<h->mv_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   }
@@ -433,16 +486,17 @@ static mdp_status arnoldi_dispatch(mdp_s* h, double gamma, int j, int refine, cu
 template <bool U>
 static mdp_status gm_residual(mdp_s* h, double gamma, const double* theta, cudaStream_t st) {
   const Sell& Q = h->Ppi;
-  gm_residual_kernel<U><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+  gm_residual_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
                                                                 gamma, theta, h->gpi, h->basis, h->partials,
                                                                 kstate(h));
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
 
-// Algorithmic work of `steps` Arnoldi steps without re-orthogonalisation: pass A
-// reads P_pi with x = u_j, j more basis vectors and writes w; pass B reads w and
-// j+1 basis vectors and writes u_{j+1}.
+// Algorithmic work of `steps` Arnoldi steps without re-orthogonalisation (one
+// pass would do): apply P_pi with x = u_j, read the other j basis vectors for
+// the dots, write w; the projection reads w and the j+1 basis vectors and
+// writes u_{j+1}.
 static void count_cycle(mdp_s* h, int steps) {
   for (int j = 0; j < steps; ++j) {
     h->matvecs += 1;
@@ -514,7 +568,7 @@ static mdp_status richardson(mdp_s* h, double gamma, double* theta, double omega
       const int batch = std::min(maxit - issued, issued < 8 ? 2 : 16);
       for (int b = 0; b < batch; ++b, ++issued) {
         const int in = issued & 1;
-        rich_step_kernel<U><<<h->vec_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+        rich_step_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
                                                                     gamma, omega, buf[in], h->gpi, buf[1 - in], in,
                                                                     h->partials, K);
         MDP_LAUNCH_CHECK(h);

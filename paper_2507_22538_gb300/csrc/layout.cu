@@ -376,6 +376,7 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   // vector passes: up to 4 blocks per SM (whole grid resident even at 128 registers
   // per thread), few enough that the last block's reduction of the partials is short
   h->vec_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, (int64_t)h->sm_count * 4));
+  h->mv_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, (int64_t)h->sm_count * 8));
   {
     // Bellman tile: a multiple of 32 states whose rows fill whole warps where possible
     int64_t ts = 32;
@@ -397,7 +398,7 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(&h->piw, S, "policy"));
   MDP_TRY(dalloc(&h->w, S, "w"));
   MDP_TRY(dalloc(&h->tmp, S, "tmp"));
-  MDP_TRY(dalloc(&h->partials, (size_t)h->vec_blocks * kPartialStride, "partials"));
+  MDP_TRY(dalloc(&h->partials, (size_t)std::max(h->vec_blocks, h->mv_blocks) * kPartialStride, "partials"));
   {
     cudaError_t e = cudaMalloc(&h->kstate, krylov_state_bytes());
     if (e != cudaSuccess) {

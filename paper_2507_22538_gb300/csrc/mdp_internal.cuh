@@ -63,7 +63,8 @@ struct mdp_s {
 
   // vector-kernel launch shape (thread per state)
   int vec_threads = 256;
-  int vec_blocks = 0;
+  int vec_blocks = 0;  // reductions over states (bounded so the last block's final sum stays short)
+  int mv_blocks = 0;   // policy mat-vec without reduction (as many resident warps as fit)
 
   // workspace
   double* TV = nullptr;      // [S]
