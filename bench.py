@@ -52,12 +52,6 @@ def bellman_bytes():
     return nnz * 12 + (R + 1) * 8 + R * 8 + S * 8 + S * (8 + 4)
 
 
-def inner_bytes(stats):
-    """Algorithmic bytes of the inner solves: each P_pi application reads the
-    policy's rows (12 B per entry) and its x once; each counted vector access
-    moves 8 B per state."""
-    per_matvec = S * K_ROW * 12 + S * 8
-    return stats["policy_matvecs"] * per_matvec + (stats["vector_reads"] + stats["vector_writes"]) * 8 * S
 
 
 def load_peaks():
@@ -300,9 +294,9 @@ def main():
     opts.gamma, opts.atol_pi, opts.alpha, opts.gmres_restart = GAMMA, TOL, ALPHA, RESTART
     opts.inner, opts.record_timing = mdp.MDP_GMRES, 1
 
-    def step():
+    def step(o=opts):
         V.zero_()
-        st, stats = mdp.mdp_solve(M.h, opts, V, pi, stream)
+        st, stats = mdp.mdp_solve(M.h, o, V, pi, stream)
         mdp.check(st, "mdp_solve")
         return stats.as_dict()
 
@@ -319,7 +313,7 @@ def main():
         for _ in range(args.steps):
             s = step()
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
-                        "inner_ms", "policy_matvecs", "vector_reads", "vector_writes"):
+                        "inner_ms", "inner_bytes"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
@@ -332,6 +326,25 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
+
+    # the same solves with the mixed-precision inner solver (FP32 Arnoldi, FP64 refinement)
+    mopts = mdp.mdp_default_opts()
+    for f, _ in mdp.mdp_solve_opts._fields_:
+        setattr(mopts, f, getattr(opts, f))
+    mopts.precision = mdp.MDP_PREC_MIXED
+    for _ in range(args.warmup):
+        step(mopts)
+    torch.cuda.synchronize()
+    mtot = {}
+    e0.record(stream)
+    for _ in range(args.steps):
+        s = step(mopts)
+        for key in ("outer_iters", "inner_iters_total", "kernel_launches", "inner_ms", "inner_bytes"):
+            mtot[key] = mtot.get(key, 0) + s[key]
+        mtot["final_residual"] = max(mtot.get("final_residual", 0.0), s["final_residual"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = e0.elapsed_time(e1) / args.steps
 
     # end to end through the C ABI from pinned host buffers: upload + layout + solve + read back
     pinned = {k: torch.from_numpy(getattr(m, k)).pin_memory() for k in ("row_ptr", "col", "val", "g")}
@@ -365,7 +378,7 @@ def main():
     sweeps = totals["bellman_sweeps"]
     bell_ms = totals["bellman_ms"] / sweeps
     bell_gbs = bellman_bytes() / (bell_ms * 1e-3) / 1e9
-    inner_gbs = inner_bytes(totals) / (totals["inner_ms"] * 1e-3) / 1e9 if totals["inner_ms"] > 0 else None
+    inner_gbs = totals["inner_bytes"] / (totals["inner_ms"] * 1e-3) / 1e9 if totals["inner_ms"] > 0 else None
     share_bell = totals["bellman_ms"] / (ms * args.steps)
     roofline = {"bound": "hbm", "kernel": "bellman_kernel (fused SpMV + min/argmin + residual + policy-row gather)",
                 "achieved": bell_gbs, "peak": peak, "unit": "GB/s", "frac": bell_gbs / peak,
@@ -375,12 +388,20 @@ def main():
                 "share_of_step": share_bell}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
-                  "bytes": inner_bytes(totals) / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
+                  "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
+    mixed = {"what": "same solves, GMRES inner solver with FP32 Arnoldi cycles and FP64 restart residuals "
+                     "(MDP_PREC_MIXED); FP64 sweep and stop test",
+             "value": mixed_ms / 1e3, "unit": "s", "ms_per_step": mixed_ms,
+             "speedup_vs_f64": ms / mixed_ms,
+             "outer_per_step": mtot["outer_iters"] / args.steps, "inner_per_step": mtot["inner_iters_total"] / args.steps,
+             "inner_ms_per_step": mtot["inner_ms"] / args.steps,
+             "inner_GBps": mtot["inner_bytes"] / (mtot["inner_ms"] * 1e-3) / 1e9 if mtot["inner_ms"] > 0 else None,
+             "max_final_residual": mtot["final_residual"], "gpu_launches": int(mtot["kernel_launches"])}
 
     line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
-            "roofline": roofline, "roofline_inner": inner_roof,
+            "roofline": roofline, "roofline_inner": inner_roof, "mixed_precision": mixed,
             "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
                            "inner_per_step": totals["inner_iters_total"] / args.steps,
                            "max_final_residual": totals["final_residual"]},

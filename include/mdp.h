@@ -49,6 +49,14 @@ typedef enum { MDP_GMRES = 0, MDP_RICHARDSON = 1 } mdp_inner;
    original (Daniel-Gragg-Kaufman-Stewart test), or always two passes. */
 typedef enum { MDP_REFINE_NEVER = 0, MDP_REFINE_IFNEEDED = 1, MDP_REFINE_ALWAYS = 2 } mdp_refine;
 
+/* Arithmetic of the GMRES inner solve.  MDP_PREC_F64: everything in binary64.
+   MDP_PREC_MIXED: each restart forms the residual g_pi - J_pi theta and updates
+   theta in binary64, while the Arnoldi cycle (mat-vec with binary32 copies of the
+   policy's probabilities, basis vectors, Gram-Schmidt) runs in binary32 and the
+   Hessenberg least-squares in binary64; restarted GMRES then acts as iterative
+   refinement.  The Bellman sweep and the outer stop test are binary64 in both. */
+typedef enum { MDP_PREC_F64 = 0, MDP_PREC_MIXED = 1 } mdp_precision;
+
 /* Options of Algorithm 1 with the defaults of Table 1 (set by mdp_default_opts). */
 typedef struct {
   double gamma;            /* discount factor, 0 < gamma < 1 (no default; must be set) */
@@ -61,6 +69,7 @@ typedef struct {
   int32_t inner;           /* an mdp_inner value                                  (MDP_GMRES) */
   int32_t record_timing;   /* nonzero: time Bellman sweeps and inner solves (CUDA events) (0) */
   int32_t gmres_refine;    /* an mdp_refine value                          (MDP_REFINE_NEVER) */
+  int32_t precision;       /* an mdp_precision value of the GMRES inner solve  (MDP_PREC_F64) */
 } mdp_solve_opts;
 
 /* Statistics of one mdp_solve call (host struct filled by the library). */
@@ -79,6 +88,7 @@ typedef struct {
   int64_t vector_reads;       /* length-S double vectors the inner kernels must read, besides
                                  the P_pi applications (each counts its x once) */
   int64_t vector_writes;      /* length-S double vectors the inner kernels write */
+  double inner_bytes;         /* algorithmic bytes the inner kernels must move, in their storage types */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -53,20 +53,20 @@ enum : int {
   kNumeric = 8,    // a non-finite norm appeared
 };
 
-// sum_j P_pi[s, j] x[col_j] for state s (lane l of slice s/32)
-template <bool UNIFORM>
-__device__ __forceinline__ double policy_row_dot(const double* __restrict__ pval, const int32_t* __restrict__ pcol,
-                                                 const int64_t* __restrict__ poff, const int32_t* __restrict__ plen,
-                                                 int k, int64_t s, const double* __restrict__ x) {
+// sum_j P_pi[s, j] x[col_j] for state s (lane l of slice s/32), in the type of x.
+template <bool UNIFORM, typename TP, typename TX>
+__device__ __forceinline__ TX policy_row_dot(const TP* __restrict__ pval, const int32_t* __restrict__ pcol,
+                                             const int64_t* __restrict__ poff, const int32_t* __restrict__ plen,
+                                             int k, int64_t s, const TX* __restrict__ x) {
   const int64_t q = s / kSlice;
   const int n = UNIFORM ? k : plen[s];
   const int64_t base = (UNIFORM ? q * kSlice * (int64_t)k : poff[q]) + (s % kSlice);
-  const double* vp = pval + base;
+  const TP* vp = pval + base;
   const int32_t* cp = pcol + base;
-  double acc = 0.0;
+  TX acc = TX(0);
   int j = 0;
   for (; j + 8 <= n; j += 8) {
-    double v[8];
+    TP v[8];
     int c[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -74,9 +74,9 @@ __device__ __forceinline__ double policy_row_dot(const double* __restrict__ pval
       c[u] = cp[(int64_t)(j + u) * kSlice];
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = fma(v[u], __ldg(x + c[u]), acc);
+    for (int u = 0; u < 8; ++u) acc = fma((TX)v[u], __ldg(x + c[u]), acc);
   }
-  for (; j < n; ++j) acc = fma(vp[(int64_t)j * kSlice], __ldg(x + cp[(int64_t)j * kSlice]), acc);
+  for (; j < n; ++j) acc = fma((TX)vp[(int64_t)j * kSlice], __ldg(x + cp[(int64_t)j * kSlice]), acc);
   return acc;
 }
 
@@ -202,14 +202,14 @@ __global__ void __launch_bounds__(kVecThreads) policy_apply_kernel(const double*
 
 // GMRES (re)start: u_0 = r = b - J theta and beta_0 = ||r||_2; prepares the next
 // cycle, or ends the solve when beta_0 < tol or the iteration cap is reached.
-template <bool U>
+template <bool U, typename T>
 __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* __restrict__ pval,
                                                                    const int32_t* __restrict__ pcol,
                                                                    const int64_t* __restrict__ poff,
                                                                    const int32_t* __restrict__ plen, int k, int64_t S,
                                                                    double gamma, const double* __restrict__ theta,
                                                                    const double* __restrict__ b,
-                                                                   double* __restrict__ u0, double* partials,
+                                                                   T* __restrict__ u0, double* partials,
                                                                    KrylovState* K) {
   if (K->flags & kSolveDone) return;
   double d[1] = {0.0};
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
     const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, theta);
     const double r = b[s] - (theta[s] - gamma * px);
     d[0] = fma(r, r, d[0]);
-    u0[s] = r;
+    u0[s] = (T)r;
   }
   __shared__ double out[1];
   if (grid_sum<1, false>(d, 0.0, partials, &K->counter, out) && threadIdx.x == 0) {
@@ -236,43 +236,47 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
 // Arnoldi step, part 1: w = J v_j = sigma_j (u_j - gamma P_pi u_j).  A lean
 // kernel (no reductions, few registers) so that enough warps are resident to
 // keep the row and gather loads of P_pi in flight.
-template <bool U>
-__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const double* __restrict__ pval,
+template <bool U, typename T>
+__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const T* __restrict__ pval,
                                                                  const int32_t* __restrict__ pcol,
                                                                  const int64_t* __restrict__ poff,
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
-                                                                 double gamma, const double* __restrict__ basis, int j,
-                                                                 double* __restrict__ w, const KrylovState* K) {
+                                                                 double gamma, const T* __restrict__ basis, int j,
+                                                                 T* __restrict__ w, const KrylovState* K) {
   if (K->flags & (kCycleStop | kSolveDone)) return;
-  const double sj = K->sigma[j];
-  const double* uj = basis + (int64_t)j * S;
+  const T sj = (T)K->sigma[j];
+  const T g = (T)gamma;
+  const T* uj = basis + (int64_t)j * S;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
-    w[s] = sj * (uj[s] - gamma * px);
+    const T px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
+    w[s] = sj * (uj[s] - g * px);
   }
 }
 
 // Arnoldi step, part 2: raw dots u_i . w (i <= j) and ||w||^2; the last block
 // turns them into the Hessenberg column h_i = v_i . w and the projection
 // coefficients.
-template <int NB>
-__global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const double* __restrict__ basis, int j,
-                                                               const double* __restrict__ w, double* partials,
+template <int NB, typename T>
+__global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T* __restrict__ basis, int j,
+                                                               const T* __restrict__ w, double* partials,
                                                                KrylovState* K) {
   if (K->flags & (kCycleStop | kSolveDone)) return;
-  double d[NB];
-  double ww = 0.0;
+  T d[NB];
+  T ww = T(0);
 #pragma unroll
-  for (int i = 0; i < NB; ++i) d[i] = 0.0;
+  for (int i = 0; i < NB; ++i) d[i] = T(0);
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    const double ws = w[s];
+    const T ws = w[s];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
       if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
     ww = fma(ws, ws, ww);
   }
+  double dd[NB];  // per-thread partials widen to double for the block and grid sums
+#pragma unroll
+  for (int i = 0; i < NB; ++i) dd[i] = (double)d[i];
   __shared__ double out[NB + 1];
-  if (grid_sum<NB, true>(d, ww, partials, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<NB, true>(dd, (double)ww, partials, &K->counter, out) && threadIdx.x == 0) {
     for (int i = 0; i <= j; ++i) {
       const double h = K->sigma[i] * out[i];
       K->hc[i] = h;
@@ -290,26 +294,26 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const d
 // second pass (MODE = kSecond): u_{j+1} -= sum_i coef_i u_i, ||u_{j+1}||^2, finish.
 enum { kPlain = 0, kDgks = 1, kAlways = 2, kSecond = 3 };
 
-template <int NB, int MODE>
-__global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, double* __restrict__ basis, int j,
-                                                                  const double* __restrict__ w, double* partials,
+template <int NB, int MODE, typename T>
+__global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
+                                                                  const T* __restrict__ w, double* partials,
                                                                   KrylovState* K) {
   constexpr bool SECOND = (MODE == kSecond);
   constexpr bool DOTS = (MODE == kDgks || MODE == kAlways);
   if (K->flags & (kCycleStop | kSolveDone)) return;
   if (SECOND && !(K->flags & kReorth)) return;
-  __shared__ double c[NB];
-  if (threadIdx.x < NB) c[threadIdx.x] = ((int)threadIdx.x <= j) ? K->coef[threadIdx.x] : 0.0;
+  __shared__ T c[NB];
+  if (threadIdx.x < NB) c[threadIdx.x] = ((int)threadIdx.x <= j) ? (T)K->coef[threadIdx.x] : T(0);
   __syncthreads();
-  double* u = basis + (int64_t)(j + 1) * S;
-  const double* src = SECOND ? u : w;
+  T* u = basis + (int64_t)(j + 1) * S;
+  const T* src = SECOND ? u : w;
   constexpr int NV = DOTS ? NB : 1;  // dots u_i . u_{j+1} (first pass with dots); ||u||^2 goes last
-  double d[NV];
-  double uu = 0.0;
+  T d[NV];
+  T uu = T(0);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) d[i] = 0.0;
+  for (int i = 0; i < NV; ++i) d[i] = T(0);
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    double x = src[s];
+    T x = src[s];
 #pragma unroll
     for (int i = 0; i < NB; ++i)
       if (i <= j) x = fma(-c[i], basis[(int64_t)i * S + s], x);
@@ -323,10 +327,13 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, doub
   }
   __shared__ double out[NV + 1];
   bool last;
-  if (DOTS)
-    last = grid_sum<NV, true>(d, uu, partials, &K->counter, out);
-  else {
-    double n1[1] = {uu};
+  if (DOTS) {
+    double dd[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) dd[i] = (double)d[i];
+    last = grid_sum<NV, true>(dd, (double)uu, partials, &K->counter, out);
+  } else {
+    double n1[1] = {(double)uu};
     last = grid_sum<1, false>(n1, 0.0, partials, &K->counter, out);
   }
   if (last && threadIdx.x == 0) {
@@ -349,7 +356,8 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, doub
 }
 
 // theta += sum_{i < jdone} y_i v_i, where every block solves R y = e by back substitution.
-__global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const double* __restrict__ basis,
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const T* __restrict__ basis,
                                                                  double* __restrict__ theta, KrylovState* K) {
   if (K->flags & kSolveDone) return;
   __shared__ double c[kMaxBasis];
@@ -368,12 +376,12 @@ __global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const
     double t0 = theta[s], t1 = 0.0, t2 = 0.0, t3 = 0.0;
     int i = 0;
     for (; i + 4 <= n; i += 4) {
-      t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
-      t1 = fma(c[i + 1], basis[(int64_t)(i + 1) * S + s], t1);
-      t2 = fma(c[i + 2], basis[(int64_t)(i + 2) * S + s], t2);
-      t3 = fma(c[i + 3], basis[(int64_t)(i + 3) * S + s], t3);
+      t0 = fma(c[i], (double)basis[(int64_t)i * S + s], t0);
+      t1 = fma(c[i + 1], (double)basis[(int64_t)(i + 1) * S + s], t1);
+      t2 = fma(c[i + 2], (double)basis[(int64_t)(i + 2) * S + s], t2);
+      t3 = fma(c[i + 3], (double)basis[(int64_t)(i + 3) * S + s], t3);
     }
-    for (; i < n; ++i) t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
+    for (; i < n; ++i) t0 = fma(c[i], (double)basis[(int64_t)i * S + s], t0);
     theta[s] = (t0 + t1) + (t2 + t3);
   }
 }
@@ -450,79 +458,121 @@ static mdp_status read_header(mdp_s* h, KrylovHeader* out, double* res2, cudaStr
   return MDP_OK;
 }
 
-template <bool U, int NB>
-static mdp_status arnoldi_step(mdp_s* h, double gamma, int j, int refine, cudaStream_t st) {
+// Typed views of the Krylov workspace: FP64 (policy rows, basis and w in double)
+// or mixed (FP32 copies of the policy rows, FP32 basis and w; the residual at
+// each restart and the iterate theta stay FP64).
+template <typename T>
+struct KrylovBuffers {
+  const T* pval;
+  T* basis;
+  T* w;
+};
+
+static KrylovBuffers<double> buffers(mdp_s* h, double*) { return {h->Ppi.val, h->basis, h->w}; }
+static KrylovBuffers<float> buffers(mdp_s* h, float*) { return {h->pval32, h->basis32, h->w32}; }
+
+template <bool U, int NB, typename T>
+static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, int refine,
+                               cudaStream_t st) {
   const Sell& Q = h->Ppi;
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
-  gm_matvec_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma, h->basis, j,
-                                                             h->w, K);
+  gm_matvec_kernel<U, T><<<h->mv_blocks, kVecThreads, 0, st>>>(B.pval, Q.col, Q.off, Q.len, k, S, gamma, B.basis, j,
+                                                                B.w, K);
   MDP_LAUNCH_CHECK(h);
-  gm_dots_kernel<NB><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+  gm_dots_kernel<NB, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
-    gm_project_kernel<NB, kPlain><<<h->mv_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+    gm_project_kernel<NB, kPlain, T><<<h->mv_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   }
   if (refine == MDP_REFINE_IFNEEDED)
-    gm_project_kernel<NB, kDgks><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+    gm_project_kernel<NB, kDgks, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   else
-    gm_project_kernel<NB, kAlways><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+    gm_project_kernel<NB, kAlways, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
-  gm_project_kernel<NB, kSecond><<<h->vec_blocks, kVecThreads, 0, st>>>(S, h->basis, j, h->w, h->partials, K);
+  gm_project_kernel<NB, kSecond, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
 
-template <bool U>
-static mdp_status arnoldi_dispatch(mdp_s* h, double gamma, int j, int refine, cudaStream_t st) {
-  if (j + 1 <= 8) return arnoldi_step<U, 8>(h, gamma, j, refine, st);
-  if (j + 1 <= 16) return arnoldi_step<U, 16>(h, gamma, j, refine, st);
-  return arnoldi_step<U, 32>(h, gamma, j, refine, st);
+template <bool U, typename T>
+static mdp_status arnoldi_dispatch(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, int refine,
+                                   cudaStream_t st) {
+  if (j + 1 <= 8) return arnoldi_step<U, 8>(h, B, gamma, j, refine, st);
+  if (j + 1 <= 16) return arnoldi_step<U, 16>(h, B, gamma, j, refine, st);
+  return arnoldi_step<U, 32>(h, B, gamma, j, refine, st);
 }
 
-template <bool U>
-static mdp_status gm_residual(mdp_s* h, double gamma, const double* theta, cudaStream_t st) {
+// FP64 residual of the policy system (the refinement residual in the mixed
+// solver), stored into basis slot 0 in the basis type.
+template <bool U, typename T>
+static mdp_status gm_residual(mdp_s* h, const KrylovBuffers<T>& B, double gamma, const double* theta,
+                              cudaStream_t st) {
   const Sell& Q = h->Ppi;
-  gm_residual_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
-                                                                gamma, theta, h->gpi, h->basis, h->partials,
-                                                                kstate(h));
+  gm_residual_kernel<U, T><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+                                                                   gamma, theta, h->gpi, B.basis, h->partials,
+                                                                   kstate(h));
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
 
-// Algorithmic work of `steps` Arnoldi steps without re-orthogonalisation (one
-// pass would do): apply P_pi with x = u_j, read the other j basis vectors for
-// the dots, write w; the projection reads w and the j+1 basis vectors and
-// writes u_{j+1}.
+// Algorithmic bytes of the inner solver: one application of P_pi reads the
+// policy's rows (value + 4 B column per entry) and its x once; the other vector
+// accesses move one element per state.
+static void add_matvec_bytes(mdp_s* h, int n, size_t value_bytes, size_t vec_bytes) {
+  const double entries = (double)h->S * (double)h->Ppi.kmax;
+  h->inner_bytes += n * (entries * (double)(value_bytes + 4) + (double)h->S * (double)vec_bytes);
+}
+
+static void add_vector_bytes(mdp_s* h, int64_t nvec, size_t vec_bytes) {
+  h->inner_bytes += (double)nvec * (double)h->S * (double)vec_bytes;
+}
+
+// Work of `steps` Arnoldi steps without re-orthogonalisation (one pass would do):
+// apply P_pi with x = u_j, read the other j basis vectors for the dots and write
+// w; the projection reads w and the j+1 basis vectors and writes u_{j+1}.  Then
+// the update (basis vectors and theta) and the FP64 residual of the restart.
+template <typename T>
 static void count_cycle(mdp_s* h, int steps) {
   for (int j = 0; j < steps; ++j) {
     h->matvecs += 1;
     h->vreads += j + (j + 2);
     h->vwrites += 2;
+    add_matvec_bytes(h, 1, sizeof(T), sizeof(T));
+    add_vector_bytes(h, j + (j + 2) + 2, sizeof(T));
   }
-  h->vreads += steps + 1;  // update: basis vectors and theta
+  h->vreads += steps + 1;
   h->vwrites += 1;
-  h->matvecs += 1;  // the residual that follows
+  add_vector_bytes(h, steps, sizeof(T));
+  add_vector_bytes(h, 2, sizeof(double));
+  h->matvecs += 1;
   h->vreads += 1;
   h->vwrites += 1;
+  add_matvec_bytes(h, 1, sizeof(double), sizeof(double));
+  add_vector_bytes(h, 1, sizeof(double));
+  add_vector_bytes(h, 1, sizeof(T));
 }
 
-template <bool U>
+template <bool U, typename T>
 static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine, double tol, int maxit,
                         int* iters, double* res2, cudaStream_t st) {
-  mdp_status r = ensure_basis(h, m + 1);
+  mdp_status r = (sizeof(T) == sizeof(double)) ? ensure_basis(h, m + 1) : ensure_mixed(h, m + 1);
   if (r != MDP_OK) return r;
+  const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
   KrylovState* K = kstate(h);
   r = init_state(h, tol, maxit, m, st);
   if (r != MDP_OK) return r;
-  r = gm_residual<U>(h, gamma, theta, st);
+  r = gm_residual<U>(h, B, gamma, theta, st);
   if (r != MDP_OK) return r;
   h->matvecs += 1;
   h->vreads += 1;
   h->vwrites += 1;
+  add_matvec_bytes(h, 1, sizeof(double), sizeof(double));
+  add_vector_bytes(h, 1, sizeof(double));
+  add_vector_bytes(h, 1, sizeof(T));
   KrylovHeader hd{};
   double rn = 0.0;
   int it_before = 0;
@@ -530,19 +580,19 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
     r = read_header(h, &hd, &rn, st);
     if (r != MDP_OK) return r;
     if (hd.flags & kSolveDone) break;
-    if (hd.it > it_before) count_cycle(h, hd.it - it_before);
+    if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
     it_before = hd.it;
     const int steps = std::min(m, maxit - hd.it);
     for (int j = 0; j < steps; ++j) {
-      r = arnoldi_dispatch<U>(h, gamma, j, refine, st);
+      r = arnoldi_dispatch<U>(h, B, gamma, j, refine, st);
       if (r != MDP_OK) return r;
     }
-    gm_update_kernel<<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, h->basis, theta, K);
+    gm_update_kernel<T><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, B.basis, theta, K);
     MDP_LAUNCH_CHECK(h);
-    r = gm_residual<U>(h, gamma, theta, st);
+    r = gm_residual<U>(h, B, gamma, theta, st);
     if (r != MDP_OK) return r;
   }
-  if (hd.it > it_before) count_cycle(h, hd.it - it_before);
+  if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
   if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
   *iters = hd.it;
   *res2 = rn;
@@ -581,6 +631,8 @@ static mdp_status richardson(mdp_s* h, double gamma, double* theta, double omega
     h->matvecs += worked;
     h->vreads += worked;
     h->vwrites += worked;
+    add_matvec_bytes(h, worked, sizeof(double), sizeof(double));
+    add_vector_bytes(h, 2 * (int64_t)worked, sizeof(double));
     if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in Richardson");
     if (hd.result == 1) MDP_CUDA(cudaMemcpyAsync(theta, h->tmp, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
@@ -603,14 +655,17 @@ mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* 
 
 size_t krylov_state_bytes() { return sizeof(KrylovState); }
 
-mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, double omega,
-                       double tol, int max_it, int* iters, double* res2, cudaStream_t st) {
+mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, int precision,
+                       double omega, double tol, int max_it, int* iters, double* res2, cudaStream_t st) {
   *iters = 0;
   *res2 = 0.0;
   const bool U = h->Ppi.uniform;
+  if (inner == MDP_GMRES && precision == MDP_PREC_MIXED)
+    return U ? gmres<true, float>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st)
+             : gmres<false, float>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st);
   if (inner == MDP_GMRES)
-    return U ? gmres<true>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st)
-             : gmres<false>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st);
+    return U ? gmres<true, double>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st)
+             : gmres<false, double>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st);
   return U ? richardson<true>(h, gamma, theta, omega, tol, max_it, iters, res2, st)
            : richardson<false>(h, gamma, theta, omega, tol, max_it, iters, res2, st);
 }

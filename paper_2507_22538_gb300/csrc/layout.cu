@@ -127,7 +127,7 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
                                       const double* __restrict__ g, const int32_t* __restrict__ pi, int64_t S, int A,
                                       double* __restrict__ pval, int32_t* __restrict__ pcol,
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
-                                      double* __restrict__ gpi) {
+                                      double* __restrict__ gpi, float* __restrict__ pval32) {
   const int64_t work = S * (int64_t)kmax;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = w % S;
@@ -147,11 +147,14 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
     if (j < n) {
       const int64_t q = r / kSlice;
       const int64_t src = (UNIFORM ? q * kSlice * (int64_t)kmax : off[q]) + (r % kSlice) + (int64_t)j * kSlice;
-      pval[dst] = sval[src];
+      const double v = sval[src];
+      pval[dst] = v;
       pcol[dst] = scol[src];
+      if (pval32) pval32[dst] = (float)v;
     } else if (UNIFORM) {
       pval[dst] = 0.0;
       pcol[dst] = 0;
+      if (pval32) pval32[dst] = 0.0f;
     }
   }
 }
@@ -221,17 +224,19 @@ static void free_sell(Sell* m) {
   *m = Sell();
 }
 
-mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st) {
+mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t st) {
   const Sell& P = h->P;
   Sell& Q = h->Ppi;
   const int64_t work = h->S * (int64_t)P.kmax;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->sm_count * 16));
   if (P.uniform)
     extract_policy_kernel<true><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
-                                                         Q.val, Q.col, Q.off, Q.len, h->gpi);
+                                                         Q.val, Q.col, Q.off, Q.len, h->gpi,
+                                                         want32 ? h->pval32 : nullptr);
   else
     extract_policy_kernel<false><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
-                                                          Q.val, Q.col, Q.off, Q.len, h->gpi);
+                                                          Q.val, Q.col, Q.off, Q.len, h->gpi,
+                                                          want32 ? h->pval32 : nullptr);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   return MDP_OK;
@@ -248,6 +253,9 @@ static void destroy_handle(mdp_s* h) {
   cudaFree(h->w);
   cudaFree(h->tmp);
   cudaFree(h->basis);
+  cudaFree(h->pval32);
+  cudaFree(h->basis32);
+  cudaFree(h->w32);
   cudaFree(h->partials);
   cudaFree(h->sc);
   cudaFree(h->resmax);
@@ -259,6 +267,19 @@ static void destroy_handle(mdp_s* h) {
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
   delete h;
+}
+
+mdp_status ensure_mixed(mdp_s* h, int nvec) {
+  if (!h->pval32) MDP_TRY(dalloc(&h->pval32, h->Ppi.nstored, "FP32 policy values"));
+  if (!h->w32) MDP_TRY(dalloc(&h->w32, h->S, "FP32 w"));
+  if (nvec > h->basis32_cap) {
+    cudaFree(h->basis32);
+    h->basis32 = nullptr;
+    h->basis32_cap = 0;
+    MDP_TRY(dalloc(&h->basis32, (size_t)nvec * (size_t)h->S, "FP32 GMRES basis"));
+    h->basis32_cap = nvec;
+  }
+  return MDP_OK;
 }
 
 mdp_status ensure_basis(mdp_s* h, int nvec) {
@@ -435,6 +456,7 @@ void mdp_default_opts(mdp_solve_opts* o) {
   o->inner = MDP_GMRES;
   o->record_timing = 0;
   o->gmres_refine = MDP_REFINE_NEVER;
+  o->precision = MDP_PREC_F64;
 }
 
 const char* mdp_last_error(void) { return g_last_error.c_str(); }

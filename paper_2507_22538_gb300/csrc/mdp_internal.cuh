@@ -73,6 +73,11 @@ struct mdp_s {
   double* tmp = nullptr;     // [S]
   double* basis = nullptr;   // [(restart + 1) * S]
   int basis_cap = 0;         // vectors allocated in basis
+  // mixed-precision inner solver: FP32 copies of the policy rows' values, FP32 basis and w
+  float* pval32 = nullptr;   // [Ppi.nstored]
+  float* basis32 = nullptr;  // [(restart + 1) * S]
+  int basis32_cap = 0;
+  float* w32 = nullptr;      // [S]
   double* partials = nullptr;  // [vec_blocks * kPartialStride]
   void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
   double* hkrylov = nullptr;   // pinned host scratch for that state [32]
@@ -84,12 +89,13 @@ struct mdp_s {
   int64_t launches = 0;
   // algorithmic work counters of the inner solver (see mdp_solve_stats)
   int64_t matvecs = 0, vreads = 0, vwrites = 0;
+  double inner_bytes = 0.0;
 };
 
 namespace mdp {
 
 // layout.cu
-mdp_status extract_policy(mdp_s* h, const int32_t* pi, cudaStream_t st);  // fill Ppi, gpi from pi
+mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t st);  // fill Ppi, gpi from pi
 
 // bellman.cu
 mdp_status configure_bellman(mdp_s* h);  // threads and grid of the Bellman sweep
@@ -97,9 +103,10 @@ mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, i
 
 // krylov.cu
 mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st);
-mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, double omega,
-                       double tol, int max_it, int* iters, double* res2, cudaStream_t st);
+mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, int precision,
+                       double omega, double tol, int max_it, int* iters, double* res2, cudaStream_t st);
 mdp_status ensure_basis(mdp_s* h, int nvec);
+mdp_status ensure_mixed(mdp_s* h, int nvec);  // FP32 policy values, basis and w for the mixed solver
 size_t krylov_state_bytes();
 
 }  // namespace mdp

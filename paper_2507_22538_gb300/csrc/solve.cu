@@ -15,7 +15,7 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
   if (!pi || !x || !y) return fail(MDP_ERR_INVALID_ARG, "null vector");
   if ((const void*)x == (const void*)y) return fail(MDP_ERR_INVALID_ARG, "x and y may not alias");
   cudaStream_t st = (cudaStream_t)stream;
-  mdp_status s = extract_policy(h, pi, st);
+  mdp_status s = extract_policy(h, pi, false, st);
   if (s != MDP_OK) return s;
   return launch_policy_apply(h, gamma, x, y, st);
 }
@@ -31,12 +31,13 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   if (max_it < 0 || !(abs_tol_2norm >= 0.0)) return fail(MDP_ERR_INVALID_ARG, "bad tolerance or iteration cap");
   cudaStream_t st = (cudaStream_t)stream;
-  mdp_status s = extract_policy(h, pi, st);
+  mdp_status s = extract_policy(h, pi, false, st);
   if (s != MDP_OK) return s;
   if (v != v0) MDP_CUDA(cudaMemcpyAsync(v, v0, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
   int it = 0;
   double r2 = 0.0;
-  s = inner_solve(h, gamma, v, inner, restart, MDP_REFINE_NEVER, omega, abs_tol_2norm, max_it, &it, &r2, st);
+  s = inner_solve(h, gamma, v, inner, restart, MDP_REFINE_NEVER, MDP_PREC_F64, omega, abs_tol_2norm, max_it, &it,
+                  &r2, st);
   MDP_CUDA(cudaStreamSynchronize(st));
   if (iters) *iters = it;
   if (res_2norm) *res_2norm = r2;
@@ -59,9 +60,17 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   if (o->gmres_refine < MDP_REFINE_NEVER || o->gmres_refine > MDP_REFINE_ALWAYS)
     return fail(MDP_ERR_INVALID_ARG, "unknown gmres_refine");
+  if (o->precision != MDP_PREC_F64 && o->precision != MDP_PREC_MIXED)
+    return fail(MDP_ERR_INVALID_ARG, "unknown precision");
+  const bool mixed = (o->precision == MDP_PREC_MIXED && o->inner == MDP_GMRES);
+  if (mixed) {
+    mdp_status s0 = ensure_mixed(h, o->gmres_restart + 1);
+    if (s0 != MDP_OK) return s0;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
+  const double ibytes0 = h->inner_bytes;
   mdp_solve_stats local;
   std::memset(&local, 0, sizeof(local));
   mdp_status status = MDP_OK;
@@ -95,7 +104,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
       break;
     }
     // step 4: the policy's rows P_pi and costs g_pi, gathered into the per-state layout
-    s = extract_policy(h, pi, st);
+    s = extract_policy(h, pi, mixed, st);
     if (s != MDP_OK) {
       status = s;
       break;
@@ -104,8 +113,8 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     int it = 0;
     double r2 = 0.0;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev2, st));
-    s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->gmres_refine, o->richardson_scale,
-                    o->alpha * res, o->max_iter_ksp, &it, &r2, st);
+    s = inner_solve(h, o->gamma, V, o->inner, o->gmres_restart, o->gmres_refine, o->precision,
+                    o->richardson_scale, o->alpha * res, o->max_iter_ksp, &it, &r2, st);
     if (s != MDP_OK) {
       status = s;
       break;
@@ -126,6 +135,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   local.policy_matvecs = h->matvecs - matvecs0;
   local.vector_reads = h->vreads - vreads0;
   local.vector_writes = h->vwrites - vwrites0;
+  local.inner_bytes = h->inner_bytes - ibytes0;
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = local;
   return status;

@@ -32,13 +32,15 @@ MDP_RICHARDSON = 1
 MDP_REFINE_NEVER = 0
 MDP_REFINE_IFNEEDED = 1
 MDP_REFINE_ALWAYS = 2
+MDP_PREC_F64 = 0
+MDP_PREC_MIXED = 1
 
 
 class mdp_solve_opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("atol_pi", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("richardson_scale", ctypes.c_double), ("max_iter_pi", ctypes.c_int32),
                 ("max_iter_ksp", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32)]
+                ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):
@@ -47,7 +49,7 @@ class mdp_solve_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double),
                 ("inner_ms", ctypes.c_double), ("policy_matvecs", ctypes.c_int64),
-                ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64)]
+                ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -241,14 +243,15 @@ class MDP:
         return v, it, res, st
 
     def solve(self, gamma, V0=None, tol=1e-8, alpha=1e-4, inner=MDP_GMRES, restart=30, omega=1.0,
-              max_outer=1000, max_inner=1000, record_timing=False, refine=MDP_REFINE_NEVER, stream=None,
-              device="cuda"):
+              max_outer=1000, max_inner=1000, record_timing=False, refine=MDP_REFINE_NEVER, precision=MDP_PREC_F64,
+              stream=None, device="cuda"):
         import torch
         o = mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.richardson_scale = gamma, tol, alpha, omega
         o.max_iter_pi, o.max_iter_ksp, o.gmres_restart, o.inner = max_outer, max_inner, restart, inner
         o.record_timing = 1 if record_timing else 0
         o.gmres_refine = refine
+        o.precision = precision
         V = torch.zeros(self.S, dtype=torch.float64, device=device) if V0 is None else V0.clone()
         pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
         st, stats = mdp_solve(self.h, o, V, pi, stream)

@@ -47,6 +47,7 @@ def test_host_only_calls(lib):
     assert (o.atol_pi, o.alpha, o.richardson_scale) == (1e-8, 1e-4, 1.0)  # Table 1 defaults
     assert (o.max_iter_pi, o.max_iter_ksp, o.gmres_restart, o.inner) == (1000, 1000, 30, mdp.MDP_GMRES)
     assert o.gmres_refine == mdp.MDP_REFINE_NEVER  # PETSc's KSPGMRES default
+    assert o.precision == mdp.MDP_PREC_F64
     # argument checks that return before touching the device
     st, h = mdp.mdp_create(0, 4, 1, 1, 1, 1, False, stream=0)
     assert st == mdp.MDP_ERR_INVALID_ARG and not h.value
@@ -57,5 +58,5 @@ def test_host_only_calls(lib):
 
 def test_struct_layouts_match_header():
     from paper_2507_22538_gb300 import mdp
-    assert ctypes.sizeof(mdp.mdp_solve_opts) == 4 * 8 + 6 * 4
-    assert ctypes.sizeof(mdp.mdp_solve_stats) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 3 * 8
+    assert ctypes.sizeof(mdp.mdp_solve_opts) == 4 * 8 + 7 * 4 + 4  # padded to 8
+    assert ctypes.sizeof(mdp.mdp_solve_stats) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 3 * 8 + 8

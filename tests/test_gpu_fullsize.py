@@ -75,3 +75,22 @@ def test_solve_full_size(workload):
     res2 = float(np.max(np.abs(Q2.min(axis=1) - V2)))
     bound = (res2 + q_tolerance(m, V2)) / (1 - m.gamma)
     assert bound <= 1e-8 * (float(np.max(np.abs(V2))) - bound)
+
+
+def test_mixed_precision_solve_full_size(workload):
+    """The mixed-precision inner solver on the full workload, bench configuration:
+    the FP64 stop test holds at the returned V and the policy is greedy for it."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = workload
+    tol = 1e-8
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol, alpha=0.01, restart=30, precision=mdp.MDP_PREC_MIXED)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.converged, stats.as_dict()
+    Vg, pg = V.cpu().numpy(), pi.cpu().numpy()
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+    rtol = q_tolerance(m, Vg)
+    assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol + rtol
+    check_policy(pg, Q, rtol)

@@ -150,3 +150,29 @@ def test_gram_schmidt_refinement_modes(refine):
         qt = q_tolerance(m, Vg)
         assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol + qt
         check_policy(pi.cpu().numpy(), Q, qt)
+
+
+@pytest.mark.parametrize("name,make,alpha,tol", [c for c in SOLVE_CASES], ids=[c[0] for c in SOLVE_CASES])
+def test_mixed_precision_solve_matches_oracle(name, make, alpha, tol):
+    """FP32 Arnoldi cycles with FP64 restart residuals (iterative refinement) reach the
+    same oracle-certified V as the FP64 path: the outer stop test stays FP64."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    from tests._util import check_policy, q_tolerance
+    m = make()
+    vn = float(np.max(np.abs(O.ipi(*_args(m), tol=tol, alpha=alpha).V)))
+    tol_p = min(tol, 0.5e-8 * (1 - m.gamma) * vn)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol_p, alpha=alpha, precision=mdp.MDP_PREC_MIXED, max_outer=300)
+        V64, _, stats64, _ = M.solve(m.gamma, tol=tol_p, alpha=alpha, max_outer=300)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.converged, stats.as_dict()
+    Vg = V.cpu().numpy()
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+    qt = q_tolerance(m, Vg)
+    assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol_p + qt
+    bound = (tol_p + qt) / (1 - m.gamma)
+    assert bound <= 1e-8 * (float(np.max(np.abs(Vg))) - bound)
+    check_policy(pi.cpu().numpy(), Q, qt)
+    assert float(np.max(np.abs(Vg - V64.cpu().numpy()))) <= 2 * bound
