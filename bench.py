@@ -76,7 +76,7 @@ def sweep_traffic():
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("bellman.cu sha256[:16]") != sha:
+    if vals.get("bellman_cu_sha256_16") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

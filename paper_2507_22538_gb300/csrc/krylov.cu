@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "mdp_internal.cuh"
 
@@ -40,10 +42,11 @@ struct KrylovState {
   double sigma[kMaxBasis + 1];            // v_i = sigma_i u_i
   double wnorm, beta, estimate, res2, tol;
   int it, maxit, m, jdone, flags, counter, result;  // result: Richardson buffer holding the answer
+  int pstride;                                       // row stride of the transposed block partials
 };
 
 struct KrylovHeader {  // host copy of the int tail of KrylovState
-  int it, maxit, m, jdone, flags, counter, result;
+  int it, maxit, m, jdone, flags, counter, result, pstride;
 };
 
 enum : int {
@@ -107,15 +110,17 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&d)[N]) {
 }
 
 // Block sums of NV per-thread values (NV a power of two) plus one extra value into
-// partials[blockIdx.x][0 .. NV] (the extra one at index NV when HAS_EXTRA); the
-// last block to finish then adds the partials of all blocks in block order into
-// out[] (shared memory) and returns true in all of its threads.  Deterministic
-// for a fixed grid.  The counter is left at zero for the next kernel.
+// partials[i * pstride + blockIdx.x] (the extra one as column NV when HAS_EXTRA);
+// the last block to finish then adds each column over all blocks in block order
+// into out[] (shared memory) and returns true in all of its threads.
+// Deterministic for a fixed grid.  The counter is left at zero for the next kernel.
 template <int NV, bool HAS_EXTRA>
-__device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ partials, int* counter, double* out) {
+__device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ partials, int pstride, int* counter,
+                         double* out) {
   constexpr int NT = NV + (HAS_EXTRA ? 1 : 0);
   constexpr int kLog = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : (NV >= 2) ? 1 : 0;
-  __shared__ double red[kVecThreads / 32][NT];
+  constexpr int kWarps = kVecThreads / 32;
+  __shared__ double red[kWarps][NT];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const double v = warp_reduce_scatter<NV>(d);
@@ -127,8 +132,8 @@ __device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ par
   __syncthreads();
   if (threadIdx.x < NT) {
     double t = 0.0;
-    for (int w = 0; w < kVecThreads / 32; ++w) t += red[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * kPartialStride + threadIdx.x] = t;
+    for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
+    partials[(int64_t)threadIdx.x * pstride + blockIdx.x] = t;
   }
   __threadfence();
   __syncthreads();
@@ -136,19 +141,34 @@ __device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ par
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  for (int i = warp; i < NT; i += kVecThreads / 32) {  // warp i adds column i over the blocks
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;       // independent loads (L2, bypassing L1)
+  // warp w adds columns w, w + 8, ...: lanes stride the blocks (coalesced rows of
+  // the transposed partials), two columns at a time with independent loads
+  const int nb = (int)gridDim.x;
+  for (int i = warp; i < NT; i += 2 * kWarps) {
+    const int i2 = i + kWarps;
+    const double* p1 = partials + (int64_t)i * pstride;
+    const double* p2 = partials + (int64_t)(i2 < NT ? i2 : i) * pstride;
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
     int b = lane;
-    for (; b + 96 < (int)gridDim.x; b += 128) {
-      v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
-      v1 += __ldcg(partials + (int64_t)(b + 32) * kPartialStride + i);
-      v2 += __ldcg(partials + (int64_t)(b + 64) * kPartialStride + i);
-      v3 += __ldcg(partials + (int64_t)(b + 96) * kPartialStride + i);
+    for (; b + 32 < nb; b += 64) {
+      a0 += __ldcg(p1 + b);
+      a1 += __ldcg(p1 + b + 32);
+      b0 += __ldcg(p2 + b);
+      b1 += __ldcg(p2 + b + 32);
     }
-    for (; b < (int)gridDim.x; b += 32) v0 += __ldcg(partials + (int64_t)b * kPartialStride + i);
-    double t = (v0 + v1) + (v2 + v3);
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) out[i] = t;
+    if (b < nb) {
+      a0 += __ldcg(p1 + b);
+      b0 += __ldcg(p2 + b);
+    }
+    double ta = a0 + a1, tb = b0 + b1;
+    for (int o = 16; o; o >>= 1) {
+      ta += __shfl_xor_sync(0xffffffffu, ta, o);
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    }
+    if (lane == 0) {
+      out[i] = ta;
+      if (i2 < NT) out[i2] = tb;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0;
@@ -220,7 +240,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
     u0[s] = (T)r;
   }
   __shared__ double out[1];
-  if (grid_sum<1, false>(d, 0.0, partials, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(d, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
     const double beta = sqrt(out[0]);
     K->res2 = beta;
     K->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -276,7 +296,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T
 #pragma unroll
   for (int i = 0; i < NB; ++i) dd[i] = (double)d[i];
   __shared__ double out[NB + 1];
-  if (grid_sum<NB, true>(dd, (double)ww, partials, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<NB, true>(dd, (double)ww, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
     for (int i = 0; i <= j; ++i) {
       const double h = K->sigma[i] * out[i];
       K->hc[i] = h;
@@ -331,10 +351,10 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, T* _
     double dd[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) dd[i] = (double)d[i];
-    last = grid_sum<NV, true>(dd, (double)uu, partials, &K->counter, out);
+    last = grid_sum<NV, true>(dd, (double)uu, partials, K->pstride, &K->counter, out);
   } else {
     double n1[1] = {(double)uu};
-    last = grid_sum<1, false>(n1, 0.0, partials, &K->counter, out);
+    last = grid_sum<1, false>(n1, 0.0, partials, K->pstride, &K->counter, out);
   }
   if (last && threadIdx.x == 0) {
     const double beta = sqrt(out[DOTS ? NV : 0]);
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __
     out[s] = fma(omega, r, th);
   }
   __shared__ double o[1];
-  if (grid_sum<1, false>(d, 0.0, partials, &K->counter, o) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(d, 0.0, partials, K->pstride, &K->counter, o) && threadIdx.x == 0) {
     const double rn = sqrt(o[0]);
     K->res2 = rn;
     if (!isfinite(rn)) {
@@ -436,12 +456,41 @@ __global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __
 
 static KrylovState* kstate(mdp_s* h) { return (KrylovState*)h->kstate; }
 
+// Grid of one full wave: as many 256-thread blocks as fit on every SM at once
+// (from the occupancy calculator, cached per kernel), but no more blocks than
+// 256-state chunks.  A partial second wave would leave most SMs idle for as long
+// as the first.
+template <typename Kern>
+static int wave_grid(mdp_s* h, Kern kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find((const void*)kernel);
+    if (it != cache.end()) {
+      per_sm = it->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVecThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+      }
+      per_sm = std::max(1, std::min(per_sm, kMaxBlocksPerSm));
+      cache[(const void*)kernel] = per_sm;
+    }
+  }
+  const int64_t chunks = (h->S + kVecThreads - 1) / kVecThreads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)h->sm_count * per_sm));
+}
+
+#define MDP_WAVE(kern) wave_grid(h, kern)  // kern in parentheses when it has template commas
+
 // Zero the device state and set tol, maxit and m (through the pinned scratch).
 static mdp_status init_state(mdp_s* h, double tol, int maxit, int m, cudaStream_t st) {
   KrylovState* K = kstate(h);
   MDP_CUDA(cudaMemsetAsync(K, 0, sizeof(KrylovState), st));
   h->hkrylov[0] = tol;
-  KrylovHeader hd{0, maxit, m, 0, 0, 0, 0};
+  KrylovHeader hd{0, maxit, m, 0, 0, 0, 0, h->partial_stride};
   std::memcpy(h->hkrylov + 2, &hd, sizeof(hd));
   MDP_CUDA(cudaMemcpyAsync(&K->tol, h->hkrylov, sizeof(double), cudaMemcpyHostToDevice, st));
   MDP_CUDA(cudaMemcpyAsync(&K->it, h->hkrylov + 2, sizeof(hd), cudaMemcpyHostToDevice, st));
@@ -478,22 +527,22 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
-  gm_matvec_kernel<U, T><<<h->mv_blocks, kVecThreads, 0, st>>>(B.pval, Q.col, Q.off, Q.len, k, S, gamma, B.basis, j,
+  gm_matvec_kernel<U, T><<<MDP_WAVE((gm_matvec_kernel<U, T>)), kVecThreads, 0, st>>>(B.pval, Q.col, Q.off, Q.len, k, S, gamma, B.basis, j,
                                                                 B.w, K);
   MDP_LAUNCH_CHECK(h);
-  gm_dots_kernel<NB, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+  gm_dots_kernel<NB, T><<<MDP_WAVE((gm_dots_kernel<NB, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
-    gm_project_kernel<NB, kPlain, T><<<h->mv_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    gm_project_kernel<NB, kPlain, T><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   }
   if (refine == MDP_REFINE_IFNEEDED)
-    gm_project_kernel<NB, kDgks, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    gm_project_kernel<NB, kDgks, T><<<MDP_WAVE((gm_project_kernel<NB, kDgks, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   else
-    gm_project_kernel<NB, kAlways, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    gm_project_kernel<NB, kAlways, T><<<MDP_WAVE((gm_project_kernel<NB, kAlways, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
-  gm_project_kernel<NB, kSecond, T><<<h->vec_blocks, kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+  gm_project_kernel<NB, kSecond, T><<<MDP_WAVE((gm_project_kernel<NB, kSecond, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
@@ -512,7 +561,7 @@ template <bool U, typename T>
 static mdp_status gm_residual(mdp_s* h, const KrylovBuffers<T>& B, double gamma, const double* theta,
                               cudaStream_t st) {
   const Sell& Q = h->Ppi;
-  gm_residual_kernel<U, T><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+  gm_residual_kernel<U, T><<<MDP_WAVE((gm_residual_kernel<U, T>)), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
                                                                    gamma, theta, h->gpi, B.basis, h->partials,
                                                                    kstate(h));
   MDP_LAUNCH_CHECK(h);
@@ -587,7 +636,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
       r = arnoldi_dispatch<U>(h, B, gamma, j, refine, st);
       if (r != MDP_OK) return r;
     }
-    gm_update_kernel<T><<<h->vec_blocks, kVecThreads, 0, st>>>(h->S, B.basis, theta, K);
+    gm_update_kernel<T><<<MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st>>>(h->S, B.basis, theta, K);
     MDP_LAUNCH_CHECK(h);
     r = gm_residual<U>(h, B, gamma, theta, st);
     if (r != MDP_OK) return r;
@@ -618,7 +667,7 @@ static mdp_status richardson(mdp_s* h, double gamma, double* theta, double omega
       const int batch = std::min(maxit - issued, issued < 8 ? 2 : 16);
       for (int b = 0; b < batch; ++b, ++issued) {
         const int in = issued & 1;
-        rich_step_kernel<U><<<h->mv_blocks, kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+        rich_step_kernel<U><<<MDP_WAVE(rich_step_kernel<U>), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
                                                                     gamma, omega, buf[in], h->gpi, buf[1 - in], in,
                                                                     h->partials, K);
         MDP_LAUNCH_CHECK(h);

@@ -419,7 +419,8 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(&h->piw, S, "policy"));
   MDP_TRY(dalloc(&h->w, S, "w"));
   MDP_TRY(dalloc(&h->tmp, S, "tmp"));
-  MDP_TRY(dalloc(&h->partials, (size_t)std::max(h->vec_blocks, h->mv_blocks) * kPartialStride, "partials"));
+  h->partial_stride = h->sm_count * kMaxBlocksPerSm;
+  MDP_TRY(dalloc(&h->partials, (size_t)kPartialRows * h->partial_stride, "partials"));
   {
     cudaError_t e = cudaMalloc(&h->kstate, krylov_state_bytes());
     if (e != cudaSuccess) {

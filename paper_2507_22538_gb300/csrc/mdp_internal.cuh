@@ -12,7 +12,8 @@ namespace mdp {
 
 constexpr int kSlice = 32;       // rows (or states) per sliced-ELL slice: one warp, one row per lane
 constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
-constexpr int kPartialStride = 40;  // per-block partial sums (up to kMaxBasis + 1 values)
+constexpr int kPartialRows = 40;    // per-block partial sums (up to kMaxBasis + 1 values), transposed
+constexpr int kMaxBlocksPerSm = 8;  // 256-thread blocks: 2048 threads per SM
 constexpr int kScalarSlots = 512;
 
 // Per-thread message of the last failure.
@@ -78,7 +79,8 @@ struct mdp_s {
   float* basis32 = nullptr;  // [(restart + 1) * S]
   int basis32_cap = 0;
   float* w32 = nullptr;      // [S]
-  double* partials = nullptr;  // [vec_blocks * kPartialStride]
+  double* partials = nullptr;  // [kPartialRows * partial_stride], row i holds value i of every block
+  int partial_stride = 0;      // sm_count * kMaxBlocksPerSm, the largest grid of a reducing kernel
   void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
   double* hkrylov = nullptr;   // pinned host scratch for that state [32]
   double* sc = nullptr;      // device scalars [kScalarSlots]
