@@ -41,7 +41,11 @@ typedef enum {
 
 typedef enum { MDP_F64 = 0 } mdp_dtype; /* storage type of the P values passed to mdp_create */
 
-typedef enum { MDP_GMRES = 0, MDP_RICHARDSON = 1 } mdp_inner;
+/* Inner solvers of Algorithm 1 (Sec. III-B.3, Table 2): restarted GMRES (the
+   default), Richardson (VI, OPI(W), beta-VI), TFQMR (used for the pendulum and
+   maze studies, Sec. IV-C/D; one half step = one iteration), and Richardson with
+   the Jacobi preconditioner D = diag(I - gamma P_pi) (J-VI). */
+typedef enum { MDP_GMRES = 0, MDP_RICHARDSON = 1, MDP_TFQMR = 2, MDP_RICHARDSON_JACOBI = 3 } mdp_inner;
 
 /* Gram-Schmidt refinement inside GMRES (the choices of PETSc's KSPGMRES, whose
    default madupite inherits, Sec. III-B.3): classical Gram-Schmidt with no second

@@ -198,6 +198,83 @@ def gmres(matvec, b, x0, restart: int, tol: float, maxit: int) -> InnerResult:
     return InnerResult(x, it, beta)
 
 
+def tfqmr(matvec, b, x0, tol: float, maxit: int) -> InnerResult:
+    """Transpose-free QMR (Freund, SIAM J. Sci. Comput. 1993), the inner solver the
+    paper uses for the pendulum and maze studies (Sec. IV-C, IV-D).
+
+    Each outer step m forms two Krylov directions (y1, y2) with two products by J
+    and takes two quasi-minimal-residual half steps.  One half step (one product
+    by J) counts as one iteration.  tau sqrt(k+1) bounds ||b - J x_k||_2 after half
+    step k (k = 1, 2, ...); the solve stops once that bound drops below tol, at
+    maxit half steps, or when rho or sigma vanish.  Returns the true residual
+    norm of the final iterate.
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - matvec(x)
+    tau = float(np.linalg.norm(r))
+    if tau < tol or maxit <= 0:
+        return InnerResult(x, 0, tau)
+    rt = r.copy()
+    w = r.copy()
+    y1 = r.copy()
+    v = matvec(y1)
+    u1 = v.copy()
+    d = np.zeros_like(x)
+    theta = eta = 0.0
+    rho = float(np.dot(rt, r))
+    k = 0
+    while k < maxit:
+        sigma = float(np.dot(rt, v))
+        if sigma == 0.0 or rho == 0.0:
+            break
+        alpha = rho / sigma
+        y2 = y1 - alpha * v
+        u2 = matvec(y2)
+        done = False
+        for half in (1, 2):
+            k += 1
+            yy, uu = (y1, u1) if half == 1 else (y2, u2)
+            w = w - alpha * uu
+            d = yy + (theta * theta * eta / alpha) * d
+            theta = float(np.linalg.norm(w)) / tau
+            c = 1.0 / math.sqrt(1.0 + theta * theta)
+            tau = tau * theta * c
+            eta = c * c * alpha
+            x = x + eta * d
+            if tau * math.sqrt(k + 1) < tol or k >= maxit:
+                done = True
+                break
+        if done:
+            break
+        rho_new = float(np.dot(rt, w))
+        beta = rho_new / rho
+        rho = rho_new
+        y1 = w + beta * y2
+        u1 = matvec(y1)
+        v = u1 + beta * (u2 + beta * v)
+    return InnerResult(x, k, float(np.linalg.norm(b - matvec(x))))
+
+
+def jacobi_richardson(matvec, diag, b, x0, omega: float, tol: float, maxit: int) -> InnerResult:
+    """Richardson with the Jacobi preconditioner D = diag(I - gamma P_pi) (Table 2, J-VI):
+    x <- x + omega D^{-1} (b - J x), stopping on the unpreconditioned ||b - J x||_2 < tol."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    it = 0
+    r = b - matvec(x)
+    rn = float(np.linalg.norm(r))
+    while rn >= tol and it < maxit:
+        x = x + omega * r / diag
+        it += 1
+        r = b - matvec(x)
+        rn = float(np.linalg.norm(r))
+    return InnerResult(x, it, rn)
+
+
+def jacobi_diagonal(Ppi, gamma: float) -> np.ndarray:
+    """Diagonal of J_pi = I - gamma P_pi: 1 - gamma P(s, s, pi(s))."""
+    return 1.0 - gamma * np.asarray(Ppi.diagonal(), dtype=np.float64)
+
+
 # --------------------------------------------------------------------------
 # Algorithm 1 and the classical methods
 # --------------------------------------------------------------------------
@@ -215,7 +292,8 @@ class SolveResult:
 def ipi(S: int, A: int, row_ptr, col, val, g, gamma: float, V0=None, tol: float = 1e-8,
         alpha: float = 1e-4, max_outer: int = 1000, max_inner: int = 1000, inner: str = "gmres",
         restart: int = 30, omega: float = 1.0) -> SolveResult:
-    """Inexact policy iteration, Algorithm 1, with the GMRES or Richardson inner solver.
+    """Inexact policy iteration, Algorithm 1, with a GMRES, TFQMR, Richardson or
+    Jacobi-preconditioned Richardson inner solver.
 
     k = 0, V = V_0.  Repeat: (TV, pi_{k+1}, res_k) = Bellman step at V_k (steps
     2-3); stop if res_k <= tol, or after max_outer evaluations; otherwise solve
@@ -240,6 +318,10 @@ def ipi(S: int, A: int, row_ptr, col, val, g, gamma: float, V0=None, tol: float 
             out = gmres(mv, gpi, V, restart, alpha * res, max_inner)
         elif inner == "richardson":
             out = richardson(mv, gpi, V, omega, alpha * res, max_inner)
+        elif inner == "tfqmr":
+            out = tfqmr(mv, gpi, V, alpha * res, max_inner)
+        elif inner == "jacobi":
+            out = jacobi_richardson(mv, jacobi_diagonal(Ppi, gamma), gpi, V, omega, alpha * res, max_inner)
         else:
             raise ValueError(inner)
         inner_its.append(out.iters)

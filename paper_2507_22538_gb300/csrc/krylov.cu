@@ -41,6 +41,8 @@ struct KrylovState {
   double coef[kMaxBasis + 1];             // projection coefficients on the stored u_i
   double sigma[kMaxBasis + 1];            // v_i = sigma_i u_i
   double wnorm, beta, estimate, res2, tol;
+  // TFQMR recurrences
+  double t_rho, t_alpha, t_beta, t_theta, t_tau, t_eta;
   int it, maxit, m, jdone, flags, counter, result;  // result: Richardson buffer holding the answer
   int pstride;                                       // row stride of the transposed block partials
 };
@@ -446,6 +448,236 @@ __global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __
   }
 }
 
+// ---- TFQMR (Freund 1993) -------------------------------------------------------------
+// Vectors (FP64, S each): rt (shadow residual r_0), w, y1, y2, u1 = J y1, u2 = J y2,
+// v, d.  One half step (one product by J) is one iteration; it counts in K->it.
+
+// r_0 = b - J x; rt = w = y1 = r_0; d = 0; tau = ||r_0||, rho = r_0 . r_0.
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) tf_init_kernel(const double* __restrict__ pval,
+                                                               const int32_t* __restrict__ pcol,
+                                                               const int64_t* __restrict__ poff,
+                                                               const int32_t* __restrict__ plen, int k, int64_t S,
+                                                               double gamma, const double* __restrict__ x,
+                                                               const double* __restrict__ b, double* __restrict__ rt,
+                                                               double* __restrict__ w, double* __restrict__ y1,
+                                                               double* __restrict__ d, double* partials,
+                                                               KrylovState* K) {
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, x);
+    const double r = b[s] - (x[s] - gamma * px);
+    rt[s] = r;
+    w[s] = r;
+    y1[s] = r;
+    d[s] = 0.0;
+    acc[0] = fma(r, r, acc[0]);
+  }
+  __shared__ double out[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+    const double tau = sqrt(out[0]);
+    K->t_tau = tau;
+    K->t_rho = out[0];
+    K->t_theta = 0.0;
+    K->t_eta = 0.0;
+    K->res2 = tau;
+    if (!isfinite(tau)) K->flags |= kNumeric | kSolveDone;
+    if (tau < K->tol || K->maxit <= 0) K->flags |= kSolveDone;
+  }
+}
+
+// y = J x with, optionally, v = y + beta (u2 + beta v) (TFQMR's v update) and u1 = y.
+template <bool U, bool VUPD>
+__global__ void __launch_bounds__(kVecThreads) tf_matvec_kernel(const double* __restrict__ pval,
+                                                                 const int32_t* __restrict__ pcol,
+                                                                 const int64_t* __restrict__ poff,
+                                                                 const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                 double gamma, const double* __restrict__ x,
+                                                                 double* __restrict__ y, const double* __restrict__ u2,
+                                                                 double* __restrict__ v, const KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  const double beta = K->t_beta;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, x);
+    const double ys = x[s] - gamma * px;
+    y[s] = ys;
+    if (VUPD) v[s] = fma(beta, fma(beta, v[s], u2[s]), ys);
+  }
+}
+
+// sigma = rt . v; alpha = rho / sigma (a zero sigma or rho ends the solve).
+__global__ void __launch_bounds__(kVecThreads) tf_sigma_kernel(int64_t S, const double* __restrict__ rt,
+                                                                const double* __restrict__ v, double* partials,
+                                                                KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
+    acc[0] = fma(rt[s], v[s], acc[0]);
+  __shared__ double out[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+    const double sigma = out[0];
+    if (sigma == 0.0 || K->t_rho == 0.0 || !isfinite(sigma)) {
+      K->flags |= kSolveDone;
+      if (!isfinite(sigma)) K->flags |= kNumeric;
+    } else {
+      K->t_alpha = K->t_rho / sigma;
+    }
+  }
+}
+
+// out = a + coef * b with coef = -alpha (y2 = y1 - alpha v) or beta (y1 = w + beta y2).
+template <bool MINUS_ALPHA>
+__global__ void __launch_bounds__(kVecThreads) tf_axpy_kernel(int64_t S, const double* __restrict__ a,
+                                                               const double* __restrict__ b, double* __restrict__ out,
+                                                               const KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  const double c = MINUS_ALPHA ? -K->t_alpha : K->t_beta;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
+    out[s] = fma(c, b[s], a[s]);
+}
+
+// One quasi-minimal-residual half step: w -= alpha u; d = y + (theta^2 eta / alpha) d;
+// then theta = ||w|| / tau, c = (1 + theta^2)^(-1/2), tau *= theta c, eta = c^2 alpha,
+// one more iteration, and the stop test tau sqrt(it + 1) < tol (or the cap).
+__global__ void __launch_bounds__(kVecThreads) tf_half_kernel(int64_t S, const double* __restrict__ y,
+                                                               const double* __restrict__ u, double* __restrict__ w,
+                                                               double* __restrict__ d, double* partials,
+                                                               KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  const double alpha = K->t_alpha;
+  const double cd = K->t_theta * K->t_theta * K->t_eta / alpha;
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double ws = fma(-alpha, u[s], w[s]);
+    w[s] = ws;
+    d[s] = fma(cd, d[s], y[s]);
+    acc[0] = fma(ws, ws, acc[0]);
+  }
+  __shared__ double out[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+    const double theta = sqrt(out[0]) / K->t_tau;
+    const double c = 1.0 / sqrt(1.0 + theta * theta);
+    K->t_theta = theta;
+    K->t_tau = K->t_tau * theta * c;
+    K->t_eta = c * c * alpha;
+    K->it += 1;
+    K->jdone = K->it;  // the x update that follows checks this
+    if (!isfinite(K->t_tau)) K->flags |= kNumeric | kSolveDone;
+    if (K->t_tau * sqrt((double)K->it + 1.0) < K->tol || K->it >= K->maxit) K->flags |= kSolveDone;
+  }
+}
+
+// x += eta d for half step number `half` (skipped when that half step did not run);
+// with RHO also rho_new = rt . w, beta = rho_new / rho (a zero rho ends the solve).
+template <bool RHO>
+__global__ void __launch_bounds__(kVecThreads) tf_xupd_kernel(int64_t S, int half, const double* __restrict__ d,
+                                                               double* __restrict__ x, const double* __restrict__ rt,
+                                                               const double* __restrict__ w, double* partials,
+                                                               KrylovState* K) {
+  const bool apply = (K->jdone == half);
+  if (!apply && (!RHO || (K->flags & kSolveDone))) return;
+  const double eta = K->t_eta;
+  const bool rho = RHO && !(K->flags & kSolveDone);
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    if (apply) x[s] = fma(eta, d[s], x[s]);
+    if (rho) acc[0] = fma(rt[s], w[s], acc[0]);
+  }
+  if (!rho) return;
+  __shared__ double out[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+    const double rn = out[0];
+    if (rn == 0.0 || !isfinite(rn)) {
+      K->flags |= kSolveDone;
+      if (!isfinite(rn)) K->flags |= kNumeric;
+    } else {
+      K->t_beta = rn / K->t_rho;
+      K->t_rho = rn;
+    }
+  }
+}
+
+// ||b - J x||_2 of the returned iterate into K->res2.
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double* __restrict__ pval,
+                                                                     const int32_t* __restrict__ pcol,
+                                                                     const int64_t* __restrict__ poff,
+                                                                     const int32_t* __restrict__ plen, int k,
+                                                                     int64_t S, double gamma,
+                                                                     const double* __restrict__ x,
+                                                                     const double* __restrict__ b, double* partials,
+                                                                     KrylovState* K) {
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, x);
+    const double r = b[s] - (x[s] - gamma * px);
+    acc[0] = fma(r, r, acc[0]);
+  }
+  __shared__ double out[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+    K->res2 = sqrt(out[0]);
+    if (!isfinite(K->res2)) K->flags |= kNumeric;
+  }
+}
+
+// One Jacobi-preconditioned Richardson step (J-VI, Table 2): r = b - J in,
+// out = in + omega r / (1 - gamma P(s, s, pi(s))).  Stop logic as rich_step_kernel.
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) jacobi_step_kernel(const double* __restrict__ pval,
+                                                                   const int32_t* __restrict__ pcol,
+                                                                   const int64_t* __restrict__ poff,
+                                                                   const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                   double gamma, double omega,
+                                                                   const double* __restrict__ pdiag,
+                                                                   const double* __restrict__ in,
+                                                                   const double* __restrict__ b,
+                                                                   double* __restrict__ out, int in_index,
+                                                                   double* partials, KrylovState* K) {
+  if (K->flags & kSolveDone) return;
+  double acc[1] = {0.0};
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, in);
+    const double th = in[s];
+    const double r = b[s] - (th - gamma * px);
+    acc[0] = fma(r, r, acc[0]);
+    out[s] = th + omega * r / (1.0 - gamma * pdiag[s]);
+  }
+  __shared__ double o[1];
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, o) && threadIdx.x == 0) {
+    const double rn = sqrt(o[0]);
+    K->res2 = rn;
+    if (!isfinite(rn)) {
+      K->flags |= kNumeric | kSolveDone;
+      K->result = in_index;
+    } else if (rn < K->tol) {
+      K->flags |= kSolveDone;
+      K->result = in_index;
+    } else {
+      K->it += 1;
+      K->result = 1 - in_index;
+      if (K->it >= K->maxit) K->flags |= kSolveDone;
+    }
+  }
+}
+
+// P(s, s, pi(s)): the self-transition entry of each policy row (0 when absent).
+template <bool U>
+__global__ void __launch_bounds__(kVecThreads) policy_diag_kernel(const double* __restrict__ pval,
+                                                                   const int32_t* __restrict__ pcol,
+                                                                   const int64_t* __restrict__ poff,
+                                                                   const int32_t* __restrict__ plen, int k, int64_t S,
+                                                                   double* __restrict__ pdiag) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = s / kSlice;
+    const int n = U ? k : plen[s];
+    const int64_t base = (U ? q * kSlice * (int64_t)k : poff[q]) + (s % kSlice);
+    double p = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (pcol[base + (int64_t)j * kSlice] == (int32_t)s) p += pval[base + (int64_t)j * kSlice];
+    pdiag[s] = p;
+  }
+}
+
 // ---- host side -------------------------------------------------------------------
 
 #define MDP_LAUNCH_CHECK(h)       \
@@ -690,6 +922,132 @@ static mdp_status richardson(mdp_s* h, double gamma, double* theta, double omega
   return MDP_OK;
 }
 
+// TFQMR on J_pi x = g_pi from x = theta: batches of outer steps (two half steps
+// each) are queued and the host waits once per batch; kernels queued after the
+// stop test return at once.
+template <bool U>
+static mdp_status tfqmr(mdp_s* h, double gamma, double* x, double tol, int maxit, int* iters, double* res2,
+                        cudaStream_t st) {
+  mdp_status r = ensure_tfqmr(h);
+  if (r != MDP_OK) return r;
+  KrylovState* K = kstate(h);
+  r = init_state(h, tol, maxit, 0, st);
+  if (r != MDP_OK) return r;
+  const Sell& Q = h->Ppi;
+  const int k = U ? Q.kmax : 0;
+  const int64_t S = h->S;
+  double* rt = h->tfq;
+  double* w = rt + S;
+  double* y1 = w + S;
+  double* y2 = y1 + S;
+  double* u1 = y2 + S;
+  double* u2 = u1 + S;
+  double* v = u2 + S;
+  double* d = v + S;
+  tf_init_kernel<U><<<MDP_WAVE(tf_init_kernel<U>), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, S, gamma, x,
+                                                                         h->gpi, rt, w, y1, d, h->partials, K);
+  MDP_LAUNCH_CHECK(h);
+  tf_matvec_kernel<U, false><<<MDP_WAVE((tf_matvec_kernel<U, false>)), kVecThreads, 0, st>>>(
+      Q.val, Q.col, Q.off, Q.len, k, S, gamma, y1, v, nullptr, nullptr, K);
+  MDP_LAUNCH_CHECK(h);
+  MDP_CUDA(cudaMemcpyAsync(u1, v, S * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  add_matvec_bytes(h, 2, sizeof(double), sizeof(double));
+  KrylovHeader hd{};
+  double rn = 0.0;
+  int half = 0;  // half steps queued so far
+  for (;;) {
+    r = read_header(h, &hd, &rn, st);
+    if (r != MDP_OK) return r;
+    if ((hd.flags & kSolveDone) || half >= maxit) break;
+    const int outer = std::max(1, std::min(8, (maxit - half + 1) / 2));
+    for (int q = 0; q < outer; ++q) {
+      tf_sigma_kernel<<<MDP_WAVE(tf_sigma_kernel), kVecThreads, 0, st>>>(S, rt, v, h->partials, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_axpy_kernel<true><<<MDP_WAVE(tf_axpy_kernel<true>), kVecThreads, 0, st>>>(S, y1, v, y2, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_matvec_kernel<U, false><<<MDP_WAVE((tf_matvec_kernel<U, false>)), kVecThreads, 0, st>>>(
+          Q.val, Q.col, Q.off, Q.len, k, S, gamma, y2, u2, nullptr, nullptr, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_half_kernel<<<MDP_WAVE(tf_half_kernel), kVecThreads, 0, st>>>(S, y1, u1, w, d, h->partials, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_xupd_kernel<false><<<MDP_WAVE(tf_xupd_kernel<false>), kVecThreads, 0, st>>>(S, ++half, d, x, rt, w,
+                                                                                    h->partials, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_half_kernel<<<MDP_WAVE(tf_half_kernel), kVecThreads, 0, st>>>(S, y2, u2, w, d, h->partials, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_xupd_kernel<true><<<MDP_WAVE(tf_xupd_kernel<true>), kVecThreads, 0, st>>>(S, ++half, d, x, rt, w,
+                                                                                  h->partials, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_axpy_kernel<false><<<MDP_WAVE(tf_axpy_kernel<false>), kVecThreads, 0, st>>>(S, w, y2, y1, K);
+      MDP_LAUNCH_CHECK(h);
+      tf_matvec_kernel<U, true><<<MDP_WAVE((tf_matvec_kernel<U, true>)), kVecThreads, 0, st>>>(
+          Q.val, Q.col, Q.off, Q.len, k, S, gamma, y1, u1, u2, v, K);
+      MDP_LAUNCH_CHECK(h);
+      if (half >= maxit) break;
+    }
+  }
+  true_residual_kernel<U><<<MDP_WAVE(true_residual_kernel<U>), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k,
+                                                                                     S, gamma, x, h->gpi,
+                                                                                     h->partials, K);
+  MDP_LAUNCH_CHECK(h);
+  r = read_header(h, &hd, &rn, st);
+  if (r != MDP_OK) return r;
+  // per half step: one product by J (12 B/entry + x) and about six vector accesses
+  add_matvec_bytes(h, hd.it + 1, sizeof(double), sizeof(double));
+  add_vector_bytes(h, 6 * (int64_t)hd.it + 2, sizeof(double));
+  h->matvecs += hd.it + 3;
+  if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in TFQMR");
+  *iters = hd.it;
+  *res2 = rn;
+  return MDP_OK;
+}
+
+// Richardson with the Jacobi preconditioner (J-VI): as richardson() with the
+// step scaled by 1 / (1 - gamma P(s, s, pi(s))).
+template <bool U>
+static mdp_status jacobi_richardson(mdp_s* h, double gamma, double* theta, double omega, double tol, int maxit,
+                                    int* iters, double* res2, cudaStream_t st) {
+  mdp_status r = ensure_tfqmr(h);  // its first vector holds the diagonal
+  if (r != MDP_OK) return r;
+  KrylovState* K = kstate(h);
+  r = init_state(h, tol, maxit, 0, st);
+  if (r != MDP_OK) return r;
+  const Sell& Q = h->Ppi;
+  const int k = U ? Q.kmax : 0;
+  double* pdiag = h->tfq;
+  policy_diag_kernel<U><<<MDP_WAVE(policy_diag_kernel<U>), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, k, h->S,
+                                                                                 pdiag);
+  MDP_LAUNCH_CHECK(h);
+  double* buf[2] = {theta, h->tmp};
+  KrylovHeader hd{};
+  double rn = INFINITY;
+  int issued = 0;
+  if (maxit > 0) {
+    for (;;) {
+      const int batch = std::min(maxit - issued, issued < 8 ? 2 : 16);
+      for (int b = 0; b < batch; ++b, ++issued) {
+        const int in = issued & 1;
+        jacobi_step_kernel<U><<<MDP_WAVE(jacobi_step_kernel<U>), kVecThreads, 0, st>>>(
+            Q.val, Q.col, Q.off, Q.len, k, h->S, gamma, omega, pdiag, buf[in], h->gpi, buf[1 - in], in, h->partials,
+            K);
+        MDP_LAUNCH_CHECK(h);
+      }
+      r = read_header(h, &hd, &rn, st);
+      if (r != MDP_OK) return r;
+      if ((hd.flags & kSolveDone) || issued >= maxit) break;
+    }
+    const int worked = hd.it + ((hd.flags & kSolveDone) && hd.it < maxit ? 1 : 0);
+    h->matvecs += worked;
+    add_matvec_bytes(h, worked, sizeof(double), sizeof(double));
+    add_vector_bytes(h, 3 * (int64_t)worked, sizeof(double));
+    if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in Jacobi-Richardson");
+    if (hd.result == 1) MDP_CUDA(cudaMemcpyAsync(theta, h->tmp, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  *iters = maxit > 0 ? hd.it : 0;
+  *res2 = rn;
+  return MDP_OK;
+}
+
 mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st) {
   const Sell& Q = h->Ppi;
   if (Q.uniform)
@@ -715,6 +1073,12 @@ mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int res
   if (inner == MDP_GMRES)
     return U ? gmres<true, double>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st)
              : gmres<false, double>(h, gamma, theta, restart, refine, tol, max_it, iters, res2, st);
+  if (inner == MDP_TFQMR)
+    return U ? tfqmr<true>(h, gamma, theta, tol, max_it, iters, res2, st)
+             : tfqmr<false>(h, gamma, theta, tol, max_it, iters, res2, st);
+  if (inner == MDP_RICHARDSON_JACOBI)
+    return U ? jacobi_richardson<true>(h, gamma, theta, omega, tol, max_it, iters, res2, st)
+             : jacobi_richardson<false>(h, gamma, theta, omega, tol, max_it, iters, res2, st);
   return U ? richardson<true>(h, gamma, theta, omega, tol, max_it, iters, res2, st)
            : richardson<false>(h, gamma, theta, omega, tol, max_it, iters, res2, st);
 }

@@ -256,6 +256,7 @@ static void destroy_handle(mdp_s* h) {
   cudaFree(h->pval32);
   cudaFree(h->basis32);
   cudaFree(h->w32);
+  cudaFree(h->tfq);
   cudaFree(h->partials);
   cudaFree(h->sc);
   cudaFree(h->resmax);
@@ -279,6 +280,11 @@ mdp_status ensure_mixed(mdp_s* h, int nvec) {
     MDP_TRY(dalloc(&h->basis32, (size_t)nvec * (size_t)h->S, "FP32 GMRES basis"));
     h->basis32_cap = nvec;
   }
+  return MDP_OK;
+}
+
+mdp_status ensure_tfqmr(mdp_s* h) {
+  if (!h->tfq) MDP_TRY(dalloc(&h->tfq, (size_t)8 * (size_t)h->S, "TFQMR vectors"));
   return MDP_OK;
 }
 

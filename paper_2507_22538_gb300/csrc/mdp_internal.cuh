@@ -79,6 +79,7 @@ struct mdp_s {
   float* basis32 = nullptr;  // [(restart + 1) * S]
   int basis32_cap = 0;
   float* w32 = nullptr;      // [S]
+  double* tfq = nullptr;     // TFQMR vectors [8 * S] (the first also holds the Jacobi diagonal)
   double* partials = nullptr;  // [kPartialRows * partial_stride], row i holds value i of every block
   int partial_stride = 0;      // sm_count * kMaxBlocksPerSm, the largest grid of a reducing kernel
   void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
@@ -109,6 +110,7 @@ mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int res
                        double omega, double tol, int max_it, int* iters, double* res2, cudaStream_t st);
 mdp_status ensure_basis(mdp_s* h, int nvec);
 mdp_status ensure_mixed(mdp_s* h, int nvec);  // FP32 policy values, basis and w for the mixed solver
+mdp_status ensure_tfqmr(mdp_s* h);            // TFQMR / Jacobi work vectors
 size_t krylov_state_bytes();
 
 }  // namespace mdp

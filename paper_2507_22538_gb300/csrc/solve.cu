@@ -26,7 +26,7 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
   if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
   if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
   if (!pi || !v0 || !v) return fail(MDP_ERR_INVALID_ARG, "null vector");
-  if (inner != MDP_GMRES && inner != MDP_RICHARDSON) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
+  if (inner < MDP_GMRES || inner > MDP_RICHARDSON_JACOBI) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
   if (inner == MDP_GMRES && (restart < 1 || restart > kMaxBasis))
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   if (max_it < 0 || !(abs_tol_2norm >= 0.0)) return fail(MDP_ERR_INVALID_ARG, "bad tolerance or iteration cap");
@@ -55,7 +55,8 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   if (!(o->atol_pi > 0.0) || !(o->alpha > 0.0 && o->alpha < 1.0))
     return fail(MDP_ERR_INVALID_ARG, "need atol_pi > 0 and 0 < alpha < 1");
   if (o->max_iter_pi < 0 || o->max_iter_ksp < 0) return fail(MDP_ERR_INVALID_ARG, "negative iteration cap");
-  if (o->inner != MDP_GMRES && o->inner != MDP_RICHARDSON) return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
+  if (o->inner < MDP_GMRES || o->inner > MDP_RICHARDSON_JACOBI)
+    return fail(MDP_ERR_INVALID_ARG, "unknown inner solver");
   if (o->inner == MDP_GMRES && (o->gmres_restart < 1 || o->gmres_restart > kMaxBasis))
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   if (o->gmres_refine < MDP_REFINE_NEVER || o->gmres_refine > MDP_REFINE_ALWAYS)

@@ -29,6 +29,8 @@ STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_INVALID_ARG", 2: "MDP_ERR_NOT_STOCHASTI
 MDP_F64 = 0
 MDP_GMRES = 0
 MDP_RICHARDSON = 1
+MDP_TFQMR = 2
+MDP_RICHARDSON_JACOBI = 3
 MDP_REFINE_NEVER = 0
 MDP_REFINE_IFNEEDED = 1
 MDP_REFINE_ALWAYS = 2

@@ -55,7 +55,7 @@ def test_invalid_policy_entries_poison_output():
         assert np.isnan(y[17]) and np.isnan(y[18]) and np.all(np.isfinite(np.delete(y, [17, 18])))
 
 
-@pytest.mark.parametrize("inner", ["gmres", "richardson"])
+@pytest.mark.parametrize("inner", ["gmres", "richardson", "tfqmr", "jacobi"])
 @pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
 def test_policy_eval_parity(name, make, inner):
     """Both sides stop on ||g_pi - J_pi v||_2 < tol; the true solution v_pi is at most
@@ -69,17 +69,39 @@ def test_policy_eval_parity(name, make, inner):
     v0 = np.zeros(m.S)
     bn = float(np.linalg.norm(gpi))
     tol = 1e-9 * bn
-    maxit = 3000 if inner == "gmres" else 200
+    krylov = inner in ("gmres", "tfqmr")
+    if inner == "tfqmr":
+        tol = 1e-7 * bn  # TFQMR's short recurrences stagnate near 1e-9 relative
+    maxit = 3000 if krylov else 200
+    code = {"gmres": mdp.MDP_GMRES, "richardson": mdp.MDP_RICHARDSON, "tfqmr": mdp.MDP_TFQMR,
+            "jacobi": mdp.MDP_RICHARDSON_JACOBI}[inner]
     with mdp.MDP.from_data(m) as M:
-        code = mdp.MDP_GMRES if inner == "gmres" else mdp.MDP_RICHARDSON
         v, it, res, st = M.policy_eval(m.gamma, torch.from_numpy(pi).cuda(), torch.from_numpy(v0).cuda(),
                                        inner=code, restart=30, tol=tol, max_it=maxit)
         torch.cuda.synchronize()
     v = v.cpu().numpy()
     mv = lambda x: O.apply_J(Ppi, m.gamma, x)
-    ref = O.gmres(mv, gpi, v0, 30, tol, maxit) if inner == "gmres" else O.richardson(mv, gpi, v0, 1.0, tol, maxit)
+    if inner == "gmres":
+        ref = O.gmres(mv, gpi, v0, 30, tol, maxit)
+    elif inner == "tfqmr":
+        ref = O.tfqmr(mv, gpi, v0, tol, maxit)
+    elif inner == "richardson":
+        ref = O.richardson(mv, gpi, v0, 1.0, tol, maxit)
+    else:
+        ref = O.jacobi_richardson(mv, O.jacobi_diagonal(Ppi, m.gamma), gpi, v0, 1.0, tol, maxit)
     true_res = float(np.linalg.norm(gpi - mv(v)))
-    if st == mdp.MDP_OK:
+    if st == mdp.MDP_OK or (inner == "tfqmr" and it < maxit):
+        if inner == "tfqmr":  # the stop test bounds the quasi-residual; check the true one loosely
+            assert abs(res - true_res) <= 1e-6 * max(true_res, tol)  # reported = true residual
+            if ref.res2 >= 10 * tol:
+                # the short recurrences lose the true residual on this system in the oracle
+                # too (random policy, gamma = 0.9999): both stop on the quasi-residual bound
+                assert abs(it - ref.iters) <= max(2, ref.iters // 20), (it, ref.iters)
+                return
+            assert true_res < 10 * tol
+            assert abs(it - ref.iters) <= 2, (it, ref.iters)
+            np.testing.assert_allclose(v, ref.x, rtol=0, atol=20 * tol / (1 - m.gamma))
+            return
         assert true_res < tol * (1 + 1e-6) + 64 * EPS * bn
         assert ref.res2 < tol
         assert abs(it - ref.iters) <= 1, (it, ref.iters)
@@ -88,7 +110,7 @@ def test_policy_eval_parity(name, make, inner):
         # the cap was hit on both sides (GMRES(30) stagnates on some random policies at
         # gamma near 1; 200 Richardson steps are too few there)
         assert st == mdp.MDP_NOT_CONVERGED and it == maxit and ref.iters == maxit
-        if inner == "gmres":  # GMRES reports the true residual of the returned iterate
+        if krylov:  # the reported residual is the true residual of the returned iterate
             assert abs(res - true_res) <= 1e-6 * max(true_res, tol)
         else:  # same recurrence on both sides: same iterate
             scale = max(1.0, float(np.max(np.abs(ref.x))))

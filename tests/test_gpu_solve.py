@@ -176,3 +176,85 @@ def test_mixed_precision_solve_matches_oracle(name, make, alpha, tol):
     assert bound <= 1e-8 * (float(np.max(np.abs(Vg))) - bound)
     check_policy(pi.cpu().numpy(), Q, qt)
     assert float(np.max(np.abs(Vg - V64.cpu().numpy()))) <= 2 * bound
+
+
+
+TFQMR_CASES = [
+    ("c1_random_s1000_a4_k8", lambda: random_sparse(1000, 4, 8, 0.9, seed=1), 1e-3, 1e-10),
+    ("banded_s5000_a20_k33", lambda: banded_birth_death(5000, 20, 16, 0.999), 0.01, 1e-8),
+    ("pendulum_60x60_a9_g0999", lambda: pendulum_grid(60, 60, 9, 0.999, seed=3), 1e-3, 1e-8),
+    ("pendulum_40x40_a9_g09999", lambda: pendulum_grid(40, 40, 9, 0.9999, seed=3), 1e-3, 1e-8),
+    ("maze_40x40", lambda: maze(40, 40, 0.2, seed=7, gamma=0.99)[0], 1e-4, 1e-8),
+]
+
+
+@pytest.mark.parametrize("name,make,alpha,tol", TFQMR_CASES, ids=[c[0] for c in TFQMR_CASES])
+def test_tfqmr_solve_certified_by_oracle(name, make, alpha, tol):
+    """iPI with the TFQMR inner solver (the paper's choice for the pendulum and maze,
+    Sec. IV-C/D), including pendulum grids where GMRES(30) stalls: the oracle's
+    Bellman residual at the returned V certifies it."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    from tests._util import check_policy, q_tolerance
+    m = make()
+    ref = O.ipi(*_args(m), tol=tol, alpha=alpha, inner="tfqmr", max_inner=5000)
+    assert ref.converged
+    vn = float(np.max(np.abs(ref.V)))
+    tol_p = min(tol, 0.5e-8 * (1 - m.gamma) * vn)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol_p, alpha=alpha, inner=mdp.MDP_TFQMR, max_inner=5000, max_outer=500)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.converged, stats.as_dict()
+    Vg = V.cpu().numpy()
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+    qt = q_tolerance(m, Vg)
+    assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol_p + qt
+    bound = (tol_p + qt) / (1 - m.gamma)
+    assert bound <= 1e-8 * (float(np.max(np.abs(Vg))) - bound)
+    check_policy(pi.cpu().numpy(), Q, qt)
+
+
+def test_maze_bfs_closed_form_on_gpu():
+    """GPU iPI (TFQMR) on the maze reproduces V*(s) = -100 gamma^d(s) / (1 - gamma)."""
+    import collections
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    H, W = 33, 33
+    m, free_idx, goal = maze(H, W, 0.25, seed=11, gamma=0.99)
+    wall = np.ones(H * W, dtype=bool)
+    wall[free_idx] = False
+    dist = np.full(H * W, -1)
+    dist[(H - 1) * W + W - 1] = 0
+    q = collections.deque([(H - 1) * W + W - 1])
+    while q:
+        c = q.popleft()
+        y, x = divmod(c, W)
+        for dy, dx in ((-1, 0), (0, 1), (1, 0), (0, -1)):
+            ny, nx = y + dy, x + dx
+            if 0 <= ny < H and 0 <= nx < W and not wall[ny * W + nx] and dist[ny * W + nx] < 0:
+                dist[ny * W + nx] = dist[c] + 1
+                q.append(ny * W + nx)
+    d = dist[free_idx]
+    expect = np.where(d >= 0, -100.0 * m.gamma ** np.maximum(d, 0) / (1 - m.gamma), 0.0)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-9, alpha=1e-4, inner=mdp.MDP_TFQMR, max_inner=5000)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK
+    np.testing.assert_allclose(V.cpu().numpy(), expect, atol=1e-9 / (1 - m.gamma) + 1e-10 * 1e4)
+
+
+@pytest.mark.parametrize("make", [lambda: random_sparse(1000, 4, 8, 0.9, seed=1),
+                                  lambda: banded_birth_death(3000, 20, 16, 0.99)], ids=["c1", "banded"])
+def test_jacobi_vi_configuration(make):
+    """J-VI (Table 2): Jacobi-preconditioned Richardson, one step per evaluation, against the oracle's run."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = make()
+    ref = O.ipi(*_args(m), tol=1e-9, alpha=0.5, inner="jacobi", max_inner=1, max_outer=100000)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=1e-9, alpha=0.5, inner=mdp.MDP_RICHARDSON_JACOBI, max_inner=1,
+                                   max_outer=100000)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and abs(stats.outer_iters - ref.outer_iters) <= 1
+    np.testing.assert_allclose(V.cpu().numpy(), ref.V, rtol=0, atol=1e-9 / (1 - m.gamma))

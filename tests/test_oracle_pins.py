@@ -303,3 +303,64 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
     elif mutant == "inner_sign":
         monkeypatch.setattr(O, "apply_J", lambda Ppi, gamma, x: x + gamma * (Ppi @ x))
     assert not _pins_hold()
+
+
+# ---------------------------------------------------------------- TFQMR and Jacobi (Sec. IV-C/D, Table 2)
+
+def test_tfqmr_solves_policy_system():
+    """TFQMR reaches the dense solution of (I - gamma P_pi) v = g_pi to its attainable
+    accuracy (short recurrences stagnate near 1e-9 relative here), counting half steps."""
+    m = random_sparse(200, 3, 6, 0.97, seed=8)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    pi = (np.arange(m.S) * 5) % m.A
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    exact = np.linalg.solve(np.eye(m.S) - m.gamma * Ppi.toarray(), gpi)
+    mv = lambda x: O.apply_J(Ppi, m.gamma, x)
+    bn = float(np.linalg.norm(gpi))
+    out = O.tfqmr(mv, gpi, np.zeros(m.S), 1e-8 * bn, 5000)
+    assert out.res2 < 1e-7 * bn
+    np.testing.assert_allclose(out.x, exact, atol=1e-7 * bn / (1 - m.gamma))
+    for cap in (1, 2, 3, 7, 20):
+        assert O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, cap).iters == cap
+    r10, r40 = (O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, c).res2 for c in (10, 40))
+    assert r40 < 1e-3 * r10
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ipi_tfqmr_and_jacobi_match_brute_force(seed):
+    rng = np.random.default_rng(50 + seed)
+    S, A = int(rng.integers(2, 6)), int(rng.integers(1, 4))
+    m = random_sparse(S, A, int(rng.integers(1, S + 1)), float(rng.choice([0.5, 0.9, 0.99])), seed=200 + seed)
+    Vb, optimal, _ = O.brute_force(*_args(m))
+    scale = max(1.0, np.abs(Vb).max())
+    for inner in ("tfqmr", "jacobi"):
+        r = O.ipi(*_args(m), tol=1e-12 * scale, alpha=1e-3, inner=inner, max_inner=5000)
+        assert r.converged
+        np.testing.assert_allclose(r.V, Vb, atol=1e-10 * scale)
+        assert tuple(r.pi) in optimal
+
+
+def test_maze_tfqmr_bfs_closed_form():
+    """The maze study's solver choice (TFQMR, Sec. IV-D) on the BFS closed form."""
+    H, W = 9, 13
+    m, free_idx, goal = maze(H, W, wall_frac=0.25, seed=5, gamma=0.9)
+    wall = np.ones(H * W, dtype=bool)
+    wall[free_idx] = False
+    dist = _bfs_distance(H, W, wall, (H - 1) * W + (W - 1))[free_idx]
+    expect = np.where(dist >= 0, -100.0 * m.gamma ** np.maximum(dist, 0) / (1 - m.gamma), 0.0)
+    r = O.ipi(*_args(m), tol=1e-11, alpha=1e-4, inner="tfqmr")
+    np.testing.assert_allclose(r.V, expect, atol=1e-8)
+
+
+def test_jacobi_diagonal_and_one_step_identity():
+    """J-VI (Table 2): one Jacobi-preconditioned step is x + D^{-1} (T_pi x - x)."""
+    m = random_sparse(60, 2, 60, 0.9, seed=3)  # dense rows: every state has a self-transition
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    pi = np.arange(m.S) % m.A
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    D = O.jacobi_diagonal(Ppi, m.gamma)
+    dense = Ppi.toarray()
+    np.testing.assert_allclose(D, 1 - m.gamma * np.diag(dense), atol=0)
+    x = random_value_vector(m.S, 2, 1.0)
+    out = O.jacobi_richardson(lambda v: O.apply_J(Ppi, m.gamma, v), D, gpi, x, 1.0, 0.0, 1)
+    np.testing.assert_allclose(out.x, x + (O.policy_operator(Ppi, gpi, m.gamma, x) - x) / D, atol=1e-13)
