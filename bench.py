@@ -177,6 +177,41 @@ def run_reference(args):
     return 0
 
 
+def run_serving(n, slots=4, seed=5):
+    """Continuous-batching measurement: n requests of mixed S (log-uniform 1e3..1e5),
+    A (2..16), k (4..32) and gamma (0.9..0.9999), Poisson arrivals at 0.8 of the
+    one-at-a-time rate, admitted by a 120 GB HBM budget into `slots` concurrent solves."""
+    import numpy as np
+
+    from mdpgen import serving_request
+    from paper_2507_22538_gb300.serve import (Request, SolveService, fifo_one_at_a_time, latency_summary,
+                                              solve_alone)
+    mix = dict(s_range=(1_000, 100_000), a_range=(2, 16), k_range=(4, 32), gammas=(0.9, 0.99, 0.999, 0.9999))
+    reqs = [Request(i, serving_request(i, seed=seed, **mix), tol=1e-8, alpha=1e-3) for i in range(n)]
+    solve_alone(reqs[0])  # warm-up
+    alone = [solve_alone(r) for r in reqs]
+    service = np.array([a.finished for a in alone])
+    rate = 0.8 / float(service.mean())
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    svc = SolveService(slots=slots, hbm_budget=120 << 30).start()
+    t0 = svc.now()
+    for r, a in zip(reqs, arrivals):
+        wait = t0 + a - svc.now()
+        if wait > 0:
+            time.sleep(wait)
+        svc.submit(r)
+    res = svc.wait(n)
+    svc.close()
+    same = all(np.array_equal(alone[r.rid].V, res[r.rid].V) and np.array_equal(alone[r.rid].pi, res[r.rid].pi)
+               for r in reqs)
+    return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
+            "mix": "S log-uniform 1e3..1e5, A 2..16, k 4..32, gamma in {0.9,0.99,0.999,0.9999}, GMRES(30), "
+                   "alpha 1e-3, tol 1e-8",
+            "continuous": latency_summary(res), "one_at_a_time": fifo_one_at_a_time(arrivals, service),
+            "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same)}
+
+
 def run_bellman_only(args):
     """Time mdp_bellman alone on the banded workload (any size), one JSON line."""
     import torch
@@ -250,6 +285,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", type=int, default=64, metavar="N",
+                    help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
                     help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
     ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only: number of states")
@@ -407,6 +444,8 @@ def main():
                            "max_final_residual": totals["final_residual"]},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks}
+    if args.serve > 0:
+        line["serving"] = run_serving(args.serve)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, info = cpu_oracle_solve()
         line["cpu_baseline"] = {"value": t, "unit": "s", "cores": 1, "kind": "oracle",

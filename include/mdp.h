@@ -120,7 +120,10 @@ mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_
                       mdp_dtype val_type, const double* g, int32_t inputs_on_device, void* stream,
                       mdp_handle* out);
 
-/* Release every device and host resource of the handle (NULL is accepted). */
+/* Release every device and host resource of the handle (NULL is accepted).  Waits
+   for the work of the handle's last call, then returns its memory to the
+   stream-ordered pool without synchronising the device; calls on one handle must
+   be ordered by the caller (one stream, or events between streams). */
 mdp_status mdp_destroy(mdp_handle h);
 
 /* Problem sizes of a handle (any out pointer may be NULL). */

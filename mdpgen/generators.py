@@ -314,6 +314,29 @@ def maze(H: int, W: int, wall_frac: float = 0.2, seed: int = 7, gamma: float = 0
     return MDPData(S, A, row_ptr, col, val, g, gamma, f"maze({H}x{W})"), free_idx, goal
 
 
+def serving_request(rid: int, seed: int = 5, s_range=(1_000, 1_000_000), a_range=(2, 32), k_range=(4, 64),
+                    gammas=(0.9, 0.99, 0.999, 0.9999)) -> MDPData:
+    """One request of a serving stream: S log-uniform in s_range, A and k uniform in
+    their ranges (k fixed over the request's rows), gamma drawn from `gammas`,
+    k uniform columns per row (drawn with replacement, sorted; a repeated column
+    simply adds its probabilities), Dirichlet(1) probabilities, costs U[0, 1).
+    Drawn from numpy's PCG64 seeded with (seed, rid), so any request is reproducible
+    alone."""
+    rng = np.random.Generator(np.random.PCG64([seed, rid]))
+    lo, hi = math.log(s_range[0]), math.log(s_range[1])
+    S = int(round(math.exp(rng.uniform(lo, hi))))
+    A = int(rng.integers(a_range[0], a_range[1] + 1))
+    k = int(min(S, rng.integers(k_range[0], k_range[1] + 1)))
+    gamma = float(gammas[int(rng.integers(0, len(gammas)))])
+    R = S * A
+    col = np.sort(rng.integers(0, S, size=(R, k), dtype=np.int32), axis=1).ravel()
+    w = rng.exponential(1.0, size=(R, k)) + 1e-12
+    val = (w / w.sum(axis=1, keepdims=True)).ravel()
+    g = rng.random(R)
+    row_ptr = np.arange(R + 1, dtype=np.int64) * k
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"request{rid}(S={S},A={A},k={k},gamma={gamma})")
+
+
 def random_value_vector(S: int, seed: int, scale: float = 1.0) -> np.ndarray:
     """A seeded test vector V ~ scale * U[-1, 1) of length S."""
     u = stream(seed, TAG_NOISE ^ 0x5A5A, np.arange(S, dtype=np.uint64), np.uint64(1))

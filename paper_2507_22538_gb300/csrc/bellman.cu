@@ -142,5 +142,6 @@ extern "C" mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, d
   if (s != MDP_OK) return s;
   if (residual_inf)
     MDP_CUDA(cudaMemcpyAsync(residual_inf, h->resmax, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  MDP_CUDA(cudaEventRecord(h->done, st));
   return MDP_OK;
 }

@@ -720,22 +720,25 @@ static int wave_grid(mdp_s* h, Kern kernel) {
 // Zero the device state and set tol, maxit and m (through the pinned scratch).
 static mdp_status init_state(mdp_s* h, double tol, int maxit, int m, cudaStream_t st) {
   KrylovState* K = kstate(h);
+  double* pin = tls_pinned();
   MDP_CUDA(cudaMemsetAsync(K, 0, sizeof(KrylovState), st));
-  h->hkrylov[0] = tol;
+  pin[32] = tol;
   KrylovHeader hd{0, maxit, m, 0, 0, 0, 0, h->partial_stride};
-  std::memcpy(h->hkrylov + 2, &hd, sizeof(hd));
-  MDP_CUDA(cudaMemcpyAsync(&K->tol, h->hkrylov, sizeof(double), cudaMemcpyHostToDevice, st));
-  MDP_CUDA(cudaMemcpyAsync(&K->it, h->hkrylov + 2, sizeof(hd), cudaMemcpyHostToDevice, st));
+  std::memcpy(pin + 34, &hd, sizeof(hd));
+  MDP_CUDA(cudaMemcpyAsync(&K->tol, pin + 32, sizeof(double), cudaMemcpyHostToDevice, st));
+  MDP_CUDA(cudaMemcpyAsync(&K->it, pin + 34, sizeof(hd), cudaMemcpyHostToDevice, st));
+  MDP_CUDA(cudaStreamSynchronize(st));  // the pinned words are reused by the next call
   return MDP_OK;
 }
 
 static mdp_status read_header(mdp_s* h, KrylovHeader* out, double* res2, cudaStream_t st) {
   KrylovState* K = kstate(h);
-  MDP_CUDA(cudaMemcpyAsync(h->hkrylov + 8, &K->it, sizeof(KrylovHeader), cudaMemcpyDeviceToHost, st));
-  MDP_CUDA(cudaMemcpyAsync(h->hkrylov + 16, &K->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  double* pin = tls_pinned();
+  MDP_CUDA(cudaMemcpyAsync(pin + 40, &K->it, sizeof(KrylovHeader), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaMemcpyAsync(pin + 48, &K->res2, sizeof(double), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaStreamSynchronize(st));
-  std::memcpy(out, h->hkrylov + 8, sizeof(KrylovHeader));
-  *res2 = h->hkrylov[16];
+  std::memcpy(out, pin + 40, sizeof(KrylovHeader));
+  *res2 = pin[48];
   return MDP_OK;
 }
 

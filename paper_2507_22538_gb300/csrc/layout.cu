@@ -165,17 +165,35 @@ static int grid_for(int64_t n, int threads, int sm_count) {
   return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
+double* tls_pinned() {
+  static thread_local double* buf = nullptr;
+  if (!buf && cudaMallocHost((void**)&buf, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    buf = nullptr;
+  }
+  return buf;
+}
+
+// Device memory comes from the stream-ordered pool on the handle's creation
+// stream (no device-wide synchronisation, so handles of concurrent solves can be
+// created and destroyed while others run).
 template <typename T>
-static mdp_status dalloc(T** p, size_t count, const char* what) {
+static mdp_status dalloc(mdp_s* h, T** p, size_t count, const char* what) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), h->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
     return fail(MDP_ERR_OOM, std::string("device allocation failed: ") + what);
   }
   return MDP_OK;
+}
+
+template <typename T>
+static void dfree(cudaStream_t st, T*& p) {
+  if (p) cudaFreeAsync((void*)p, st);
+  p = nullptr;
 }
 
 #define MDP_TRY(x)                     \
@@ -195,32 +213,32 @@ static mdp_status build_sell(mdp_s* h, Sell* m, const int32_t* dlen, int64_t row
     m->nstored = m->nslices * kSlice * (int64_t)kmax;
   } else {
     int32_t* dwidth = nullptr;
-    MDP_TRY(dalloc(&dwidth, m->nslices, "slice widths"));
+    MDP_TRY(dalloc(h, &dwidth, m->nslices, "slice widths"));
     slice_width_kernel<<<grid_for(m->nslices, 256, h->sm_count), 256, 0, st>>>(dlen, rows, m->nslices, dwidth);
     h->launches++;
     std::vector<int32_t> width(m->nslices);
     cudaError_t e = cudaMemcpyAsync(width.data(), dwidth, m->nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(dwidth);
+    dfree(st, dwidth);
     if (e != cudaSuccess) return cuda_fail(e, "slice widths");
     std::vector<int64_t> off(m->nslices + 1);
     off[0] = 0;
     for (int64_t q = 0; q < m->nslices; ++q) off[q + 1] = off[q] + (int64_t)width[q] * kSlice;
     m->nstored = off[m->nslices];
-    MDP_TRY(dalloc(&m->off, m->nslices + 1, "slice offsets"));
+    MDP_TRY(dalloc(h, &m->off, m->nslices + 1, "slice offsets"));
     MDP_CUDA(cudaMemcpyAsync(m->off, off.data(), (m->nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    MDP_TRY(dalloc(&m->len, rows, "row lengths"));
+    MDP_TRY(dalloc(h, &m->len, rows, "row lengths"));
   }
-  MDP_TRY(dalloc(&m->val, m->nstored, "sliced values"));
-  MDP_TRY(dalloc(&m->col, m->nstored, "sliced columns"));
+  MDP_TRY(dalloc(h, &m->val, m->nstored, "sliced values"));
+  MDP_TRY(dalloc(h, &m->col, m->nstored, "sliced columns"));
   return MDP_OK;
 }
 
-static void free_sell(Sell* m) {
-  cudaFree(m->off);
-  cudaFree(m->len);
-  cudaFree(m->val);
-  cudaFree(m->col);
+static void free_sell(cudaStream_t st, Sell* m) {
+  dfree(st, m->off);
+  dfree(st, m->len);
+  dfree(st, m->val);
+  dfree(st, m->col);
   *m = Sell();
 }
 
@@ -242,58 +260,60 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
   return MDP_OK;
 }
 
+// Frees go to the legacy stream, ordered after everything the caller already
+// completed; the caller makes sure no work on the handle is still in flight.
 static void destroy_handle(mdp_s* h) {
   if (!h) return;
-  free_sell(&h->P);
-  free_sell(&h->Ppi);
-  cudaFree(h->g);
-  cudaFree(h->gpi);
-  cudaFree(h->TV);
-  cudaFree(h->piw);
-  cudaFree(h->w);
-  cudaFree(h->tmp);
-  cudaFree(h->basis);
-  cudaFree(h->pval32);
-  cudaFree(h->basis32);
-  cudaFree(h->w32);
-  cudaFree(h->tfq);
-  cudaFree(h->partials);
-  cudaFree(h->sc);
-  cudaFree(h->resmax);
-  if (h->hpin) cudaFreeHost(h->hpin);
-  if (h->hkrylov) cudaFreeHost(h->hkrylov);
-  cudaFree(h->kstate);
+  if (h->done) cudaEventSynchronize(h->done);  // the last call's work has finished
+  const cudaStream_t st = 0;
+  free_sell(st, &h->P);
+  free_sell(st, &h->Ppi);
+  dfree(st, h->g);
+  dfree(st, h->gpi);
+  dfree(st, h->TV);
+  dfree(st, h->piw);
+  dfree(st, h->w);
+  dfree(st, h->tmp);
+  dfree(st, h->basis);
+  dfree(st, h->pval32);
+  dfree(st, h->basis32);
+  dfree(st, h->w32);
+  dfree(st, h->tfq);
+  dfree(st, h->partials);
+  dfree(st, h->sc);
+  dfree(st, h->resmax);
+  char* ks = (char*)h->kstate;
+  dfree(st, ks);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
+  if (h->done) cudaEventDestroy(h->done);
   delete h;
 }
 
 mdp_status ensure_mixed(mdp_s* h, int nvec) {
-  if (!h->pval32) MDP_TRY(dalloc(&h->pval32, h->Ppi.nstored, "FP32 policy values"));
-  if (!h->w32) MDP_TRY(dalloc(&h->w32, h->S, "FP32 w"));
+  if (!h->pval32) MDP_TRY(dalloc(h, &h->pval32, h->Ppi.nstored, "FP32 policy values"));
+  if (!h->w32) MDP_TRY(dalloc(h, &h->w32, h->S, "FP32 w"));
   if (nvec > h->basis32_cap) {
-    cudaFree(h->basis32);
-    h->basis32 = nullptr;
+    dfree(h->stream, h->basis32);
     h->basis32_cap = 0;
-    MDP_TRY(dalloc(&h->basis32, (size_t)nvec * (size_t)h->S, "FP32 GMRES basis"));
+    MDP_TRY(dalloc(h, &h->basis32, (size_t)nvec * (size_t)h->S, "FP32 GMRES basis"));
     h->basis32_cap = nvec;
   }
   return MDP_OK;
 }
 
 mdp_status ensure_tfqmr(mdp_s* h) {
-  if (!h->tfq) MDP_TRY(dalloc(&h->tfq, (size_t)8 * (size_t)h->S, "TFQMR vectors"));
+  if (!h->tfq) MDP_TRY(dalloc(h, &h->tfq, (size_t)8 * (size_t)h->S, "TFQMR vectors"));
   return MDP_OK;
 }
 
 mdp_status ensure_basis(mdp_s* h, int nvec) {
   if (nvec <= h->basis_cap) return MDP_OK;
-  cudaFree(h->basis);
-  h->basis = nullptr;
+  dfree(h->stream, h->basis);
   h->basis_cap = 0;
-  MDP_TRY(dalloc(&h->basis, (size_t)nvec * (size_t)h->S, "GMRES basis"));
+  MDP_TRY(dalloc(h, &h->basis, (size_t)nvec * (size_t)h->S, "GMRES basis"));
   h->basis_cap = nvec;
   return MDP_OK;
 }
@@ -301,6 +321,7 @@ mdp_status ensure_basis(mdp_s* h, int nvec) {
 static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
                               mdp_dtype val_type, const double* g, int32_t on_device, cudaStream_t st,
                               mdp_s* h) {
+  h->stream = st;
   MDP_CUDA(cudaGetDevice(&h->device));
   MDP_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
   h->S = S;
@@ -327,13 +348,13 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   int32_t* tcol = nullptr;
   double* tval = nullptr;
   struct Temps {
-    int64_t** a; int32_t** b; double** c;
-    ~Temps() { cudaFree(*a); cudaFree(*b); cudaFree(*c); }
-  } temps{&trp, &tcol, &tval};
+    cudaStream_t st; int64_t** a; int32_t** b; double** c;
+    ~Temps() { dfree(st, *a); dfree(st, *b); dfree(st, *c); }
+  } temps{st, &trp, &tcol, &tval};
   if (!on_device) {
-    MDP_TRY(dalloc(&trp, R + 1, "row pointers"));
-    MDP_TRY(dalloc(&tcol, nnz, "columns"));
-    MDP_TRY(dalloc(&tval, nnz, "values"));
+    MDP_TRY(dalloc(h, &trp, R + 1, "row pointers"));
+    MDP_TRY(dalloc(h, &tcol, nnz, "columns"));
+    MDP_TRY(dalloc(h, &tval, nnz, "values"));
     MDP_CUDA(cudaMemcpyAsync(trp, row_ptr, (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MDP_CUDA(cudaMemcpyAsync(tcol, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     MDP_CUDA(cudaMemcpyAsync(tval, val, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -341,16 +362,15 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
     dcol = tcol;
     dval = tval;
   }
-  MDP_TRY(dalloc(&h->g, R, "stage costs"));
+  MDP_TRY(dalloc(h, &h->g, R, "stage costs"));
   MDP_CUDA(cudaMemcpyAsync(h->g, g, R * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
 
   // validation (flags, kmin, kmax live in the scalar area)
-  MDP_TRY(dalloc(&h->sc, kScalarSlots, "scalars"));
-  MDP_TRY(dalloc(&h->resmax, 1, "residual"));
-  MDP_CUDA(cudaMallocHost((void**)&h->hpin, kScalarSlots * sizeof(double)));
+  MDP_TRY(dalloc(h, &h->sc, kScalarSlots, "scalars"));
+  MDP_TRY(dalloc(h, &h->resmax, 1, "residual"));
   int32_t* dlen = nullptr;
-  MDP_TRY(dalloc(&dlen, R, "row lengths"));
-  struct FreeLen { int32_t** p; ~FreeLen() { cudaFree(*p); } } free_len{&dlen};
+  MDP_TRY(dalloc(h, &dlen, R, "row lengths"));
+  struct FreeLen { cudaStream_t st; int32_t** p; ~FreeLen() { dfree(st, *p); } } free_len{st, &dlen};
   int* dflags = (int*)h->sc;
   int init[3] = {0, 0x7fffffff, 0};
   MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
@@ -389,12 +409,11 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
     MDP_TRY(build_sell(h, &h->Ppi, dlen, S, kmax, kmax, st));
   } else {
     int32_t* smax = nullptr;
-    MDP_TRY(dalloc(&smax, S, "state max length"));
+    MDP_TRY(dalloc(h, &smax, S, "state max length"));
     state_maxlen_kernel<<<grid_for(S, 256, h->sm_count), 256, 0, st>>>(dlen, S, A, smax);
     h->launches++;
     mdp_status s2 = build_sell(h, &h->Ppi, smax, S, 0, kmax, st);
-    MDP_CUDA(cudaStreamSynchronize(st));
-    cudaFree(smax);
+    dfree(st, smax);
     MDP_TRY(s2);
   }
 
@@ -420,26 +439,24 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
     h->bell_tile_states = (int)ts;
     MDP_TRY(configure_bellman(h));
   }
-  MDP_TRY(dalloc(&h->gpi, S, "g_pi"));
-  MDP_TRY(dalloc(&h->TV, S, "TV"));
-  MDP_TRY(dalloc(&h->piw, S, "policy"));
-  MDP_TRY(dalloc(&h->w, S, "w"));
-  MDP_TRY(dalloc(&h->tmp, S, "tmp"));
+  MDP_TRY(dalloc(h, &h->gpi, S, "g_pi"));
+  MDP_TRY(dalloc(h, &h->TV, S, "TV"));
+  MDP_TRY(dalloc(h, &h->piw, S, "policy"));
+  MDP_TRY(dalloc(h, &h->w, S, "w"));
+  MDP_TRY(dalloc(h, &h->tmp, S, "tmp"));
   h->partial_stride = h->sm_count * kMaxBlocksPerSm;
-  MDP_TRY(dalloc(&h->partials, (size_t)kPartialRows * h->partial_stride, "partials"));
+  MDP_TRY(dalloc(h, &h->partials, (size_t)kPartialRows * h->partial_stride, "partials"));
   {
-    cudaError_t e = cudaMalloc(&h->kstate, krylov_state_bytes());
-    if (e != cudaSuccess) {
-      h->kstate = nullptr;
-      cudaGetLastError();
-      return fail(MDP_ERR_OOM, "device allocation failed: solver state");
-    }
+    char* ks = nullptr;
+    MDP_TRY(dalloc(h, &ks, krylov_state_bytes(), "solver state"));
+    h->kstate = ks;
   }
-  MDP_CUDA(cudaMallocHost((void**)&h->hkrylov, 32 * sizeof(double)));
+  if (!tls_pinned()) return fail(MDP_ERR_OOM, "pinned host allocation failed");
   MDP_CUDA(cudaEventCreate(&h->ev0));
   MDP_CUDA(cudaEventCreate(&h->ev1));
   MDP_CUDA(cudaEventCreate(&h->ev2));
   MDP_CUDA(cudaEventCreate(&h->ev3));
+  MDP_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
   MDP_CUDA(cudaStreamSynchronize(st));
   return MDP_OK;
 }
@@ -495,7 +512,6 @@ mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_
 
 mdp_status mdp_destroy(mdp_handle h) {
   if (!h) return MDP_OK;
-  cudaDeviceSynchronize();
   destroy_handle(h);
   return MDP_OK;
 }

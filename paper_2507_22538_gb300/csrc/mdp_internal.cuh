@@ -83,12 +83,12 @@ struct mdp_s {
   double* partials = nullptr;  // [kPartialRows * partial_stride], row i holds value i of every block
   int partial_stride = 0;      // sm_count * kMaxBlocksPerSm, the largest grid of a reducing kernel
   void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
-  double* hkrylov = nullptr;   // pinned host scratch for that state [32]
   double* sc = nullptr;      // device scalars [kScalarSlots]
   unsigned long long* resmax = nullptr;  // device max of |TV - V| bits
-  double* hpin = nullptr;    // pinned host scalars [kScalarSlots]
+  cudaStream_t stream = nullptr;         // stream of mdp_create: device memory is allocated on it
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after the work of every call; mdp_destroy waits on it
   int64_t launches = 0;
   // algorithmic work counters of the inner solver (see mdp_solve_stats)
   int64_t matvecs = 0, vreads = 0, vwrites = 0;
@@ -96,6 +96,10 @@ struct mdp_s {
 };
 
 namespace mdp {
+
+// Pinned host scratch of the calling thread (64 doubles), for small stream-ordered
+// copies of scalars; allocated once per host thread.
+double* tls_pinned();
 
 // layout.cu
 mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t st);  // fill Ppi, gpi from pi

@@ -17,7 +17,10 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
   cudaStream_t st = (cudaStream_t)stream;
   mdp_status s = extract_policy(h, pi, false, st);
   if (s != MDP_OK) return s;
-  return launch_policy_apply(h, gamma, x, y, st);
+  s = launch_policy_apply(h, gamma, x, y, st);
+  if (s != MDP_OK) return s;
+  MDP_CUDA(cudaEventRecord(h->done, st));
+  return MDP_OK;
 }
 
 mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const double* v0, double* v,
@@ -38,6 +41,7 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
   double r2 = 0.0;
   s = inner_solve(h, gamma, v, inner, restart, MDP_REFINE_NEVER, MDP_PREC_F64, omega, abs_tol_2norm, max_it, &it,
                   &r2, st);
+  MDP_CUDA(cudaEventRecord(h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   if (iters) *iters = it;
   if (res_2norm) *res_2norm = r2;
@@ -83,9 +87,10 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     if (s != MDP_OK) return s;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev1, st));
     local.bellman_sweeps++;
-    MDP_CUDA(cudaMemcpyAsync(h->hpin, h->resmax, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double* pin = tls_pinned();
+    MDP_CUDA(cudaMemcpyAsync(pin, h->resmax, sizeof(double), cudaMemcpyDeviceToHost, st));
     MDP_CUDA(cudaStreamSynchronize(st));
-    const double res = h->hpin[0];
+    const double res = pin[0];
     if (o->record_timing) {
       float ms = 0.f;
       MDP_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -130,6 +135,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     local.inner_iters_total += it;
     ++k;
   }
+  MDP_CUDA(cudaEventRecord(h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   local.outer_iters = k;
   local.kernel_launches = h->launches - launches0;
