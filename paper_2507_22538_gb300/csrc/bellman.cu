@@ -128,20 +128,3 @@ mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, i
 }
 
 }  // namespace mdp
-
-using namespace mdp;
-
-extern "C" mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
-                                  double* residual_inf, void* stream) {
-  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
-  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
-  if (!V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
-  if ((const void*)V == (const void*)TV) return fail(MDP_ERR_INVALID_ARG, "V and TV may not alias");
-  cudaStream_t st = (cudaStream_t)stream;
-  mdp_status s = launch_bellman(h, gamma, V, TV, pi, st);
-  if (s != MDP_OK) return s;
-  if (residual_inf)
-    MDP_CUDA(cudaMemcpyAsync(residual_inf, h->resmax, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  MDP_CUDA(cudaEventRecord(h->done, st));
-  return MDP_OK;
-}

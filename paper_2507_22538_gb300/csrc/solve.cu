@@ -1,4 +1,4 @@
-// Entry points for policy evaluation and for Algorithm 1 (inexact policy iteration).
+// Entry points: the Bellman application, policy evaluation and Algorithm 1 (inexact policy iteration).
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -8,6 +8,20 @@
 using namespace mdp;
 
 extern "C" {
+mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
+                                  double* residual_inf, void* stream) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
+  if (!V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
+  if ((const void*)V == (const void*)TV) return fail(MDP_ERR_INVALID_ARG, "V and TV may not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  mdp_status s = launch_bellman(h, gamma, V, TV, pi, st);
+  if (s != MDP_OK) return s;
+  if (residual_inf)
+    MDP_CUDA(cudaMemcpyAsync(residual_inf, h->resmax, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  MDP_CUDA(cudaEventRecord(h->done, st));
+  return MDP_OK;
+}
 
 mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const double* x, double* y, void* stream) {
   if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");

@@ -12,7 +12,6 @@ kernels; this module only schedules.
 from __future__ import annotations
 
 import dataclasses
-import queue
 import threading
 import time
 
@@ -154,6 +153,10 @@ class SolveService:
             admitted = self.now()
             try:
                 res = self._solve(req, stream)
+            except Exception as exc:  # a failed request still completes, with its status
+                status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
+                res = Result(req.rid, status, np.empty(0), np.empty(0, dtype=np.int32), 0, 0, float("nan"),
+                             req.arrival, 0.0, 0.0)
             finally:
                 with self._cv:
                     self._free += need
