@@ -134,6 +134,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -160,12 +170,12 @@ def run_reference(args):
     times = []
     info = None
     for i in range(args.warmup + args.steps):
-        t, info = cpu_oracle_solve()
+        t, info = cpu_oracle_solve(args.reference_div)
         if i >= args.warmup:
             times.append(t)
     v = sum(times) / len(times)
-    sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the S={S // CPU_SAMPLE_DIV} "
-              f"instance of the same generator (same A, k, gamma, tol, alpha), wall time x{CPU_SAMPLE_DIV} "
+    sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the S={S // args.reference_div} "
+              f"instance of the same generator (same A, k, gamma, tol, alpha), wall time x{args.reference_div} "
               f"(cost is linear in S at fixed iteration counts); last run {info}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
@@ -284,6 +294,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--reference-div", type=int, default=CPU_SAMPLE_DIV,
+                    help="the CPU oracle solves the workload's generator at S / this and scales the time back")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", type=int, default=64, metavar="N",
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
@@ -357,11 +369,7 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     clocks = clk.summary()
 
     # the same solves with the mixed-precision inner solver (FP32 Arnoldi, FP64 refinement)
@@ -406,10 +414,8 @@ def main():
         if i:  # the first pass is a warm-up
             e2e_times.append(time.perf_counter() - t0)
     e2e = sum(e2e_times) / len(e2e_times) if e2e_times else None
-    if dist and e2e is not None:
-        t = torch.tensor([e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    if e2e is not None:
+        e2e = max_over_ranks(e2e, dist, "cuda")
 
     peak, peak_kind = load_peaks()
     sweeps = totals["bellman_sweeps"]

@@ -91,20 +91,20 @@ __device__ __forceinline__ TX policy_row_dot(const TP* __restrict__ pval, const 
 // instead of 5 N for N separate shuffle trees; the last levels, once a lane
 // carries one value, are plain butterflies.  Returns the warp sum of value
 // index (lane >> (5 - log2 N)) in every lane.
-template <int N>
-__device__ __forceinline__ double warp_reduce_scatter(double (&d)[N]) {
+template <int N, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&d)[N]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int half = N / 2, o = 16; half >= 1; half /= 2, o /= 2) {
     const bool upper = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
-      const double keep = upper ? d[i + half] : d[i];
-      const double send = upper ? d[i] : d[i + half];
+      const T keep = upper ? d[i + half] : d[i];
+      const T send = upper ? d[i] : d[i + half];
       d[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
-  double v = d[0];
+  T v = d[0];
   constexpr int kSplitLevels = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
 #pragma unroll
   for (int o = 16 >> kSplitLevels; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -116,8 +116,8 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&d)[N]) {
 // the last block to finish then adds each column over all blocks in block order
 // into out[] (shared memory) and returns true in all of its threads.
 // Deterministic for a fixed grid.  The counter is left at zero for the next kernel.
-template <int NV, bool HAS_EXTRA>
-__device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ partials, int pstride, int* counter,
+template <int NV, bool HAS_EXTRA, typename TW>
+__device__ bool grid_sum(TW (&d)[NV], double extra, double* __restrict__ partials, int pstride, int* counter,
                          double* out) {
   constexpr int NT = NV + (HAS_EXTRA ? 1 : 0);
   constexpr int kLog = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : (NV >= 2) ? 1 : 0;
@@ -125,7 +125,7 @@ __device__ bool grid_sum(double (&d)[NV], double extra, double* __restrict__ par
   __shared__ double red[kWarps][NT];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const double v = warp_reduce_scatter<NV>(d);
+  const double v = (double)warp_reduce_scatter<NV>(d);  // the warp stage runs in the threads' type
   if ((lane & ((1 << (5 - kLog)) - 1)) == 0) red[warp][lane >> (5 - kLog)] = v;
   if (HAS_EXTRA) {
     for (int o = 16; o; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o);
@@ -294,11 +294,8 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T
       if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
     ww = fma(ws, ws, ww);
   }
-  double dd[NB];  // per-thread partials widen to double for the block and grid sums
-#pragma unroll
-  for (int i = 0; i < NB; ++i) dd[i] = (double)d[i];
-  __shared__ double out[NB + 1];
-  if (grid_sum<NB, true>(dd, (double)ww, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  __shared__ double out[NB + 1];  // warp sums in T, block and grid sums in double
+  if (grid_sum<NB, true>(d, (double)ww, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
     for (int i = 0; i <= j; ++i) {
       const double h = K->sigma[i] * out[i];
       K->hc[i] = h;
@@ -350,12 +347,9 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, T* _
   __shared__ double out[NV + 1];
   bool last;
   if (DOTS) {
-    double dd[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) dd[i] = (double)d[i];
-    last = grid_sum<NV, true>(dd, (double)uu, partials, K->pstride, &K->counter, out);
+    last = grid_sum<NV, true>(d, (double)uu, partials, K->pstride, &K->counter, out);
   } else {
-    double n1[1] = {(double)uu};
+    T n1[1] = {uu};
     last = grid_sum<1, false>(n1, 0.0, partials, K->pstride, &K->counter, out);
   }
   if (last && threadIdx.x == 0) {
@@ -377,12 +371,15 @@ __global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, T* _
   }
 }
 
-// theta += sum_{i < jdone} y_i v_i, where every block solves R y = e by back substitution.
+// theta += sum_{i < jdone} y_i v_i, where every block solves R y = e by back
+// substitution.  The correction is accumulated in the basis type (binary32 in
+// the mixed solver, whose corrections only need that precision) and added to
+// theta in binary64.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const T* __restrict__ basis,
                                                                  double* __restrict__ theta, KrylovState* K) {
   if (K->flags & kSolveDone) return;
-  __shared__ double c[kMaxBasis];
+  __shared__ T c[kMaxBasis];
   const int n = K->jdone;
   if (threadIdx.x == 0) {
     double y[kMaxBasis];
@@ -391,20 +388,20 @@ __global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const
       for (int q = i + 1; q < n; ++q) t -= K->H[i * kMaxBasis + q] * y[q];
       y[i] = t / K->H[i * kMaxBasis + i];
     }
-    for (int i = 0; i < n; ++i) c[i] = y[i] * K->sigma[i];
+    for (int i = 0; i < n; ++i) c[i] = (T)(y[i] * K->sigma[i]);
   }
   __syncthreads();
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
-    double t0 = theta[s], t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    T t0 = T(0), t1 = T(0), t2 = T(0), t3 = T(0);
     int i = 0;
     for (; i + 4 <= n; i += 4) {
-      t0 = fma(c[i], (double)basis[(int64_t)i * S + s], t0);
-      t1 = fma(c[i + 1], (double)basis[(int64_t)(i + 1) * S + s], t1);
-      t2 = fma(c[i + 2], (double)basis[(int64_t)(i + 2) * S + s], t2);
-      t3 = fma(c[i + 3], (double)basis[(int64_t)(i + 3) * S + s], t3);
+      t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
+      t1 = fma(c[i + 1], basis[(int64_t)(i + 1) * S + s], t1);
+      t2 = fma(c[i + 2], basis[(int64_t)(i + 2) * S + s], t2);
+      t3 = fma(c[i + 3], basis[(int64_t)(i + 3) * S + s], t3);
     }
-    for (; i < n; ++i) t0 = fma(c[i], (double)basis[(int64_t)i * S + s], t0);
-    theta[s] = (t0 + t1) + (t2 + t3);
+    for (; i < n; ++i) t0 = fma(c[i], basis[(int64_t)i * S + s], t0);
+    theta[s] += (double)((t0 + t1) + (t2 + t3));
   }
 }
 
@@ -693,7 +690,7 @@ static KrylovState* kstate(mdp_s* h) { return (KrylovState*)h->kstate; }
 // 256-state chunks.  A partial second wave would leave most SMs idle for as long
 // as the first.
 template <typename Kern>
-static int wave_grid(mdp_s* h, Kern kernel) {
+static int wave_grid(mdp_s* h, Kern kernel, int max_per_sm = kMaxBlocksPerSm) {
   static std::mutex mu;
   static std::unordered_map<const void*, int> cache;
   int per_sm = 0;
@@ -712,10 +709,11 @@ static int wave_grid(mdp_s* h, Kern kernel) {
     }
   }
   const int64_t chunks = (h->S + kVecThreads - 1) / kVecThreads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)h->sm_count * per_sm));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)h->sm_count * std::min(per_sm, max_per_sm)));
 }
 
 #define MDP_WAVE(kern) wave_grid(h, kern)  // kern in parentheses when it has template commas
+
 
 // Zero the device state and set tol, maxit and m (through the pinned scratch).
 static mdp_status init_state(mdp_s* h, double tol, int maxit, int m, cudaStream_t st) {
