@@ -297,6 +297,8 @@ def main():
     ap.add_argument("--reference-div", type=int, default=CPU_SAMPLE_DIV,
                     help="the CPU oracle solves the workload's generator at S / this and scales the time back")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quantized", dest="quantized", action="store_false",
+                    help="skip the binary16-exact variant of the workload")
     ap.add_argument("--serve", type=int, default=64, metavar="N",
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
@@ -391,13 +393,51 @@ def main():
     torch.cuda.synchronize()
     mixed_ms = e0.elapsed_time(e1) / args.steps
 
+    # the quantised variant of the workload (binomial band rounded to multiples of 2^-11 so
+    # that every probability is exact in binary16): FP64 path vs mixed path with binary16
+    # policy rows, both on the same quantised MDP
+    quant = None
+    if args.quantized:
+        M.close()
+        mq = banded_birth_death(S, A, H, GAMMA, quant_bits=11)
+        Mq = mdp.MDP.from_data(mq, stream)
+
+        def qstep(o):
+            V.zero_()
+            st, stats = mdp.mdp_solve(Mq.h, o, V, pi, stream)
+            mdp.check(st, "mdp_solve")
+            return stats.as_dict()
+
+        quant = {}
+        for name, o in (("f64", opts), ("mixed", mopts)):
+            for _ in range(args.warmup):
+                qstep(o)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            its = []
+            for _ in range(args.steps):
+                s = qstep(o)
+                its.append((s["outer_iters"], s["inner_iters_total"], s["policy_value_bytes"], s["final_residual"]))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            quant[name] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "outer": its[-1][0],
+                           "inner": its[-1][1], "policy_value_bytes": its[-1][2],
+                           "max_final_residual": max(i[3] for i in its)}
+        quant["speedup_mixed_vs_f64"] = quant["f64"]["ms_per_step"] / quant["mixed"]["ms_per_step"]
+        quant["what"] = ("banded workload with the band's probabilities rounded to multiples of 2^-11 "
+                         "(exact in binary16); the mixed path reads binary16 policy rows")
+        Mq.close()
+        del mq
+        M = None
+
     # end to end through the C ABI from pinned host buffers: upload + layout + solve + read back
     pinned = {k: torch.from_numpy(getattr(m, k)).pin_memory() for k in ("row_ptr", "col", "val", "g")}
     h2d = sum(int(t.numel() * t.element_size()) for t in pinned.values())
     Vh = torch.empty(S, dtype=torch.float64).pin_memory()
     pih = torch.empty(S, dtype=torch.int32).pin_memory()
     d2h = S * 8 + S * 4
-    M.close()
+    if M is not None:
+        M.close()
     torch.cuda.synchronize()
     e2e_times = []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
@@ -445,6 +485,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
             "roofline": roofline, "roofline_inner": inner_roof, "mixed_precision": mixed,
+            "mixed_precision_binary16": quant,
             "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
                            "inner_per_step": totals["inner_iters_total"] / args.steps,
                            "max_final_residual": totals["final_residual"]},

@@ -93,6 +93,9 @@ typedef struct {
                                  the P_pi applications (each counts its x once) */
   int64_t vector_writes;      /* length-S double vectors the inner kernels write */
   double inner_bytes;         /* algorithmic bytes the inner kernels must move, in their storage types */
+  int32_t policy_value_bytes; /* bytes per probability the inner mat-vecs read: 8 (binary64), or with
+                                 MDP_PREC_MIXED 4 (binary32) or 2 (binary16 / bfloat16, used when every
+                                 probability of the MDP is exactly representable there) */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -79,9 +79,9 @@ __device__ __forceinline__ TX policy_row_dot(const TP* __restrict__ pval, const 
       c[u] = cp[(int64_t)(j + u) * kSlice];
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc = fma((TX)v[u], __ldg(x + c[u]), acc);
+    for (int u = 0; u < 8; ++u) acc = fma(static_cast<TX>(v[u]), __ldg(x + c[u]), acc);
   }
-  for (; j < n; ++j) acc = fma((TX)vp[(int64_t)j * kSlice], __ldg(x + cp[(int64_t)j * kSlice]), acc);
+  for (; j < n; ++j) acc = fma(static_cast<TX>(vp[(int64_t)j * kSlice]), __ldg(x + cp[(int64_t)j * kSlice]), acc);
   return acc;
 }
 
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
 // Arnoldi step, part 1: w = J v_j = sigma_j (u_j - gamma P_pi u_j).  A lean
 // kernel (no reductions, few registers) so that enough warps are resident to
 // keep the row and gather loads of P_pi in flight.
-template <bool U, typename T>
-__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const T* __restrict__ pval,
+template <bool U, typename TP, typename T>
+__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const TP* __restrict__ pval,
                                                                  const int32_t* __restrict__ pcol,
                                                                  const int64_t* __restrict__ poff,
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
@@ -745,13 +745,37 @@ static mdp_status read_header(mdp_s* h, KrylovHeader* out, double* res2, cudaStr
 // each restart and the iterate theta stay FP64).
 template <typename T>
 struct KrylovBuffers {
-  const T* pval;
+  const void* pval;  // double (FP64 solver); float, binary16 or bfloat16 per h->pstore (mixed solver)
   T* basis;
   T* w;
 };
 
 static KrylovBuffers<double> buffers(mdp_s* h, double*) { return {h->Ppi.val, h->basis, h->w}; }
-static KrylovBuffers<float> buffers(mdp_s* h, float*) { return {h->pval32, h->basis32, h->w32}; }
+static KrylovBuffers<float> buffers(mdp_s* h, float*) {
+  return {h->pstore == kStoreF32 ? (const void*)h->pval32 : (const void*)h->pval16, h->basis32, h->w32};
+}
+
+template <bool U, typename T>
+static mdp_status launch_matvec(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, cudaStream_t st) {
+  const Sell& Q = h->Ppi;
+  const int k = U ? Q.kmax : 0;
+  KrylovState* K = kstate(h);
+  if (sizeof(T) == sizeof(double)) {
+    gm_matvec_kernel<U, T, T><<<MDP_WAVE((gm_matvec_kernel<U, T, T>)), kVecThreads, 0, st>>>(
+        (const T*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+  } else if (h->pstore == kStoreF16) {
+    gm_matvec_kernel<U, __half, T><<<MDP_WAVE((gm_matvec_kernel<U, __half, T>)), kVecThreads, 0, st>>>(
+        (const __half*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+  } else if (h->pstore == kStoreBF16) {
+    gm_matvec_kernel<U, __nv_bfloat16, T><<<MDP_WAVE((gm_matvec_kernel<U, __nv_bfloat16, T>)), kVecThreads, 0, st>>>(
+        (const __nv_bfloat16*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+  } else {
+    gm_matvec_kernel<U, float, T><<<MDP_WAVE((gm_matvec_kernel<U, float, T>)), kVecThreads, 0, st>>>(
+        (const float*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+  }
+  MDP_LAUNCH_CHECK(h);
+  return MDP_OK;
+}
 
 template <bool U, int NB, typename T>
 static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, int refine,
@@ -760,9 +784,8 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
-  gm_matvec_kernel<U, T><<<MDP_WAVE((gm_matvec_kernel<U, T>)), kVecThreads, 0, st>>>(B.pval, Q.col, Q.off, Q.len, k, S, gamma, B.basis, j,
-                                                                B.w, K);
-  MDP_LAUNCH_CHECK(h);
+  mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
+  if (r != MDP_OK) return r;
   gm_dots_kernel<NB, T><<<MDP_WAVE((gm_dots_kernel<NB, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
@@ -819,11 +842,12 @@ static void add_vector_bytes(mdp_s* h, int64_t nvec, size_t vec_bytes) {
 // the update (basis vectors and theta) and the FP64 residual of the restart.
 template <typename T>
 static void count_cycle(mdp_s* h, int steps) {
+  const size_t vbytes = (sizeof(T) == sizeof(double) || h->pstore == kStoreF32) ? sizeof(T) : 2;
   for (int j = 0; j < steps; ++j) {
     h->matvecs += 1;
     h->vreads += j + (j + 2);
     h->vwrites += 2;
-    add_matvec_bytes(h, 1, sizeof(T), sizeof(T));
+    add_matvec_bytes(h, 1, vbytes, sizeof(T));
     add_vector_bytes(h, j + (j + 2) + 2, sizeof(T));
   }
   h->vreads += steps + 1;

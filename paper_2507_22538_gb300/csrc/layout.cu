@@ -71,6 +71,19 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
   atomicMax(kmax, lmax);
 }
 
+// Whether every probability is exactly representable in binary16 / bfloat16.
+__global__ void narrow_exact_kernel(const double* __restrict__ val, int64_t nnz, int* __restrict__ f16_ok,
+                                    int* __restrict__ bf16_ok) {
+  bool a = true, b = true;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+    const double v = val[j];
+    a &= ((double)__half2float(__double2half(v)) == v);
+    b &= ((double)__bfloat162float(__double2bfloat16(v)) == v);
+  }
+  if (!__all_sync(0xffffffffu, a) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
+  if (!__all_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
+}
+
 // Width of each slice of `rows` rows: the longest row among its 32.
 __global__ void slice_width_kernel(const int32_t* __restrict__ len, int64_t rows, int64_t nslices,
                                    int32_t* __restrict__ width) {
@@ -127,7 +140,8 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
                                       const double* __restrict__ g, const int32_t* __restrict__ pi, int64_t S, int A,
                                       double* __restrict__ pval, int32_t* __restrict__ pcol,
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
-                                      double* __restrict__ gpi, float* __restrict__ pval32) {
+                                      double* __restrict__ gpi, float* __restrict__ pval32,
+                                      uint16_t* __restrict__ pval16, int store16) {
   const int64_t work = S * (int64_t)kmax;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = w % S;
@@ -151,10 +165,14 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
       pval[dst] = v;
       pcol[dst] = scol[src];
       if (pval32) pval32[dst] = (float)v;
+      if (pval16)
+        pval16[dst] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v))
+                                             : __bfloat16_as_ushort(__double2bfloat16(v));
     } else if (UNIFORM) {
       pval[dst] = 0.0;
       pcol[dst] = 0;
       if (pval32) pval32[dst] = 0.0f;
+      if (pval16) pval16[dst] = 0;
     }
   }
 }
@@ -248,13 +266,15 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
   const int64_t work = h->S * (int64_t)P.kmax;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->sm_count * 16));
   if (P.uniform)
-    extract_policy_kernel<true><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
-                                                         Q.val, Q.col, Q.off, Q.len, h->gpi,
-                                                         want32 ? h->pval32 : nullptr);
+    extract_policy_kernel<true><<<blocks, 256, 0, st>>>(
+        P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,
+        want32 && h->pstore == kStoreF32 ? h->pval32 : nullptr, want32 && h->pstore != kStoreF32 ? h->pval16 : nullptr,
+        h->pstore);
   else
-    extract_policy_kernel<false><<<blocks, 256, 0, st>>>(P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A,
-                                                          Q.val, Q.col, Q.off, Q.len, h->gpi,
-                                                          want32 ? h->pval32 : nullptr);
+    extract_policy_kernel<false><<<blocks, 256, 0, st>>>(
+        P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,
+        want32 && h->pstore == kStoreF32 ? h->pval32 : nullptr, want32 && h->pstore != kStoreF32 ? h->pval16 : nullptr,
+        h->pstore);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   return MDP_OK;
@@ -276,6 +296,7 @@ static void destroy_handle(mdp_s* h) {
   dfree(st, h->tmp);
   dfree(st, h->basis);
   dfree(st, h->pval32);
+  dfree(st, h->pval16);
   dfree(st, h->basis32);
   dfree(st, h->w32);
   dfree(st, h->tfq);
@@ -293,7 +314,8 @@ static void destroy_handle(mdp_s* h) {
 }
 
 mdp_status ensure_mixed(mdp_s* h, int nvec) {
-  if (!h->pval32) MDP_TRY(dalloc(h, &h->pval32, h->Ppi.nstored, "FP32 policy values"));
+  if (h->pstore == kStoreF32 && !h->pval32) MDP_TRY(dalloc(h, &h->pval32, h->Ppi.nstored, "FP32 policy values"));
+  if (h->pstore != kStoreF32 && !h->pval16) MDP_TRY(dalloc(h, &h->pval16, h->Ppi.nstored, "16-bit policy values"));
   if (!h->w32) MDP_TRY(dalloc(h, &h->w32, h->S, "FP32 w"));
   if (nvec > h->basis32_cap) {
     dfree(h->stream, h->basis32);
@@ -394,6 +416,18 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
                     ? MDP_ERR_INVALID_ARG : MDP_ERR_NOT_STOCHASTIC, m);
   }
   const int kmin = res[1], kmax = res[2];
+
+  // narrowest exact storage for the mixed solver's copies of the policy rows
+  {
+    int ok[2] = {1, 1};
+    MDP_CUDA(cudaMemcpyAsync(dflags + 4, ok, sizeof(ok), cudaMemcpyHostToDevice, st));
+    narrow_exact_kernel<<<grid_for(nnz, 256, h->sm_count), 256, 0, st>>>(dval, nnz, dflags + 4, dflags + 5);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    MDP_CUDA(cudaMemcpyAsync(ok, dflags + 4, sizeof(ok), cudaMemcpyDeviceToHost, st));
+    MDP_CUDA(cudaStreamSynchronize(st));
+    h->pstore = ok[0] ? kStoreF16 : (ok[1] ? kStoreBF16 : kStoreF32);
+  }
 
   // stacked matrix in sliced layout
   MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));

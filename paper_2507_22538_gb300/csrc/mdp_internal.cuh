@@ -1,6 +1,8 @@
 // Internal declarations of libmdp: the handle, error plumbing and kernel launchers.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +16,7 @@ constexpr int kSlice = 32;       // rows (or states) per sliced-ELL slice: one w
 constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
 constexpr int kPartialRows = 40;    // per-block partial sums (up to kMaxBasis + 1 values), transposed
 constexpr int kMaxBlocksPerSm = 8;  // 256-thread blocks: 2048 threads per SM
+enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 constexpr int kScalarSlots = 512;
 
 // Per-thread message of the last failure.
@@ -76,6 +79,10 @@ struct mdp_s {
   int basis_cap = 0;         // vectors allocated in basis
   // mixed-precision inner solver: FP32 copies of the policy rows' values, FP32 basis and w
   float* pval32 = nullptr;   // [Ppi.nstored]
+  // narrowest exact storage of the probabilities, found at creation: 0 = binary32,
+  // 1 = binary16, 2 = bfloat16 (the mixed solver's policy rows then use it)
+  int pstore = 0;
+  uint16_t* pval16 = nullptr;  // [Ppi.nstored], binary16 or bfloat16 bits
   float* basis32 = nullptr;  // [(restart + 1) * S]
   int basis32_cap = 0;
   float* w32 = nullptr;      // [S]

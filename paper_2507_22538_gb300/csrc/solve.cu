@@ -157,6 +157,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   local.vector_reads = h->vreads - vreads0;
   local.vector_writes = h->vwrites - vwrites0;
   local.inner_bytes = h->inner_bytes - ibytes0;
+  local.policy_value_bytes = !mixed ? 8 : (h->pstore == kStoreF32 ? 4 : 2);
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = local;
   return status;

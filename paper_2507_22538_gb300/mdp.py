@@ -51,7 +51,8 @@ class mdp_solve_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double),
                 ("inner_ms", ctypes.c_double), ("policy_matvecs", ctypes.c_int64),
-                ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double)]
+                ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double),
+                ("policy_value_bytes", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -59,4 +59,4 @@ def test_host_only_calls(lib):
 def test_struct_layouts_match_header():
     from paper_2507_22538_gb300 import mdp
     assert ctypes.sizeof(mdp.mdp_solve_opts) == 4 * 8 + 7 * 4 + 4  # padded to 8
-    assert ctypes.sizeof(mdp.mdp_solve_stats) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 3 * 8 + 8
+    assert ctypes.sizeof(mdp.mdp_solve_stats) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 3 * 8 + 8 + 4 + 4

@@ -258,3 +258,45 @@ def test_jacobi_vi_configuration(make):
         torch.cuda.synchronize()
     assert st == mdp.MDP_OK and abs(stats.outer_iters - ref.outer_iters) <= 1
     np.testing.assert_allclose(V.cpu().numpy(), ref.V, rtol=0, atol=1e-9 / (1 - m.gamma))
+
+
+
+def _power_of_two_rows(S, A, k, gamma, seed):
+    """Probabilities 2^-1, ..., 2^-(k-1), 2^-(k-1) per row (exact in bfloat16, and
+    with k = 31 the smallest, 2^-30, is below binary16's range)."""
+    from mdpgen import MDPData
+    rng = np.random.default_rng(seed)
+    R = S * A
+    col = np.sort(np.stack([rng.choice(S, size=k, replace=False) for _ in range(R)]), axis=1).astype(np.int32)
+    p = np.array([2.0 ** -(i + 1) for i in range(k - 1)] + [2.0 ** -(k - 1)])
+    val = np.stack([rng.permutation(p) for _ in range(R)])
+    g = rng.random(R)
+    return MDPData(S, A, np.arange(R + 1, dtype=np.int64) * k, col.ravel(), val.ravel(), g, gamma)
+
+
+@pytest.mark.parametrize("storage", ["binary16", "bfloat16", "binary32"])
+def test_mixed_precision_narrow_storage(storage):
+    """With MDP_PREC_MIXED the policy rows are kept in the narrowest format that holds every
+    probability exactly (dyadic inputs, binary16 or bfloat16), else binary32; the result
+    is certified by the oracle either way."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    from tests._util import check_policy, q_tolerance
+    if storage == "binary16":
+        m, expect = random_sparse(2000, 6, 16, 0.99, seed=41, quant_bits=11), 2
+    elif storage == "bfloat16":
+        m, expect = _power_of_two_rows(400, 3, 31, 0.99, seed=42), 2
+    else:
+        m, expect = random_sparse(2000, 6, 16, 0.99, seed=41), 4
+    vn = float(np.max(np.abs(O.ipi(*_args(m), tol=1e-8, alpha=1e-3).V)))
+    tol_p = min(1e-8, 0.5e-8 * (1 - m.gamma) * vn)
+    with mdp.MDP.from_data(m) as M:
+        V, pi, stats, st = M.solve(m.gamma, tol=tol_p, alpha=1e-3, precision=mdp.MDP_PREC_MIXED)
+        torch.cuda.synchronize()
+    assert st == mdp.MDP_OK and stats.policy_value_bytes == expect, stats.as_dict()
+    Vg = V.cpu().numpy()
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, Vg, m.S, m.A)
+    qt = q_tolerance(m, Vg)
+    assert float(np.max(np.abs(Q.min(axis=1) - Vg))) <= tol_p + qt
+    check_policy(pi.cpu().numpy(), Q, qt)
