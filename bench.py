@@ -63,20 +63,27 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def bellman_source_sha():
+    """sha256 (first 16 hex digits) of the sources that make the Bellman kernel."""
+    h = hashlib.sha256()
+    for f in ("sell.cuh", "bellman_dev.cuh", "bellman.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2507_22538_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def sweep_traffic():
     """DRAM bytes per Bellman launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2507_22538_gb300", "csrc", "bellman.cu")
     summ = os.path.join(ROOT, "profiles", "bellman_sweep_banded_s1e6.txt")
     if not os.path.exists(summ):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = bellman_source_sha()
     vals = {}
     for line in open(summ):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("bellman_cu_sha256_16") != sha:
+    if vals.get("bellman_src_sha256_16") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -190,7 +197,9 @@ def run_reference(args):
 def run_serving(n, slots=4, seed=5):
     """Continuous-batching measurement: n requests of mixed S (log-uniform 1e3..1e5),
     A (2..16), k (4..32) and gamma (0.9..0.9999), Poisson arrivals at 0.8 of the
-    one-at-a-time rate, admitted by a 120 GB HBM budget into `slots` concurrent solves."""
+    one-at-a-time rate (and a burst of all n at once), admitted by a 120 GB HBM budget
+    into `slots` concurrent solves, each solve one request or (batch_max 8) up to 8
+    same-gamma requests stacked block-diagonally."""
     import numpy as np
 
     from mdpgen import serving_request
@@ -204,21 +213,36 @@ def run_serving(n, slots=4, seed=5):
     rate = 0.8 / float(service.mean())
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
-    svc = SolveService(slots=slots, hbm_budget=120 << 30).start()
-    t0 = svc.now()
-    for r, a in zip(reqs, arrivals):
-        wait = t0 + a - svc.now()
-        if wait > 0:
-            time.sleep(wait)
-        svc.submit(r)
-    res = svc.wait(n)
-    svc.close()
+
+    def drive(arr, batch_max):
+        svc = SolveService(slots=slots, hbm_budget=120 << 30, batch_max=batch_max).start()
+        t0 = svc.now()
+        for r, a in zip(reqs, arr):
+            wait = t0 + a - svc.now()
+            if wait > 0:
+                time.sleep(wait)
+            svc.submit(r)
+        out = svc.wait(n)
+        svc.close()
+        summ = latency_summary(out)
+        if batch_max > 1:
+            summ.update(batch_max=batch_max, mean_batch=float(np.mean(svc.batches)), solves=len(svc.batches))
+        return out, summ, svc
+
+    res, cont, svc = drive(arrivals, 1)
+    # the same arrivals, and a burst of all n at once, with same-gamma requests stacked
+    # block-diagonally (up to 8 per solve)
+    _, cont_b, _ = drive(arrivals, 8)
+    burst = np.zeros(n)
+    _, burst1, _ = drive(burst, 1)
+    _, burst8, _ = drive(burst, 8)
     same = all(np.array_equal(alone[r.rid].V, res[r.rid].V) and np.array_equal(alone[r.rid].pi, res[r.rid].pi)
                for r in reqs)
     return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
             "mix": "S log-uniform 1e3..1e5, A 2..16, k 4..32, gamma in {0.9,0.99,0.999,0.9999}, GMRES(30), "
                    "alpha 1e-3, tol 1e-8",
-            "continuous": latency_summary(res), "one_at_a_time": fifo_one_at_a_time(arrivals, service),
+            "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
+            "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same)}
 
 
@@ -244,12 +268,59 @@ def run_bellman_only(args):
             mdp.check(mdp.mdp_bellman(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman")
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.bellman_only
+        ms = e0.elapsed_time(e1) / args.bellman_only
+        # the greedy policy's rows gathered (Algorithm 1 step 4) and applied once: mdp_policy_apply
+        Y = torch.empty_like(V)
+        mdp.check(mdp.mdp_policy_apply(M.h, GAMMA, pi, V, Y, stream), "mdp_policy_apply")
+        e0.record(stream)
+        for _ in range(args.bellman_only):
+            mdp.check(mdp.mdp_policy_apply(M.h, GAMMA, pi, V, Y, stream), "mdp_policy_apply")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_pa = e0.elapsed_time(e1) / args.bellman_only
     R = m.S * A
     nbytes = R * K_ROW * 12 + (R + 1) * 8 + R * 8 + m.S * 8 + m.S * 12
+    # gather: read pi and the S chosen rows (12 B per entry) and g; write the rows and g_pi
+    gather_bytes = m.S * (4 + 8 + 8) + 2 * m.S * K_ROW * 12
     peak, _ = load_peaks()
     print(json.dumps({"mode": "bellman_only", "S": m.S, "ms_per_sweep": ms, "bytes": nbytes,
-                      "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak}), flush=True)
+                      "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
+                      "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes}), flush=True)
+    return 0
+
+
+def run_solve_only(args):
+    """Time W + K solves of the workload at one precision, one JSON line (profiling
+    aid: the launch list of a single solve without the rest of the bench)."""
+    import torch
+
+    from mdpgen import banded_birth_death
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.build import build
+    build()
+    m = banded_birth_death(args.states, A, H, GAMMA)
+    stream = torch.cuda.current_stream()
+    prec = mdp.MDP_PREC_MIXED if args.solve_only == "mixed" else mdp.MDP_PREC_F64
+    with mdp.MDP.from_data(m, stream) as M:
+        V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+        pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+        o = mdp.mdp_default_opts()
+        o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.inner, o.precision = GAMMA, TOL, ALPHA, RESTART, mdp.MDP_GMRES, prec
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        for i in range(args.warmup + args.steps):
+            if i == args.warmup:
+                torch.cuda.synchronize()
+                e0.record(stream)
+            V.zero_()
+            st, stats = mdp.mdp_solve(M.h, o, V, pi, stream)
+            mdp.check(st, "mdp_solve")
+            launches = stats.kernel_launches
+        e1.record(stream)
+        torch.cuda.synchronize()
+    print(json.dumps({"mode": "solve_only", "precision": args.solve_only, "S": m.S,
+                      "ms_per_solve": e0.elapsed_time(e1) / max(1, args.steps), "launches_per_solve": launches,
+                      "outer": stats.outer_iters, "inner": stats.inner_iters_total}), flush=True)
     return 0
 
 
@@ -303,11 +374,15 @@ def main():
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
                     help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
-    ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only: number of states")
+    ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only/--solve-only: number of states")
     ap.add_argument("--inner-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: ITERS GMRES(30) iterations of mdp_policy_eval on the rows of action 0 "
                          "of the workload (a one-action MDP; no bench line)")
+    ap.add_argument("--solve-only", choices=["f64", "mixed"], default=None,
+                    help="profiling aid: W + K solves of the workload at this precision (no bench line)")
     args = ap.parse_args()
+    if args.solve_only:
+        return run_solve_only(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.bellman_only:

@@ -190,6 +190,34 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_
                      mdp_solve_stats* stats, void* stream);
 
 /*
+ * mdp_solve_batch -- Algorithm 1 on n independent MDPs at once (problems of
+ * different S, A, row lengths and gamma), each with its own options, advanced
+ * in lockstep: every kernel launch of the batch covers all problems that are
+ * still running (per-problem descriptors and block ranges in device memory),
+ * with one residual read per outer iteration and one solver-state read per
+ * GMRES cycle for the whole batch.  The paper solves one MDP per call; this is
+ * the same method applied to many, with the per-problem arithmetic unchanged:
+ * each problem's V, pi, iteration counts and status equal those of mdp_solve on
+ * that problem alone, bit for bit.
+ *
+ *  n        number of problems, >= 1.
+ *  handles  [n] distinct handles on the current device (each used by this call only).
+ *  opts     [n] options as for mdp_solve; inner must be MDP_GMRES and gmres_refine
+ *           MDP_REFINE_NEVER; precision MDP_PREC_F64 or MDP_PREC_MIXED, per problem.
+ *  V, pi    [n] device pointers: V[i] double[S_i] (in V_0, out V), pi[i] int32[S_i].
+ *  stats    [n] host structs (may be NULL): per problem as mdp_solve, except that
+ *           seconds and kernel_launches are those of the whole batch and the
+ *           bellman_ms, inner_ms and byte counters are not filled (0).
+ *  status   [n] host: each problem's mdp_solve status (MDP_OK, MDP_NOT_CONVERGED,
+ *           MDP_ERR_NUMERIC).
+ * Blocks until every problem has stopped.  Returns MDP_OK when the batch ran
+ * (per-problem outcomes in status[]), MDP_ERR_INVALID_ARG for a bad argument
+ * (nothing runs), MDP_ERR_OOM or MDP_ERR_CUDA when the batch could not run.
+ */
+mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve_opts* opts, double* const* V,
+                           int32_t* const* pi, mdp_solve_stats* stats, mdp_status* status, void* stream);
+
+/*
  * mdp_bellman_csr_noalloc -- the Bellman application of mdp_bellman (TV, greedy pi,
  * ||TV - V||_inf) computed straight from the caller's row-stacked CSR arrays,
  * with no handle and no device allocation.  The paper has no counterpart: it is

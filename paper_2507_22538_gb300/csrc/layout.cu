@@ -5,7 +5,7 @@
 #include <cstring>
 #include <vector>
 
-#include "mdp_internal.cuh"
+#include "layout_dev.cuh"
 
 namespace mdp {
 
@@ -106,7 +106,7 @@ __global__ void state_maxlen_kernel(const int32_t* __restrict__ len, int64_t S, 
   }
 }
 
-// CSR -> sliced ELL: one thread per row copies its entries into column-major slice order.
+// CSR -> sliced ELL: one thread per row copies its entries into their chunked slice positions.
 __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                    const double* __restrict__ val, int64_t R, const int64_t* __restrict__ off,
                                    int uniform_k, double* __restrict__ sval, int32_t* __restrict__ scol) {
@@ -116,8 +116,8 @@ __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t
     int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
     int64_t width = uniform_k ? uniform_k : (off[q + 1] - off[q]) / kSlice;
     int64_t lo = rp[r], n = rp[r + 1] - lo;
-    for (int64_t j = 0; j < width; ++j) {
-      int64_t d = base + j * kSlice + lane;
+    for (int j = 0; j < (int)width; ++j) {
+      const int64_t d = sell_at(base, (int)width, lane, j);
       if (j < n) {
         sval[d] = val[lo + j];
         scol[d] = col[lo + j];
@@ -129,11 +129,7 @@ __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t
   }
 }
 
-// Algorithm 1 step 4: gather the policy's rows r(s) = s*A + pi(s) of the stacked
-// matrix into the per-state sliced layout, and g_pi(s) = g(s, pi(s)).  One thread
-// per (state, entry) with the state fastest, so each warp's writes are
-// contiguous and every load is independent.  States whose pi(s) lies outside
-// [0, A) get an empty row (zero values, column 0) and g_pi = NaN.
+// Algorithm 1 step 4 on one problem (body in layout_dev.cuh).
 template <bool UNIFORM>
 __global__ void extract_policy_kernel(const double* __restrict__ sval, const int32_t* __restrict__ scol,
                                       const int64_t* __restrict__ off, const int32_t* __restrict__ len, int kmax,
@@ -142,39 +138,7 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi, float* __restrict__ pval32,
                                       uint16_t* __restrict__ pval16, int store16) {
-  const int64_t work = S * (int64_t)kmax;
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = w % S;
-    const int j = (int)(w / S);
-    const int a = pi[s];
-    const bool ok = (a >= 0 && a < A);
-    const int64_t r = s * A + (ok ? a : 0);
-    const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
-    if (j == 0) {
-      if (!UNIFORM) plen[s] = n;
-      gpi[s] = ok ? g[r] : __longlong_as_double(0x7ff8000000000000ULL);
-    }
-    const int64_t ps = s / kSlice;
-    const int64_t pmax = UNIFORM ? kmax : (poff[ps + 1] - poff[ps]) / kSlice;
-    if (j >= pmax) continue;
-    const int64_t dst = (UNIFORM ? ps * kSlice * (int64_t)kmax : poff[ps]) + (s % kSlice) + (int64_t)j * kSlice;
-    if (j < n) {
-      const int64_t q = r / kSlice;
-      const int64_t src = (UNIFORM ? q * kSlice * (int64_t)kmax : off[q]) + (r % kSlice) + (int64_t)j * kSlice;
-      const double v = sval[src];
-      pval[dst] = v;
-      pcol[dst] = scol[src];
-      if (pval32) pval32[dst] = (float)v;
-      if (pval16)
-        pval16[dst] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v))
-                                             : __bfloat16_as_ushort(__double2bfloat16(v));
-    } else if (UNIFORM) {
-      pval[dst] = 0.0;
-      pcol[dst] = 0;
-      if (pval32) pval32[dst] = 0.0f;
-      if (pval16) pval16[dst] = 0;
-    }
-  }
+  extract_policy_body<UNIFORM>((int)blockIdx.x, (int)gridDim.x, sval, scol, off, len, kmax, g, pi, S, A, pval, pcol, poff, plen, gpi, pval32, pval16, store16);
 }
 
 static int grid_for(int64_t n, int threads, int sm_count) {
@@ -214,11 +178,11 @@ static void dfree(cudaStream_t st, T*& p) {
   p = nullptr;
 }
 
-#define MDP_TRY(x)                     \
-  do {                                 \
-    mdp_status st_ = (x);              \
-    if (st_ != MDP_OK) return st_;     \
-  } while (0)
+mdp_status bind_stream(mdp_s* h, cudaStream_t st) {
+  MDP_CUDA(cudaStreamWaitEvent(st, h->done, 0));
+  h->stream = st;
+  return MDP_OK;
+}
 
 // Build a sliced layout from per-row lengths (device) for `rows` rows.
 static mdp_status build_sell(mdp_s* h, Sell* m, const int32_t* dlen, int64_t rows, int kmin, int kmax,
@@ -260,11 +224,15 @@ static void free_sell(cudaStream_t st, Sell* m) {
   *m = Sell();
 }
 
+int extract_blocks(const mdp_s* h) {
+  const int64_t work = h->S * (int64_t)((h->P.kmax + kChunk - 1) / kChunk);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->sm_count * 16));
+}
+
 mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t st) {
   const Sell& P = h->P;
   Sell& Q = h->Ppi;
-  const int64_t work = h->S * (int64_t)P.kmax;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)h->sm_count * 16));
+  const int blocks = extract_blocks(h);
   if (P.uniform)
     extract_policy_kernel<true><<<blocks, 256, 0, st>>>(
         P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,

@@ -1,0 +1,81 @@
+// Device side of the policy-row gather (Algorithm 1 step 4), shared by the
+// single-problem kernel and the batched kernel.  The body works on one problem
+// with `nb` blocks of which the calling block is number `bid`.
+#pragma once
+
+#include "mdp_internal.cuh"
+
+namespace mdp {
+
+// Algorithm 1 step 4: gather the policy's rows r(s) = s*A + pi(s) of the stacked
+// matrix into the per-state sliced layout, and g_pi(s) = g(s, pi(s)).  One thread
+// per (state, 4-entry chunk) with the state fastest: each warp writes whole
+// contiguous chunks and each thread reads one 32-byte run of its row.  States
+// whose pi(s) lies outside [0, A) get an empty row (zero values, column 0) and
+// g_pi = NaN.
+__device__ __forceinline__ void put_narrow(float* p32, uint16_t* p16, int store16, int64_t i, double v) {
+  if (p32) p32[i] = (float)v;
+  if (p16) p16[i] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v)) : __bfloat16_as_ushort(__double2bfloat16(v));
+}
+
+template <bool UNIFORM>
+__device__ __forceinline__ void extract_policy_body(int bid, int nb, const double* __restrict__ sval, const int32_t* __restrict__ scol,
+                                      const int64_t* __restrict__ off, const int32_t* __restrict__ len, int kmax,
+                                      const double* __restrict__ g, const int32_t* __restrict__ pi, int64_t S, int A,
+                                      double* __restrict__ pval, int32_t* __restrict__ pcol,
+                                      const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
+                                      double* __restrict__ gpi, float* __restrict__ pval32,
+                                      uint16_t* __restrict__ pval16, int store16) {
+  const int nunits = (kmax + kChunk - 1) / kChunk;
+  const int64_t work = S * (int64_t)nunits;
+  for (int64_t w = bid * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)nb * blockDim.x) {
+    const int64_t s = w % S;
+    const int u = (int)(w / S);
+    const int a = pi[s];
+    const bool ok = (a >= 0 && a < A);
+    const int64_t r = s * A + (ok ? a : 0);
+    const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
+    if (u == 0) {
+      if (!UNIFORM) plen[s] = n;
+      gpi[s] = ok ? g[r] : __longlong_as_double(0x7ff8000000000000ULL);
+    }
+    const int64_t ps = s / kSlice, q = r / kSlice;
+    const int pw = UNIFORM ? kmax : (int)((poff[ps + 1] - poff[ps]) / kSlice);  // destination slice width
+    const int sw = UNIFORM ? kmax : (int)((off[q + 1] - off[q]) / kSlice);      // source slice width
+    const int64_t pbase = UNIFORM ? ps * kSlice * (int64_t)kmax : poff[ps];
+    const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
+    const int pl = (int)(s % kSlice), sl = (int)(r % kSlice);
+    const int j0 = u * kChunk;
+    if (UNIFORM && ok && j0 + kChunk <= (kmax & ~(kChunk - 1))) {  // whole chunk on both sides
+      double v[kChunk];
+      int c[kChunk];
+      const int64_t si = sell_at(sbase, sw, sl, j0), di = sell_at(pbase, pw, pl, j0);
+      load_chunk(sval + si, v);
+      load_chunk(scol + si, c);
+      *reinterpret_cast<double2*>(pval + di) = make_double2(v[0], v[1]);
+      *reinterpret_cast<double2*>(pval + di + 2) = make_double2(v[2], v[3]);
+      *reinterpret_cast<int4*>(pcol + di) = make_int4(c[0], c[1], c[2], c[3]);
+      if (pval32) *reinterpret_cast<float4*>(pval32 + di) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+      if (pval16)
+#pragma unroll
+        for (int e = 0; e < kChunk; ++e) put_narrow(nullptr, pval16, store16, di + e, v[e]);
+      continue;
+    }
+    for (int j = j0; j < j0 + kChunk && j < pw; ++j) {
+      const int64_t di = sell_at(pbase, pw, pl, j);
+      if (j < n) {
+        const int64_t si = sell_at(sbase, sw, sl, j);
+        const double v = sval[si];
+        pval[di] = v;
+        pcol[di] = scol[si];
+        put_narrow(pval32, pval16, store16, di, v);
+      } else if (UNIFORM) {
+        pval[di] = 0.0;
+        pcol[di] = 0;
+        put_narrow(pval32, pval16, store16, di, 0.0);
+      }
+    }
+  }
+}
+
+}  // namespace mdp

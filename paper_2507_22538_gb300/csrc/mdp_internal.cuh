@@ -9,10 +9,10 @@
 #include <string>
 
 #include "../../include/mdp.h"
+#include "sell.cuh"
 
 namespace mdp {
 
-constexpr int kSlice = 32;       // rows (or states) per sliced-ELL slice: one warp, one row per lane
 constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
 constexpr int kPartialRows = 40;    // per-block partial sums (up to kMaxBasis + 1 values), transposed
 constexpr int kMaxBlocksPerSm = 8;  // 256-thread blocks: 2048 threads per SM
@@ -24,6 +24,12 @@ void set_error(const std::string& msg);
 mdp_status fail(mdp_status st, const std::string& msg);
 mdp_status cuda_fail(cudaError_t e, const char* what);
 
+#define MDP_TRY(x)                 \
+  do {                             \
+    mdp_status st_ = (x);          \
+    if (st_ != MDP_OK) return st_; \
+  } while (0)
+
 #define MDP_CUDA(call)                                   \
   do {                                                   \
     cudaError_t e_ = (call);                             \
@@ -31,8 +37,14 @@ mdp_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 // Sliced-ELL (slice height 32) copy of a row-major matrix: slice q holds rows
-// 32q..32q+31; element j of lane l sits at off[q] + 32*j + l.  When every row
-// has the same length k, `uniform` is set, off[q] = 32*k*q and len[] is unused.
+// 32q..32q+31, each padded to the slice's width w.  The first w & ~3 entries of
+// a row are stored in chunks of 4 consecutive entries (chunk c of lane l at
+// off[q] + 128 c + 4 l), the remaining w & 3 column-major (entry j of lane l at
+// off[q] + 32 j + l).  A warp streaming 32 rows still reads whole contiguous
+// lines, and one row's entries come 4 to a 32-byte sector, which is what a
+// gather of single rows (the policy rows of Algorithm 1 step 4) pays for.
+// When every row has the same length k, `uniform` is set, off[q] = 32*k*q and
+// len[] is unused.
 struct Sell {
   int64_t rows = 0;
   int64_t nslices = 0;
@@ -119,6 +131,15 @@ mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, i
 mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st);
 mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, int precision,
                        double omega, double tol, int max_it, int* iters, double* res2, cudaStream_t st);
+// Order a call on stream `st` after the handle's earlier calls (its `done`
+// event) and make `st` the stream of the handle's later allocations.
+mdp_status bind_stream(mdp_s* h, cudaStream_t st);
+
+// Launch shapes of the single-problem passes, reused by the batched solver.
+enum GmresPass { kPassResidual, kPassMatvec, kPassUpdate, kPassDots, kPassProject };
+int gmres_grid(mdp_s* h, GmresPass pass, int NB, bool mixed);
+int extract_blocks(const mdp_s* h);
+size_t bellman_smem_bytes(const mdp_s* h);
 mdp_status ensure_basis(mdp_s* h, int nvec);
 mdp_status ensure_mixed(mdp_s* h, int nvec);  // FP32 policy values, basis and w for the mixed solver
 mdp_status ensure_tfqmr(mdp_s* h);            // TFQMR / Jacobi work vectors

@@ -15,6 +15,7 @@ mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, 
   if (!V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
   if ((const void*)V == (const void*)TV) return fail(MDP_ERR_INVALID_ARG, "V and TV may not alias");
   cudaStream_t st = (cudaStream_t)stream;
+  MDP_TRY(bind_stream(h, st));
   mdp_status s = launch_bellman(h, gamma, V, TV, pi, st);
   if (s != MDP_OK) return s;
   if (residual_inf)
@@ -29,6 +30,7 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
   if (!pi || !x || !y) return fail(MDP_ERR_INVALID_ARG, "null vector");
   if ((const void*)x == (const void*)y) return fail(MDP_ERR_INVALID_ARG, "x and y may not alias");
   cudaStream_t st = (cudaStream_t)stream;
+  MDP_TRY(bind_stream(h, st));
   mdp_status s = extract_policy(h, pi, false, st);
   if (s != MDP_OK) return s;
   s = launch_policy_apply(h, gamma, x, y, st);
@@ -48,6 +50,7 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
     return fail(MDP_ERR_INVALID_ARG, "GMRES restart must be in 1..32");
   if (max_it < 0 || !(abs_tol_2norm >= 0.0)) return fail(MDP_ERR_INVALID_ARG, "bad tolerance or iteration cap");
   cudaStream_t st = (cudaStream_t)stream;
+  MDP_TRY(bind_stream(h, st));
   mdp_status s = extract_policy(h, pi, false, st);
   if (s != MDP_OK) return s;
   if (v != v0) MDP_CUDA(cudaMemcpyAsync(v, v0, h->S * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -82,11 +85,12 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   if (o->precision != MDP_PREC_F64 && o->precision != MDP_PREC_MIXED)
     return fail(MDP_ERR_INVALID_ARG, "unknown precision");
   const bool mixed = (o->precision == MDP_PREC_MIXED && o->inner == MDP_GMRES);
+  cudaStream_t st = (cudaStream_t)stream;
+  MDP_TRY(bind_stream(h, st));
   if (mixed) {
     mdp_status s0 = ensure_mixed(h, o->gmres_restart + 1);
     if (s0 != MDP_OK) return s0;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
   const double ibytes0 = h->inner_bytes;

@@ -74,6 +74,9 @@ _SIGNATURES = {
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
     "mdp_solve": (ctypes.c_int, [_P, ctypes.POINTER(mdp_solve_opts), _P, _P, ctypes.POINTER(mdp_solve_stats), _P]),
+    "mdp_solve_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_opts),
+                                       ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_stats),
+                                       ctypes.POINTER(ctypes.c_int), _P]),
     "mdp_last_error": (ctypes.c_char_p, []),
     "mdp_bellman_csr_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                                _P, _P, _P, _P, _P]),
@@ -181,6 +184,23 @@ def mdp_solve(h, opts: mdp_solve_opts, V, pi, stream=None):
     stats = mdp_solve_stats()
     st = load().mdp_solve(h, ctypes.byref(opts), _ptr(V), _ptr(pi), ctypes.byref(stats), _stream(stream))
     return st, stats
+
+
+def mdp_solve_batch(handles, opts, V, pi, stream=None):
+    """Solve len(handles) MDPs in lockstep.  opts: a list of mdp_solve_opts; V, pi:
+    lists of device tensors.  Returns (status of the call, [per-problem status],
+    [per-problem mdp_solve_stats])."""
+    n = len(handles)
+    if not (len(opts) == len(V) == len(pi) == n):
+        raise ValueError("handles, opts, V and pi must have the same length")
+    hs = (_P * n)(*handles)
+    os_ = (mdp_solve_opts * n)(*opts)
+    vs = (_P * n)(*[_ptr(v) for v in V])
+    ps = (_P * n)(*[_ptr(p) for p in pi])
+    stats = (mdp_solve_stats * n)()
+    status = (ctypes.c_int * n)()
+    st = load().mdp_solve_batch(n, hs, os_, vs, ps, stats, status, _stream(stream))
+    return st, list(status), list(stats)
 
 
 def mdp_bellman_csr_noalloc(S, A, row_ptr, col, val, g, gamma, V, TV, pi, residual_inf=None, stream=None) -> int:

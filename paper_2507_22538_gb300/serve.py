@@ -5,7 +5,10 @@ request is admitted as soon as one of `slots` workers is free and its device
 footprint fits in what is left of the HBM budget; each worker owns a CUDA
 stream, uploads the MDP (mdp_create), runs Algorithm 1 (mdp_solve) and copies
 V and the policy back, so admitted requests overlap on the GPU while later
-ones wait.  The solver calls release the Python interpreter lock, so the
+ones wait.  With batch_max > 1 a worker takes, besides the first request that
+fits, later pending requests that also fit (any S, A, k and gamma; GMRES in
+FP64 or mixed precision) and solves them together with mdp_solve_batch: one launch per pass for
+all of them, each result bit for bit its stand-alone one.  The solver calls release the Python interpreter lock, so the
 workers' host threads run concurrently.  All computation happens in libmdp's
 kernels; this module only schedules.
 """
@@ -57,6 +60,10 @@ def device_bytes(data, restart: int = 30, precision: int = mdp.MDP_PREC_F64) -> 
     S, A = int(data.S), int(data.A)
     nnz = int(data.row_ptr[-1])
     kmax = int(np.max(np.diff(data.row_ptr))) if S * A else 0
+    return _footprint(S, A, nnz, kmax, restart, precision)
+
+
+def _footprint(S, A, nnz, kmax, restart, precision) -> int:
     stacked = 12 * nnz + 8 * S * A
     upload = 12 * nnz + 8 * (S * A + 1)
     policy = 16 * S * kmax
@@ -68,9 +75,10 @@ def device_bytes(data, restart: int = 30, precision: int = mdp.MDP_PREC_F64) -> 
 class SolveService:
     """A fixed pool of worker slots with an HBM admission budget."""
 
-    def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0):
+    def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0, batch_max: int = 1):
         import torch
         self.slots = slots
+        self.batch_max = max(1, int(batch_max))
         self.budget = int(hbm_budget)
         self.device = device
         self._free = self.budget
@@ -84,6 +92,7 @@ class SolveService:
         self._workers = [threading.Thread(target=self._work, args=(i,), daemon=True) for i in range(slots)]
         self.peak_in_flight = 0
         self._in_flight = 0
+        self.batches: list[int] = []  # size of every solve the workers ran
 
     # -- client side --------------------------------------------------------------
     def start(self):
@@ -126,13 +135,31 @@ class SolveService:
             return dict(self._results)
 
     # -- workers ------------------------------------------------------------------
+    @staticmethod
+    def _batchable(r: Request) -> bool:
+        return r.inner == mdp.MDP_GMRES and r.precision in (mdp.MDP_PREC_F64, mdp.MDP_PREC_MIXED)
+
     def _admit(self):
-        """First pending request (arrival order) that fits the free budget."""
+        """First pending request (arrival order) that fits the free budget, plus (with
+        batch_max > 1) later pending requests that still fit, when all of them run
+        GMRES: they are solved together by one mdp_solve_batch call."""
         for i, r in enumerate(self._pending):
             need = device_bytes(r.data, r.restart, r.precision)
             if need <= self._free:
-                self._free -= need
-                return self._pending.pop(i), need
+                batch = [r]
+                total = need
+                if self.batch_max > 1 and self._batchable(r):
+                    for r2 in self._pending[i + 1:]:
+                        if len(batch) == self.batch_max:
+                            break
+                        n2 = device_bytes(r2.data, r2.restart, r2.precision)
+                        if self._batchable(r2) and total + n2 <= self._free:
+                            batch.append(r2)
+                            total += n2
+                ids = {id(b) for b in batch}
+                self._pending = [p for p in self._pending if id(p) not in ids]
+                self._free -= total
+                return batch, total
         return None, 0
 
     def _work(self, slot: int):
@@ -144,28 +171,31 @@ class SolveService:
                 while True:
                     if self._stop and not self._pending:
                         return
-                    req, need = self._admit()
-                    if req is not None:
+                    batch, need = self._admit()
+                    if batch is not None:
                         break
                     self._cv.wait()
-                self._in_flight += 1
+                self._in_flight += len(batch)
                 self.peak_in_flight = max(self.peak_in_flight, self._in_flight)
             admitted = self.now()
             try:
-                res = self._solve(req, stream)
-            except Exception as exc:  # a failed request still completes, with its status
+                outs = [self._solve(batch[0], stream)] if len(batch) == 1 else self._solve_batch(batch, stream)
+            except Exception as exc:  # failed requests still complete, with their status
                 status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
-                res = Result(req.rid, status, np.empty(0), np.empty(0, dtype=np.int32), 0, 0, float("nan"),
-                             req.arrival, 0.0, 0.0)
+                outs = [Result(r.rid, status, np.empty(0), np.empty(0, dtype=np.int32), 0, 0, float("nan"),
+                               r.arrival, 0.0, 0.0) for r in batch]
             finally:
                 with self._cv:
                     self._free += need
-                    self._in_flight -= 1
+                    self._in_flight -= len(batch)
                     self._cv.notify_all()
-            res.admitted = admitted
-            res.finished = self.now()
+            done = self.now()
             with self._cv:
-                self._results[req.rid] = res
+                for res in outs:
+                    res.admitted = admitted
+                    res.finished = done
+                    self._results[res.rid] = res
+                self.batches.append(len(batch))
                 self._cv.notify_all()
 
     @staticmethod
@@ -187,6 +217,36 @@ class SolveService:
                 mdp.mdp_destroy(h)
         return Result(req.rid, st, Vh.numpy(), pih.numpy(), stats.outer_iters, int(stats.inner_iters_total),
                       stats.final_residual, req.arrival, 0.0, 0.0)
+
+    @staticmethod
+    def _solve_batch(batch, stream) -> list:
+        import torch
+        handles = []
+        with torch.cuda.stream(stream):
+            try:
+                for r in batch:
+                    d = r.data
+                    st, h = mdp.mdp_create(d.S, d.A, d.row_ptr, d.col, d.val, d.g, False, stream)
+                    mdp.check(st, f"mdp_create (request {r.rid})")
+                    handles.append(h)
+                opts = []
+                for r in batch:
+                    o = mdp.mdp_default_opts()
+                    o.gamma, o.atol_pi, o.alpha, o.inner = r.data.gamma, r.tol, r.alpha, r.inner
+                    o.gmres_restart, o.precision = r.restart, r.precision
+                    opts.append(o)
+                V = [torch.zeros(r.data.S, dtype=torch.float64, device="cuda") for r in batch]
+                pi = [torch.empty(r.data.S, dtype=torch.int32, device="cuda") for r in batch]
+                st, status, stats = mdp.mdp_solve_batch(handles, opts, V, pi, stream)
+                mdp.check(st, "mdp_solve_batch")
+                Vh = [v.cpu() for v in V]  # on this stream: ordered after the solve
+                pih = [p.cpu() for p in pi]
+            finally:
+                for h in handles:
+                    mdp.mdp_destroy(h)
+        return [Result(r.rid, status[i], Vh[i].numpy(), pih[i].numpy(), stats[i].outer_iters,
+                       int(stats[i].inner_iters_total), stats[i].final_residual, r.arrival, 0.0, 0.0)
+                for i, r in enumerate(batch)]
 
 
 def solve_alone(req: Request) -> Result:

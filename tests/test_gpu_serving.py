@@ -64,3 +64,23 @@ def test_request_above_budget_is_refused():
     svc = SolveService(slots=1, hbm_budget=1 << 20)
     with pytest.raises(ValueError):
         svc.submit(Request(0, serving_request(0, seed=1, **MIX)))
+
+
+def test_batched_service_equals_alone():
+    """With batch_max > 1 the service solves pending requests of different S, A, k and
+    gamma together (mdp_solve_batch); each result still equals the request solved
+    alone, bit for bit."""
+    from paper_2507_22538_gb300.serve import Request, SolveService, solve_alone
+    reqs = [Request(i, serving_request(i, seed=29, **MIX), tol=1e-8, alpha=1e-3) for i in range(16)]
+    svc = SolveService(slots=2, batch_max=8).start()
+    for r in reqs:
+        svc.submit(r)
+    res = svc.wait(len(reqs))
+    svc.close()
+    assert max(svc.batches) > 1
+    for r in reqs:
+        alone = solve_alone(r)
+        out = res[r.rid]
+        assert out.status == alone.status
+        assert np.array_equal(out.V, alone.V) and np.array_equal(out.pi, alone.pi)
+        assert (out.outer_iters, out.inner_iters) == (alone.outer_iters, alone.inner_iters)
