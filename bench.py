@@ -209,7 +209,8 @@ def run_serving(n, slots=4, seed=5):
     reqs = [Request(i, serving_request(i, seed=seed, **mix), tol=1e-8, alpha=1e-3) for i in range(n)]
     solve_alone(reqs[0])  # warm-up
     alone = [solve_alone(r) for r in reqs]
-    service = np.array([a.finished for a in alone])
+    again = [solve_alone(r) for r in reqs]  # service time: the faster of two stand-alone runs
+    service = np.array([min(a.finished, b.finished) for a, b in zip(alone, again)])
     rate = 0.8 / float(service.mean())
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -244,6 +245,95 @@ def run_serving(n, slots=4, seed=5):
             "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same)}
+
+
+def run_stress(sweeps=10):
+    """The bandwidth-stress random workload at full size (S = 2e6, A = 32, 32 entries
+    per row = 2.05e9 entries, Dirichlet(0.5) quantised to 2^-11, gamma = 0.99), built on
+    the device: event-timed Bellman sweeps against the HBM roofline, and one FP64 and
+    one mixed-precision solve (GMRES(30), alpha = 1e-4, tol = 1e-8)."""
+    import torch
+
+    from mdpgen.torch_gen import random_sparse_device
+    from paper_2507_22538_gb300 import mdp
+    Sx, Ax, Kx, gx = 2_000_000, 32, 32, 0.99
+    t0 = time.perf_counter()
+    rp, col, val, g = random_sparse_device(Sx, Ax, Kx, gx, 21, conc=0.5, quant_bits=11)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    out = {"workload": "random sparse S=2e6, A=32, k=32 (2.05e9 entries), Dirichlet(0.5) quantised to 2^-11, "
+                       "gamma=0.99, built on the device", "generate_s": t_gen}
+    with mdp.MDP(Sx, Ax, rp, col, val, g, stream) as M:
+        del rp, col, val, g
+        torch.cuda.empty_cache()
+        V = torch.zeros(Sx, dtype=torch.float64, device="cuda")
+        TV = torch.empty_like(V)
+        pi = torch.empty(Sx, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(sweeps):
+            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / sweeps
+        R = Sx * Ax
+        nbytes = R * Kx * 12 + R * 16 + Sx * 20
+        peak, _ = load_peaks()
+        out["bellman"] = {"ms_per_sweep": ms, "bytes": nbytes, "GB/s": nbytes / ms / 1e6,
+                          "frac": nbytes / ms / 1e6 / peak, "fp64_fma_per_s": R * Kx / (ms * 1e-3)}
+        for name, prec in (("solve_f64", mdp.MDP_PREC_F64), ("solve_mixed", mdp.MDP_PREC_MIXED)):
+            o = mdp.mdp_default_opts()
+            o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.precision = gx, 1e-8, 1e-4, 30, prec
+            for rep in range(2):  # the first call allocates the Krylov workspace
+                V.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, stats = mdp.mdp_solve(M.h, o, V, pi, stream)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            mdp.check(st, "mdp_solve")
+            out[name] = {"s": dt, "outer": stats.outer_iters, "inner": stats.inner_iters_total,
+                         "final_residual": stats.final_residual, "policy_value_bytes": stats.policy_value_bytes}
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_pendulum():
+    """The pendulum grid at full size (1000 x 1000 states, A = 9, 4 entries per row,
+    gamma = 0.9999): Algorithm 1 to tol = 1e-8 with the Table 1 defaults (alpha = 1e-4,
+    at most 1000 outer and 1000 inner iterations) and GMRES(30), FP64 and mixed, and
+    with TFQMR; then the variant whose bilinear weights are rounded to 2^-8 (exact in
+    bfloat16), FP64 against mixed with bfloat16 policy values."""
+    import torch
+
+    from mdpgen import pendulum_grid
+    from paper_2507_22538_gb300 import mdp
+    out = {"workload": "pendulum grid 1000 x 1000, A=9, k=4, gamma=0.9999, Ts=0.01", "tol": 1e-8, "alpha": 1e-4}
+    stream = torch.cuda.current_stream()
+    for tag, qb in (("", None), ("bf16_exact_", 8)):
+        m = pendulum_grid(1000, 1000, 9, 0.9999, seed=3, quant_bits=qb)
+        runs = (("gmres_f64", mdp.MDP_GMRES, mdp.MDP_PREC_F64), ("gmres_mixed", mdp.MDP_GMRES, mdp.MDP_PREC_MIXED))
+        if qb is None:
+            runs += (("tfqmr_f64", mdp.MDP_TFQMR, mdp.MDP_PREC_F64),)
+        with mdp.MDP.from_data(m, stream) as M:
+            V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+            pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+            for name, inner, prec in runs:
+                o = mdp.mdp_default_opts()
+                o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.inner, o.precision = 0.9999, 1e-8, 1e-4, 30, inner, prec
+                V.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, stats = mdp.mdp_solve(M.h, o, V, pi, stream)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                out[tag + name] = {"s": dt, "status": st, "outer": stats.outer_iters, "inner": stats.inner_iters_total,
+                                   "final_residual": stats.final_residual,
+                                   "policy_value_bytes": stats.policy_value_bytes}
+    return out
 
 
 def run_bellman_only(args):
@@ -370,6 +460,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quantized", dest="quantized", action="store_false",
                     help="skip the binary16-exact variant of the workload")
+    ap.add_argument("--no-pendulum", dest="pendulum", action="store_false",
+                    help="skip the full-size pendulum grid solves (gamma = 0.9999)")
+    ap.add_argument("--no-stress", dest="stress", action="store_false",
+                    help="skip the 2.05e9-entry random workload (sweep roofline and two solves)")
     ap.add_argument("--serve", type=int, default=64, metavar="N",
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
@@ -568,6 +662,10 @@ def main():
             "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks}
     if args.serve > 0:
         line["serving"] = run_serving(args.serve)
+    if args.stress:
+        line["bandwidth_stress"] = run_stress()
+    if args.pendulum:
+        line["pendulum"] = run_pendulum()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, info = cpu_oracle_solve()
         line["cpu_baseline"] = {"value": t, "unit": "s", "cores": 1, "kind": "oracle",

@@ -89,7 +89,7 @@ __device__ __forceinline__ int find_problem(const int32_t* __restrict__ start, i
   const int nb = __ldg(start + i + 1) - __ldg(start + i);   \
   const BatchProblem& p = P[i];
 
-__global__ void __launch_bounds__(kBellThreads) bb_bellman_kernel(const BatchProblem* __restrict__ P,
+__global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bb_bellman_kernel(const BatchProblem* __restrict__ P,
                                                                    const int32_t* __restrict__ start, int n) {
   BATCH_PROLOGUE
   if (p.suniform)
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kVecThreads) bb_dots_kernel(const BatchProblem
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kVecThreads) bb_project_kernel(const BatchProblem* __restrict__ P,
+__global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) bb_project_kernel(const BatchProblem* __restrict__ P,
                                                                   const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
   gm_project_body<NB, kPlain, double>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kVecThreads) bb_dots_f_kernel(const BatchProbl
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kVecThreads) bb_project_f_kernel(const BatchProblem* __restrict__ P,
+__global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) bb_project_f_kernel(const BatchProblem* __restrict__ P,
                                                                     const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
   gm_project_body<NB, kPlain, float>(bid, nb, p.S, p.basis32, j, p.w32, p.partials, p.K);

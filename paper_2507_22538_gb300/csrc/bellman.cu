@@ -5,7 +5,7 @@
 namespace mdp {
 
 template <bool UNIFORM>
-__global__ void __launch_bounds__(kBellThreads) bellman_kernel(
+__global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_kernel(
     const double* __restrict__ sval, const int32_t* __restrict__ scol, const int64_t* __restrict__ off,
     const int32_t* __restrict__ len, int k, const double* __restrict__ g, const double* __restrict__ V, int64_t S,
     int A, int TS, double gamma, double* __restrict__ TV, int32_t* __restrict__ pi,

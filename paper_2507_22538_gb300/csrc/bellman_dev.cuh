@@ -17,6 +17,10 @@
 namespace mdp {
 
 constexpr int kBellThreads = 256;
+// At least 6 resident blocks per SM: the register cap (40) keeps the chunk loads
+// unspilled and gives 48 warps per SM for the V gathers; at 48 registers (5
+// blocks) the full-size sweep measured 4% slower.
+constexpr int kBellMinBlocks = 6;
 
 __device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
 

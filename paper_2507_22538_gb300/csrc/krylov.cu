@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T
 }
 
 template <int NB, int MODE, typename T>
-__global__ void __launch_bounds__(kVecThreads) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
+__global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
                                                                   const T* __restrict__ w, double* partials,
                                                                   KrylovState* K) {
   gm_project_body<NB, MODE, T>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from mdpgen import (banded_birth_death, pendulum_grid, philox4x32, quantize_rows, random_sparse,
                     regenerate_rows)
@@ -83,3 +84,45 @@ def test_regenerate_rows_matches_full_build():
         lo, hi = b.row_ptr[r], b.row_ptr[r + 1]
         assert np.array_equal(c[i], b.col[lo:hi]) and np.array_equal(p[i], b.val[lo:hi])
         assert g[i] == b.g[r]
+
+
+def test_torch_philox_known_answers():
+    """The tensor Philox (used to build large workloads on the device) on the same
+    Random123 known-answer vectors."""
+    import torch
+
+    from mdpgen.torch_gen import philox4x32 as tphilox
+    cases = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, expect in cases:
+        out = tphilox(*(torch.tensor([c], dtype=torch.int64) for c in ctr), *key)
+        assert tuple(int(x[0]) for x in out) == expect
+
+
+@pytest.mark.parametrize("conc,quant", [(1.0, None), (0.5, None), (0.5, 11)])
+def test_torch_generator_matches_numpy(conc, quant):
+    """random_sparse_device (run here on the CPU) against random_sparse: columns, row
+    pointers and costs bit for bit; probabilities to rounding, and quantised ones
+    equal in all but rare rows, each row summing to exactly 1."""
+    import torch
+
+    from mdpgen.torch_gen import random_sparse_device
+    m = random_sparse(3000, 5, 16, 0.99, seed=12, conc=conc, quant_bits=quant)
+    rp, col, val, g = random_sparse_device(3000, 5, 16, 0.99, seed=12, conc=conc, quant_bits=quant, device="cpu",
+                                           chunk_rows=4096)
+    assert np.array_equal(rp.numpy(), m.row_ptr)
+    assert np.array_equal(col.numpy(), m.col)
+    assert np.array_equal(g.numpy(), m.g)
+    v = val.numpy().reshape(-1, 16)
+    ref = m.val.reshape(-1, 16)
+    if quant is None:
+        np.testing.assert_allclose(v, ref, rtol=1e-13, atol=1e-16)
+    else:
+        same = np.all(v == ref, axis=1)
+        assert same.mean() > 0.999
+        assert np.all(v.sum(axis=1) == 1.0)
+        assert np.all(v * 2048 == np.floor(v * 2048))
