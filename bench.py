@@ -194,23 +194,42 @@ def run_reference(args):
     return 0
 
 
+class DeviceRequest:
+    """A request of the counter-based serving stream, drawn on the device (CUDA
+    generator) when a worker admits it: the stand-in for the client's upload."""
+
+    def __init__(self, rid, seed, **ranges):
+        from mdpgen import request_header
+        self.rid, self.seed, self.ranges = rid, seed, ranges
+        self.S, self.A, self.k, self.gamma = request_header(rid, seed, **ranges)
+        self.nnz, self.kmax = self.S * self.A * self.k, self.k
+
+    def device_arrays(self):
+        from mdpgen.cuda_gen import serving_request_cuda
+        return serving_request_cuda(self.rid, self.seed, **self.ranges)[4:]
+
+
+SERVE_MIX = dict(s_range=(1_000, 1_000_000), a_range=(2, 32), k_range=(4, 64), gammas=(0.9, 0.99, 0.999, 0.9999))
+
+
 def run_serving(n, slots=4, seed=5):
-    """Continuous-batching measurement: n requests of mixed S (log-uniform 1e3..1e5),
-    A (2..16), k (4..32) and gamma (0.9..0.9999), Poisson arrivals at 0.8 of the
-    one-at-a-time rate (and a burst of all n at once), admitted by a 120 GB HBM budget
-    into `slots` concurrent solves, each solve one request or (batch_max 8) up to 8
-    same-gamma requests stacked block-diagonally."""
+    """Continuous-batching measurement on the serving stream: n requests with S
+    log-uniform in [1e3, 1e6], A in [2, 32], k in [4, 64] entries per row and gamma in
+    {0.9, 0.99, 0.999, 0.9999}, each drawn on the device at admission; Poisson
+    arrivals at 0.8 of the one-at-a-time rate (and a burst of all n at once),
+    admitted by a 120 GB HBM budget into `slots` concurrent solves, each solve one
+    request or (batch_max 8) up to 8 requests through mdp_solve_batch."""
     import numpy as np
 
-    from mdpgen import serving_request
+    from mdpgen.cuda_gen import load as load_gen
     from paper_2507_22538_gb300.serve import (Request, SolveService, fifo_one_at_a_time, latency_summary,
                                               solve_alone)
-    mix = dict(s_range=(1_000, 100_000), a_range=(2, 16), k_range=(4, 32), gammas=(0.9, 0.99, 0.999, 0.9999))
-    reqs = [Request(i, serving_request(i, seed=seed, **mix), tol=1e-8, alpha=1e-3) for i in range(n)]
-    solve_alone(reqs[0])  # warm-up
+    load_gen()
+    reqs = [Request(i, DeviceRequest(i, seed, **SERVE_MIX), tol=1e-8, alpha=1e-3) for i in range(n)]
+    for r in reqs[:3]:
+        solve_alone(r)  # warm-up
     alone = [solve_alone(r) for r in reqs]
-    again = [solve_alone(r) for r in reqs]  # service time: the faster of two stand-alone runs
-    service = np.array([min(a.finished, b.finished) for a, b in zip(alone, again)])
+    service = np.array([a.finished for a in alone])
     rate = 0.8 / float(service.mean())
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -231,17 +250,20 @@ def run_serving(n, slots=4, seed=5):
         return out, summ, svc
 
     res, cont, svc = drive(arrivals, 1)
-    # the same arrivals, and a burst of all n at once, with same-gamma requests stacked
-    # block-diagonally (up to 8 per solve)
-    _, cont_b, _ = drive(arrivals, 8)
+    # the same arrivals, and a burst of all n at once, with waiting requests solved
+    # together by mdp_solve_batch (up to 8 per call)
+    resb, cont_b, _ = drive(arrivals, 8)
     burst = np.zeros(n)
     _, burst1, _ = drive(burst, 1)
     _, burst8, _ = drive(burst, 8)
-    same = all(np.array_equal(alone[r.rid].V, res[r.rid].V) and np.array_equal(alone[r.rid].pi, res[r.rid].pi)
-               for r in reqs)
+    same = all(np.array_equal(alone[r.rid].V, out[r.rid].V) and np.array_equal(alone[r.rid].pi, out[r.rid].pi)
+               for out in (res, resb) for r in reqs)
+    nnz = np.array([r.data.nnz for r in reqs], dtype=np.float64)
     return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
-            "mix": "S log-uniform 1e3..1e5, A 2..16, k 4..32, gamma in {0.9,0.99,0.999,0.9999}, GMRES(30), "
-                   "alpha 1e-3, tol 1e-8",
+            "mix": "S log-uniform 1e3..1e6, A 2..32, k 4..64, gamma in {0.9,0.99,0.999,0.9999}, Dirichlet(1), "
+                   "GMRES(30), alpha 1e-3, tol 1e-8; drawn on the device at admission (counted in the latency)",
+            "entries_per_request": {"mean": float(nnz.mean()), "max": float(nnz.max())},
+            "one_at_a_time_mean_s": float(service.mean()),
             "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same)}
@@ -464,7 +486,7 @@ def main():
                     help="skip the full-size pendulum grid solves (gamma = 0.9999)")
     ap.add_argument("--no-stress", dest="stress", action="store_false",
                     help="skip the 2.05e9-entry random workload (sweep roofline and two solves)")
-    ap.add_argument("--serve", type=int, default=64, metavar="N",
+    ap.add_argument("--serve", type=int, default=200, metavar="N",
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
                     help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
@@ -530,14 +552,19 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
+        marks = []
         for _ in range(args.steps):
             s = step()
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            marks.append(ev)
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
                         "inner_ms", "inner_bytes"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
         torch.cuda.synchronize()
+        step_ms = [e0.elapsed_time(marks[0])] + [a.elapsed_time(b) for a, b in zip(marks, marks[1:])]
     if dist:
         dist.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
@@ -659,7 +686,8 @@ def main():
                            "inner_per_step": totals["inner_iters_total"] / args.steps,
                            "max_final_residual": totals["final_residual"]},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks}
+            "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}
     if args.serve > 0:
         line["serving"] = run_serving(args.serve)
     if args.stress:

@@ -337,6 +337,49 @@ def serving_request(rid: int, seed: int = 5, s_range=(1_000, 1_000_000), a_range
     return MDPData(S, A, row_ptr, col, val, g, gamma, f"request{rid}(S={S},A={A},k={k},gamma={gamma})")
 
 
+TAG_REQ = 0x72657173  # "reqs"
+REQUEST_ROW_BITS = 40  # request rid's rows use Philox row counters rid * 2**40 + r
+
+
+def request_header(rid: int, seed: int, s_range=(1_000, 1_000_000), a_range=(2, 32), k_range=(4, 64),
+                   gammas=(0.9, 0.99, 0.999, 0.9999)):
+    """(S, A, k, gamma) of request rid of the counter-based serving stream: S
+    log-uniform in s_range, A and k uniform in their ranges (k <= S), gamma drawn
+    from `gammas`; four Philox draws at counter (rid, 0..3)."""
+    u = stream(seed, TAG_REQ, np.uint64(rid), np.arange(4, dtype=np.uint64))
+    lo, hi = math.log(s_range[0]), math.log(s_range[1])
+    S = int(round(math.exp(lo + float(u[0]) * (hi - lo))))
+    A = a_range[0] + min(int(float(u[1]) * (a_range[1] - a_range[0] + 1)), a_range[1] - a_range[0])
+    k = min(S, k_range[0] + min(int(float(u[2]) * (k_range[1] - k_range[0] + 1)), k_range[1] - k_range[0]))
+    gamma = float(gammas[min(int(float(u[3]) * len(gammas)), len(gammas) - 1)])
+    return S, A, k, gamma
+
+
+def serving_request_philox(rid: int, seed: int = 5, s_range=(1_000, 1_000_000), a_range=(2, 32),
+                           k_range=(4, 64), gammas=(0.9, 0.99, 0.999, 0.9999)) -> MDPData:
+    """Request rid of the counter-based serving stream (the header of
+    request_header).  Row r of the request draws from Philox row counter
+    rid * 2**40 + r: k uniform columns with replacement (draw j at block j,
+    sorted; a repeated column adds its probabilities), Dirichlet(1) weights
+    -log(1 - U) (block k + j), normalised, and a cost U[0, 1) (stream TAG_COST).
+    Any request, or any row of it, is reproducible alone, and
+    mdpgen.torch_gen.serving_request_device draws the same request on the
+    device."""
+    S, A, k, gamma = request_header(rid, seed, s_range, a_range, k_range, gammas)
+    R = S * A
+    rows = (np.uint64(rid) << np.uint64(REQUEST_ROW_BITS)) + np.arange(R, dtype=np.uint64)
+    j = np.arange(k, dtype=np.uint64)[None, :]
+    u = stream(seed, TAG_COLS, rows[:, None], j)
+    col = np.minimum(np.floor(u * S).astype(np.int64), S - 1)
+    col.sort(axis=1)
+    w = -np.log1p(-stream(seed, TAG_VALS, rows[:, None], j + np.uint64(k)))
+    val = w / w.sum(axis=1, keepdims=True)
+    g = stream(seed, TAG_COST, rows, np.uint64(0))
+    row_ptr = np.arange(R + 1, dtype=np.int64) * k
+    return MDPData(S, A, row_ptr, col.astype(np.int32).ravel(), val.ravel(), g, gamma,
+                   f"request{rid}(S={S},A={A},k={k},gamma={gamma})")
+
+
 def random_value_vector(S: int, seed: int, scale: float = 1.0) -> np.ndarray:
     """A seeded test vector V ~ scale * U[-1, 1) of length S."""
     u = stream(seed, TAG_NOISE ^ 0x5A5A, np.arange(S, dtype=np.uint64), np.uint64(1))

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import math
 
-from .generators import TAG_COLS, TAG_COST, TAG_VALS
+from .generators import REQUEST_ROW_BITS, TAG_COLS, TAG_COST, TAG_VALS, request_header
 
 _M0 = 0xD2511F53
 _M1 = 0xCD9E8D57
@@ -116,3 +116,32 @@ def random_sparse_device(S: int, A: int, k: int, gamma: float, seed: int, conc: 
                torch.tensor(0, dtype=torch.int64, device=device))
     row_ptr = torch.arange(R + 1, dtype=torch.int64, device=device) * k
     return row_ptr, col, val, g
+
+
+def serving_request_device(rid: int, seed: int = 5, s_range=(1_000, 1_000_000), a_range=(2, 32), k_range=(4, 64),
+                           gammas=(0.9, 0.99, 0.999, 0.9999), device="cuda", chunk_rows: int = 1 << 21):
+    """Request rid of generators.serving_request_philox drawn with tensor ops:
+    (S, A, k, gamma, row_ptr, col, val, g) with device tensors.  Columns and costs
+    equal the numpy draw bit for bit; probabilities agree to rounding."""
+    import torch
+    S, A, k, gamma = request_header(rid, seed, s_range, a_range, k_range, gammas)
+    R = S * A
+    col = torch.empty(R * k, dtype=torch.int32, device=device)
+    val = torch.empty(R * k, dtype=torch.float64, device=device)
+    j = torch.arange(k, dtype=torch.int64, device=device)[None, :]
+    base = rid << REQUEST_ROW_BITS
+    for r0 in range(0, R, chunk_rows):
+        r1 = min(R, r0 + chunk_rows)
+        rows = base + torch.arange(r0, r1, dtype=torch.int64, device=device)[:, None]
+        u = stream(seed, TAG_COLS, rows, j)
+        c = torch.clamp(torch.floor(u * S).to(torch.int64), max=S - 1)
+        c, _ = torch.sort(c, dim=1)
+        w = -torch.log1p(-stream(seed, TAG_VALS, rows, j + k))
+        p = w / w.sum(dim=1, keepdim=True)
+        col[r0 * k:r1 * k] = c.reshape(-1).to(torch.int32)
+        val[r0 * k:r1 * k] = p.reshape(-1)
+        del u, c, w, p
+    g = stream(seed, TAG_COST, base + torch.arange(R, dtype=torch.int64, device=device),
+               torch.tensor(0, dtype=torch.int64, device=device))
+    row_ptr = torch.arange(R + 1, dtype=torch.int64, device=device) * k
+    return S, A, k, gamma, row_ptr, col, val, g

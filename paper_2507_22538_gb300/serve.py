@@ -26,7 +26,10 @@ from . import mdp
 @dataclasses.dataclass
 class Request:
     rid: int
-    data: object  # an MDPData-like object: S, A, row_ptr, col, val, g, gamma
+    # an MDPData-like object (S, A, row_ptr, col, val, g, gamma as host arrays), or
+    # one with S, A, gamma, nnz, kmax and device_arrays() -> (row_ptr, col, val, g)
+    # device tensors made when a worker admits the request (on the worker's stream)
+    data: object
     tol: float = 1e-8
     alpha: float = 1e-3
     inner: int = mdp.MDP_GMRES
@@ -58,8 +61,11 @@ def device_bytes(data, restart: int = 30, precision: int = mdp.MDP_PREC_F64) -> 
     sliced layout (12 B per entry), its temporary CSR copy during upload, the
     policy rows, costs, work vectors and the Krylov basis."""
     S, A = int(data.S), int(data.A)
-    nnz = int(data.row_ptr[-1])
-    kmax = int(np.max(np.diff(data.row_ptr))) if S * A else 0
+    if hasattr(data, "device_arrays"):  # drawn on the device at admission: sizes known up front
+        nnz, kmax = int(data.nnz), int(data.kmax)
+    else:
+        nnz = int(data.row_ptr[-1])
+        kmax = int(np.max(np.diff(data.row_ptr))) if S * A else 0
     return _footprint(S, A, nnz, kmax, restart, precision)
 
 
@@ -70,6 +76,16 @@ def _footprint(S, A, nnz, kmax, restart, precision) -> int:
     basis = 8 * (restart + 1) * S + (4 * (restart + 1) * S if precision == mdp.MDP_PREC_MIXED else 0)
     vectors = 16 * 8 * S
     return stacked + upload + policy + basis + vectors + (1 << 20)
+
+
+def _create(d, stream):
+    """mdp_create from host arrays, or from device arrays the request makes now."""
+    if hasattr(d, "device_arrays"):
+        rp, col, val, g = d.device_arrays()
+        out = mdp.mdp_create(d.S, d.A, rp, col, val, g, True, stream)  # copies; returns after the copy
+        del rp, col, val, g
+        return out
+    return mdp.mdp_create(d.S, d.A, d.row_ptr, d.col, d.val, d.g, False, stream)
 
 
 class SolveService:
@@ -203,7 +219,7 @@ class SolveService:
         import torch
         d = req.data
         with torch.cuda.stream(stream):
-            st, h = mdp.mdp_create(d.S, d.A, d.row_ptr, d.col, d.val, d.g, False, stream)
+            st, h = _create(d, stream)
             mdp.check(st, f"mdp_create (request {req.rid})")
             try:
                 o = mdp.mdp_default_opts()
@@ -225,8 +241,7 @@ class SolveService:
         with torch.cuda.stream(stream):
             try:
                 for r in batch:
-                    d = r.data
-                    st, h = mdp.mdp_create(d.S, d.A, d.row_ptr, d.col, d.val, d.g, False, stream)
+                    st, h = _create(r.data, stream)
                     mdp.check(st, f"mdp_create (request {r.rid})")
                     handles.append(h)
                 opts = []

@@ -84,3 +84,65 @@ def test_batched_service_equals_alone():
         assert out.status == alone.status
         assert np.array_equal(out.V, alone.V) and np.array_equal(out.pi, alone.pi)
         assert (out.outer_iters, out.inner_iters) == (alone.outer_iters, alone.inner_iters)
+
+
+def test_cuda_request_generator_matches_numpy():
+    """The CUDA draw of the counter-based serving requests against the numpy draw:
+    columns and costs bit for bit, probabilities to rounding."""
+    from mdpgen import serving_request_philox
+    from mdpgen.cuda_gen import serving_request_cuda
+    rng = dict(s_range=(300, 4000), a_range=(2, 9), k_range=(4, 64))
+    for rid in (0, 3, 99):
+        m = serving_request_philox(rid, seed=11, **rng)
+        S, A, k, gamma, rp, col, val, g = serving_request_cuda(rid, seed=11, **rng)
+        assert (S, A, gamma) == (m.S, m.A, m.gamma)
+        assert np.array_equal(rp.cpu().numpy(), m.row_ptr)
+        assert np.array_equal(col.cpu().numpy(), m.col)
+        assert np.array_equal(g.cpu().numpy(), m.g)
+        np.testing.assert_allclose(val.cpu().numpy(), m.val, rtol=1e-13, atol=0)
+
+
+class DeviceRequest:
+    """A counter-based request drawn on the device when the service admits it."""
+
+    def __init__(self, rid, seed, **ranges):
+        from mdpgen import request_header
+        self.rid, self.seed, self.ranges = rid, seed, ranges
+        self.S, self.A, self.k, self.gamma = request_header(rid, seed, **ranges)
+        self.nnz, self.kmax = self.S * self.A * self.k, self.k
+
+    def device_arrays(self):
+        from mdpgen.cuda_gen import serving_request_cuda
+        return serving_request_cuda(self.rid, self.seed, **self.ranges)[4:]
+
+
+def test_device_drawn_requests_equal_alone_and_certified():
+    """Requests drawn on the device at admission, served continuously with and
+    without batching: each result equals the request solved alone, and the oracle
+    certifies the smaller ones (regenerated on the host by the numpy draw)."""
+    from mdpgen import serving_request_philox
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.serve import Request, SolveService, solve_alone
+    from tests._util import q_tolerance
+    rng = dict(s_range=(300, 30_000), a_range=(2, 12), k_range=(4, 40), gammas=(0.9, 0.99, 0.999))
+    reqs = [Request(i, DeviceRequest(i, 17, **rng), tol=1e-8, alpha=1e-3) for i in range(12)]
+    alone = {r.rid: solve_alone(r) for r in reqs}
+    for batch_max in (1, 4):
+        svc = SolveService(slots=2, batch_max=batch_max).start()
+        for r in reqs:
+            svc.submit(r)
+        res = svc.wait(len(reqs))
+        svc.close()
+        for r in reqs:
+            assert res[r.rid].status == mdp.MDP_OK
+            assert np.array_equal(res[r.rid].V, alone[r.rid].V) and np.array_equal(res[r.rid].pi, alone[r.rid].pi)
+    for r in reqs:
+        if r.data.S * r.data.A * r.data.k > 300_000:
+            continue
+        m = serving_request_philox(r.rid, 17, **rng)
+        V = alone[r.rid].V
+        P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+        Q = O.q_values(P, m.g, m.gamma, V, m.S, m.A)
+        # the device draw's probabilities differ from the host draw's by rounding, which
+        # moves Q by at most a few ulps of gamma * ||V||
+        assert float(np.max(np.abs(Q.min(axis=1) - V))) <= 1e-8 + 4 * q_tolerance(m, V)

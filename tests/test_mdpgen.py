@@ -126,3 +126,34 @@ def test_torch_generator_matches_numpy(conc, quant):
         assert same.mean() > 0.999
         assert np.all(v.sum(axis=1) == 1.0)
         assert np.all(v * 2048 == np.floor(v * 2048))
+
+
+def test_serving_request_philox_device_matches_numpy():
+    """The counter-based serving request drawn with tensor ops (here on the CPU)
+    against the numpy draw: header, columns and costs bit for bit, probabilities
+    to rounding; every row sums to 1 and columns lie in [0, S)."""
+    from mdpgen import request_header, serving_request_philox
+    from mdpgen.torch_gen import serving_request_device
+    rng = dict(s_range=(200, 3000), a_range=(2, 6), k_range=(3, 9))
+    for rid in (0, 1, 7, 123456):
+        m = serving_request_philox(rid, seed=3, **rng)
+        S, A, k, gamma, rp, col, val, g = serving_request_device(rid, seed=3, device="cpu", chunk_rows=1000, **rng)
+        assert (S, A, k, gamma) == (m.S, m.A, int(m.row_ptr[1]), m.gamma) == request_header(rid, 3, **rng)[:3] + (gamma,)
+        assert np.array_equal(rp.numpy(), m.row_ptr) and np.array_equal(col.numpy(), m.col)
+        assert np.array_equal(g.numpy(), m.g)
+        np.testing.assert_allclose(val.numpy(), m.val, rtol=1e-13, atol=0)
+        assert m.col.min() >= 0 and m.col.max() < S
+        np.testing.assert_allclose(m.val.reshape(-1, k).sum(axis=1), 1.0, rtol=0, atol=1e-14)
+        assert np.all(np.diff(m.col.reshape(-1, k), axis=1) >= 0)
+
+
+def test_request_header_ranges():
+    from mdpgen import request_header
+    hs = [request_header(r, 5) for r in range(400)]
+    S = np.array([h[0] for h in hs])
+    assert S.min() >= 1000 and S.max() <= 1_000_000
+    assert {h[1] for h in hs} <= set(range(2, 33)) and len({h[1] for h in hs}) > 20
+    assert {h[2] for h in hs} <= set(range(4, 65))
+    assert {h[3] for h in hs} == {0.9, 0.99, 0.999, 0.9999}
+    # log-uniform: about a third of the requests below 1e4
+    assert 0.2 < np.mean(S < 10_000) < 0.45
