@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "layout_dev.cuh"
@@ -33,13 +34,33 @@ enum : int {
   kLongRow = 64,
 };
 
-// One thread per row of Eq. 5: check the CSR invariants and record the row length.
+// Whether a finite double v >= 0 is exactly a binary16 / bfloat16 value, read off its
+// IEEE-754 fields: with unbiased exponent e, a normal target (e >= emin) keeps `p`
+// fraction bits, a subnormal one (emin - p <= e < emin) keeps e - (emin - p) of them,
+// and every dropped fraction bit must be zero.  (binary16: p = 10, emin = -14;
+// bfloat16: p = 7, emin = -126.)
+__device__ __forceinline__ bool exact_in(uint64_t bits, int p, int emin, int emax) {
+  if ((bits << 1) == 0) return true;  // +-0
+  const int ebits = (int)((bits >> 52) & 0x7ff);
+  if (ebits == 0) return false;  // a double subnormal is below both formats' range
+  const int e = ebits - 1023;
+  if (e > emax || e < emin - p) return false;
+  const int kept = e >= emin ? p : e - (emin - p);
+  const uint64_t dropped = (1ull << (52 - kept)) - 1;
+  return (bits & dropped) == 0;
+}
+
+// One thread per row of Eq. 5: check the CSR invariants, record the row length and
+// whether every probability is exact in binary16 / bfloat16 (the narrowest exact
+// storage for the mixed solver's copies of the policy rows).
 __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                      const double* __restrict__ val, const double* __restrict__ g, int64_t R,
                                      int64_t S, int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
-                                     int* __restrict__ kmin, int* __restrict__ kmax) {
+                                     int* __restrict__ kmin, int* __restrict__ kmax, int* __restrict__ f16_ok,
+                                     int* __restrict__ bf16_ok) {
   int bad = 0;
   int lmin = 0x7fffffff, lmax = 0;
+  bool a16 = true, b16 = true;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
     int64_t lo = rp[r], hi = rp[r + 1];
     int l = 0;
@@ -57,6 +78,9 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
         double v = val[j];
         if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
         if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
+        const uint64_t bits = (uint64_t)__double_as_longlong(v);
+        a16 &= exact_in(bits, 10, -14, 15);
+        b16 &= exact_in(bits, 7, -126, 127);
         sum += v;
       }
       if (!(fabs(sum - 1.0) <= 1e-12)) bad |= kRowSum;
@@ -69,19 +93,8 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
   if (bad) atomicOr(flags, bad);
   atomicMin(kmin, lmin);
   atomicMax(kmax, lmax);
-}
-
-// Whether every probability is exactly representable in binary16 / bfloat16.
-__global__ void narrow_exact_kernel(const double* __restrict__ val, int64_t nnz, int* __restrict__ f16_ok,
-                                    int* __restrict__ bf16_ok) {
-  bool a = true, b = true;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
-    const double v = val[j];
-    a &= ((double)__half2float(__double2half(v)) == v);
-    b &= ((double)__bfloat162float(__double2bfloat16(v)) == v);
-  }
-  if (!__all_sync(0xffffffffu, a) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
-  if (!__all_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
+  if (!__all_sync(0xffffffffu, a16) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
+  if (!__all_sync(0xffffffffu, b16) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
 }
 
 // Width of each slice of `rows` rows: the longest row among its 32.
@@ -308,12 +321,33 @@ mdp_status ensure_basis(mdp_s* h, int nvec) {
   return MDP_OK;
 }
 
+// The stream-ordered pool that every device buffer of the library comes from
+// keeps up to an eighth of the device's memory across synchronisations (the
+// default returns all of it to the driver at each one), so handles created and
+// destroyed in turn reuse their buffers instead of mapping memory again.  This is
+// the process's default pool of the device: the setting ends with the process.
+static mdp_status retain_pool(int device) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (device < 0 || device >= 64 || done[device]) return MDP_OK;
+  size_t free_b = 0, total_b = 0;
+  MDP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  cudaMemPool_t pool;
+  MDP_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+  uint64_t keep = (uint64_t)(total_b / 8);
+  MDP_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  done[device] = true;
+  return MDP_OK;
+}
+
 static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
                               mdp_dtype val_type, const double* g, int32_t on_device, cudaStream_t st,
                               mdp_s* h) {
   h->stream = st;
   MDP_CUDA(cudaGetDevice(&h->device));
   MDP_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+  MDP_TRY(retain_pool(h->device));
   h->S = S;
   h->A = A;
   h->R = S * (int64_t)A;
@@ -362,13 +396,14 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(h, &dlen, R, "row lengths"));
   struct FreeLen { cudaStream_t st; int32_t** p; ~FreeLen() { dfree(st, *p); } } free_len{st, &dlen};
   int* dflags = (int*)h->sc;
-  int init[3] = {0, 0x7fffffff, 0};
+  int init[5] = {0, 0x7fffffff, 0, 1, 1};
   MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
   validate_rows_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, dcol, dval, h->g, R, S, nnz, dlen,
-                                                                    dflags, dflags + 1, dflags + 2);
+                                                                    dflags, dflags + 1, dflags + 2, dflags + 3,
+                                                                    dflags + 4);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
-  int res[3];
+  int res[5];
   MDP_CUDA(cudaMemcpyAsync(res, dflags, sizeof(res), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   if (res[0]) {
@@ -386,16 +421,7 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   const int kmin = res[1], kmax = res[2];
 
   // narrowest exact storage for the mixed solver's copies of the policy rows
-  {
-    int ok[2] = {1, 1};
-    MDP_CUDA(cudaMemcpyAsync(dflags + 4, ok, sizeof(ok), cudaMemcpyHostToDevice, st));
-    narrow_exact_kernel<<<grid_for(nnz, 256, h->sm_count), 256, 0, st>>>(dval, nnz, dflags + 4, dflags + 5);
-    h->launches++;
-    MDP_CUDA(cudaGetLastError());
-    MDP_CUDA(cudaMemcpyAsync(ok, dflags + 4, sizeof(ok), cudaMemcpyDeviceToHost, st));
-    MDP_CUDA(cudaStreamSynchronize(st));
-    h->pstore = ok[0] ? kStoreF16 : (ok[1] ? kStoreBF16 : kStoreF32);
-  }
+  h->pstore = res[3] ? kStoreF16 : (res[4] ? kStoreBF16 : kStoreF32);
 
   // stacked matrix in sliced layout
   MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));
