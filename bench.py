@@ -289,6 +289,9 @@ def run_stress(sweeps=10):
     with mdp.MDP(Sx, Ax, rp, col, val, g, stream) as M:
         del rp, col, val, g
         torch.cuda.empty_cache()
+        st_t, tile_states, _ = mdp.mdp_tune(M.h, gx, stream)
+        mdp.check(st_t, "mdp_tune")
+        out["tile_states"] = tile_states
         V = torch.zeros(Sx, dtype=torch.float64, device="cuda")
         TV = torch.empty_like(V)
         pi = torch.empty(Sx, dtype=torch.int32, device="cuda")
@@ -369,6 +372,8 @@ def run_bellman_only(args):
     m = banded_birth_death(args.states, A, H, GAMMA)
     stream = torch.cuda.current_stream()
     with mdp.MDP.from_data(m, stream) as M:
+        st_t, tile_states, _ = mdp.mdp_tune(M.h, GAMMA, stream)
+        mdp.check(st_t, "mdp_tune")
         V = torch.from_numpy(random_value_vector(m.S, 1, 1000.0)).cuda()
         TV = torch.empty_like(V)
         pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
@@ -397,7 +402,8 @@ def run_bellman_only(args):
     peak, _ = load_peaks()
     print(json.dumps({"mode": "bellman_only", "S": m.S, "ms_per_sweep": ms, "bytes": nbytes,
                       "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
-                      "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes}), flush=True)
+                      "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes,
+                      "tile_states": tile_states}), flush=True)
     return 0
 
 
@@ -414,6 +420,7 @@ def run_solve_only(args):
     stream = torch.cuda.current_stream()
     prec = mdp.MDP_PREC_MIXED if args.solve_only == "mixed" else mdp.MDP_PREC_F64
     with mdp.MDP.from_data(m, stream) as M:
+        mdp.check(mdp.mdp_tune(M.h, GAMMA, stream)[0], "mdp_tune")
         V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
         pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
         o = mdp.mdp_default_opts()
@@ -530,6 +537,8 @@ def main():
     m = banded_birth_death(S, A, H, GAMMA)
     stream = torch.cuda.current_stream()
     M = mdp.MDP.from_data(m, stream)
+    st_t, tile_states, tune_ms = mdp.mdp_tune(M.h, GAMMA, stream)  # launch-shape autotuner, outside the timing
+    mdp.check(st_t, "mdp_tune")
     V = torch.zeros(S, dtype=torch.float64, device="cuda")
     pi = torch.empty(S, dtype=torch.int32, device="cuda")
     opts = mdp.mdp_default_opts()
@@ -664,7 +673,7 @@ def main():
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "traffic": sweep_traffic(),
                 "bytes_per_launch": bellman_bytes(), "avg_launch_ms": bell_ms,
-                "share_of_step": share_bell}
+                "share_of_step": share_bell, "tile_states": tile_states}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}

@@ -190,6 +190,22 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_
                      mdp_solve_stats* stats, void* stream);
 
 /*
+ * mdp_tune -- autotune the launch shape of the Bellman sweep (Eq. 3-4) on this
+ * handle's matrix: times the fused sweep at V = 0 for each tile size (states per
+ * block: 8 .. 512 that fit in shared memory) and keeps the fastest, which every
+ * later mdp_bellman, mdp_solve and mdp_solve_batch call on the handle uses.  The
+ * paper has no counterpart (its sparse kernels are PETSc's).  Results do not
+ * depend on the tile size: every state's Q values, minimum and the residual are
+ * computed the same way in any tile.
+ *
+ *  gamma         discount factor of the timed sweeps, in (0, 1).
+ *  tile_states   host out (may be NULL): the chosen tile size.
+ *  ms_per_sweep  host out (may be NULL): its time per sweep.
+ * Blocks until done.  Overwrites the handle's scratch vectors only.
+ */
+mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_per_sweep, void* stream);
+
+/*
  * mdp_solve_batch -- Algorithm 1 on n independent MDPs at once (problems of
  * different S, A, row lengths and gamma), each with its own options, advanced
  * in lockstep: every kernel launch of the batch covers all problems that are

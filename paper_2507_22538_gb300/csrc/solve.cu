@@ -67,6 +67,52 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
   return MDP_OK;
 }
 
+mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_per_sweep, void* stream) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
+  cudaStream_t st = (cudaStream_t)stream;
+  MDP_TRY(bind_stream(h, st));
+  // the sweep at V = 0 into the handle's own vectors (w, TV, the policy scratch)
+  MDP_CUDA(cudaMemsetAsync(h->w, 0, h->S * sizeof(double), st));
+  auto time_one = [&](float* ms) -> mdp_status {
+    MDP_TRY(launch_bellman(h, gamma, h->w, h->TV, h->piw, st));  // warm-up
+    MDP_CUDA(cudaEventRecord(h->ev0, st));
+    for (int r = 0; r < 3; ++r) MDP_TRY(launch_bellman(h, gamma, h->w, h->TV, h->piw, st));
+    MDP_CUDA(cudaEventRecord(h->ev1, st));
+    MDP_CUDA(cudaEventSynchronize(h->ev1));
+    MDP_CUDA(cudaEventElapsedTime(ms, h->ev0, h->ev1));
+    *ms /= 3.f;
+    return MDP_OK;
+  };
+  const int start = h->bell_tile_states;
+  int best = start;
+  float best_ms = 0.f;
+  MDP_TRY(time_one(&best_ms));
+  static const int kCandidates[] = {8, 16, 32, 64, 128, 256, 512};
+  for (int ts : kCandidates) {
+    if (ts == start || ts > h->S || (size_t)ts * h->A * sizeof(double) > 227 * 1024) continue;
+    h->bell_tile_states = ts;
+    if (configure_bellman(h) != MDP_OK) continue;  // the tile does not fit: skip it
+    float ms = 0.f;
+    mdp_status s = time_one(&ms);
+    if (s != MDP_OK) {
+      h->bell_tile_states = best;
+      configure_bellman(h);
+      return s;
+    }
+    if (ms < 0.98f * best_ms) {  // a clear gain only
+      best = ts;
+      best_ms = ms;
+    }
+  }
+  h->bell_tile_states = best;
+  MDP_TRY(configure_bellman(h));
+  MDP_CUDA(cudaEventRecord(h->done, st));
+  if (tile_states) *tile_states = best;
+  if (ms_per_sweep) *ms_per_sweep = best_ms;
+  return MDP_OK;
+}
+
 mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* stats,
                      void* stream) {
   const auto t0 = std::chrono::steady_clock::now();

@@ -77,6 +77,8 @@ _SIGNATURES = {
     "mdp_solve_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_opts),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_stats),
                                        ctypes.POINTER(ctypes.c_int), _P]),
+    "mdp_tune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                _P]),
     "mdp_last_error": (ctypes.c_char_p, []),
     "mdp_bellman_csr_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                                _P, _P, _P, _P, _P]),
@@ -184,6 +186,14 @@ def mdp_solve(h, opts: mdp_solve_opts, V, pi, stream=None):
     stats = mdp_solve_stats()
     st = load().mdp_solve(h, ctypes.byref(opts), _ptr(V), _ptr(pi), ctypes.byref(stats), _stream(stream))
     return st, stats
+
+
+def mdp_tune(h, gamma, stream=None):
+    """Returns (status, chosen tile size, ms per sweep)."""
+    ts = ctypes.c_int32(0)
+    ms = ctypes.c_float(0.0)
+    st = load().mdp_tune(h, float(gamma), ctypes.byref(ts), ctypes.byref(ms), _stream(stream))
+    return st, ts.value, ms.value
 
 
 def mdp_solve_batch(handles, opts, V, pi, stream=None):

@@ -144,3 +144,20 @@ def test_invalid_inputs_are_rejected(bad):
     st, h = mdp.mdp_create(m.S, m.A, rp, col, val, g, False, stream=0)
     assert st == expect, (st, mdp.mdp_last_error())
     assert not h.value
+
+
+@pytest.mark.parametrize("S,A,k", [(3000, 32, 12), (5000, 3, 7), (700, 100, 5)])
+def test_tune_keeps_results(S, A, k):
+    """mdp_tune picks a tile size by timing; the Bellman outputs stay bit for bit the same."""
+    import torch
+    from mdpgen import random_sparse, random_value_vector
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(S, A, k, 0.95, seed=4)
+    V = torch.from_numpy(random_value_vector(S, 2, 5.0)).cuda()
+    with mdp.MDP.from_data(m) as M:
+        TV0, pi0, r0 = M.bellman(m.gamma, V)
+        st, ts, ms = mdp.mdp_tune(M.h, m.gamma)
+        assert st == mdp.MDP_OK and ts in (8, 16, 32, 64, 128, 256, 512) and ms > 0
+        TV1, pi1, r1 = M.bellman(m.gamma, V)
+        torch.cuda.synchronize()
+    assert torch.equal(TV0, TV1) and torch.equal(pi0, pi1) and torch.equal(r0, r1)
