@@ -247,6 +247,7 @@ def run_serving(n, slots=4, seed=5):
         summ = latency_summary(out)
         if batch_max > 1:
             summ.update(batch_max=batch_max, mean_batch=float(np.mean(svc.batches)), solves=len(svc.batches))
+        summ["oom_retries"] = svc.oom_retries
         return out, summ, svc
 
     res, cont, svc = drive(arrivals, 1)
@@ -256,8 +257,15 @@ def run_serving(n, slots=4, seed=5):
     burst = np.zeros(n)
     _, burst1, _ = drive(burst, 1)
     _, burst8, _ = drive(burst, 8)
-    same = all(np.array_equal(alone[r.rid].V, out[r.rid].V) and np.array_equal(alone[r.rid].pi, out[r.rid].pi)
-               for out in (res, resb) for r in reqs)
+    mism = []
+    for tag, out in (("continuous", res), ("continuous_batched", resb)):
+        for r in reqs:
+            a, b = alone[r.rid], out[r.rid]
+            if not (a.status == b.status and np.array_equal(a.V, b.V) and np.array_equal(a.pi, b.pi)):
+                mism.append({"run": tag, "rid": r.rid, "status_alone": a.status, "status": b.status,
+                             "outer": [a.outer_iters, b.outer_iters], "inner": [a.inner_iters, b.inner_iters],
+                             "max_dV": float(np.max(np.abs(a.V - b.V))) if a.V.shape == b.V.shape and a.V.size else None})
+    same = not mism
     nnz = np.array([r.data.nnz for r in reqs], dtype=np.float64)
     return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
             "mix": "S log-uniform 1e3..1e6, A 2..32, k 4..64, gamma in {0.9,0.99,0.999,0.9999}, Dirichlet(1), "
@@ -266,7 +274,9 @@ def run_serving(n, slots=4, seed=5):
             "one_at_a_time_mean_s": float(service.mean()),
             "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
-            "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same)}
+            "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same),
+            "statuses_alone": {int(k): int(v) for k, v in zip(*np.unique([a.status for a in alone], return_counts=True))},
+            "mismatches": mism[:8], "n_mismatches": len(mism)}
 
 
 def run_stress(sweeps=10):

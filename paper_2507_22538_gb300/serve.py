@@ -109,6 +109,8 @@ class SolveService:
         self.peak_in_flight = 0
         self._in_flight = 0
         self.batches: list[int] = []  # size of every solve the workers ran
+        self.oom_retries = 0  # requests requeued after running out of device memory
+        self._retry_wait = False  # hold admissions until a request in flight finishes
 
     # -- client side --------------------------------------------------------------
     def start(self):
@@ -187,26 +189,43 @@ class SolveService:
                 while True:
                     if self._stop and not self._pending:
                         return
-                    batch, need = self._admit()
+                    batch, need = (None, 0) if self._retry_wait else self._admit()
                     if batch is not None:
                         break
                     self._cv.wait()
                 self._in_flight += len(batch)
                 self.peak_in_flight = max(self.peak_in_flight, self._in_flight)
             admitted = self.now()
+            retry = False
             try:
                 outs = [self._solve(batch[0], stream)] if len(batch) == 1 else self._solve_batch(batch, stream)
             except Exception as exc:  # failed requests still complete, with their status
                 status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
-                outs = [Result(r.rid, status, np.empty(0), np.empty(0, dtype=np.int32), 0, 0, float("nan"),
-                               r.arrival, 0.0, 0.0) for r in batch]
+                oom = isinstance(exc, torch.cuda.OutOfMemoryError) or status == mdp.MDP_ERR_OOM
+                outs = [Result(r.rid, status if not oom else mdp.MDP_ERR_OOM, np.empty(0),
+                               np.empty(0, dtype=np.int32), 0, 0, float("nan"), r.arrival, 0.0, 0.0) for r in batch]
+                retry = oom
+                if oom:
+                    torch.cuda.empty_cache()  # hand torch's unused cached blocks back before the retry
             finally:
                 with self._cv:
                     self._free += need
                     self._in_flight -= len(batch)
+                    # the budget is an estimate (caching allocators, fragmentation): a request that
+                    # ran out of device memory while others were in flight goes back to the front
+                    # of the queue and is admitted again once one of them finishes
+                    if retry and self._in_flight > 0:
+                        self._pending[0:0] = batch
+                        self.oom_retries += len(batch)
+                        self._retry_wait = True
+                    else:
+                        retry = False
                     self._cv.notify_all()
+            if retry:
+                continue
             done = self.now()
             with self._cv:
+                self._retry_wait = False
                 for res in outs:
                     res.admitted = admitted
                     res.finished = done

@@ -146,3 +146,46 @@ def test_device_drawn_requests_equal_alone_and_certified():
         # the device draw's probabilities differ from the host draw's by rounding, which
         # moves Q by at most a few ulps of gamma * ||V||
         assert float(np.max(np.abs(Q.min(axis=1) - V))) <= 1e-8 + 4 * q_tolerance(m, V)
+
+
+class FlakyRequest(DeviceRequest):
+    """Fails its first `fails` draws with the allocator's out-of-memory error (a
+    host-side fault: nothing runs on the GPU)."""
+
+    def __init__(self, rid, seed, fails=1, **ranges):
+        super().__init__(rid, seed, **ranges)
+        self.fails = fails
+
+    def device_arrays(self):
+        import torch
+        if self.fails > 0:
+            self.fails -= 1
+            raise torch.cuda.OutOfMemoryError("injected out-of-memory")
+        return super().device_arrays()
+
+
+def test_out_of_memory_is_retried_while_others_run():
+    """A request that runs out of device memory while another is in flight goes back
+    to the queue and completes after it; alone, it fails with MDP_ERR_OOM."""
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.serve import Request, SolveService, solve_alone
+    big = dict(s_range=(60_000, 60_001), a_range=(8, 8), k_range=(32, 32), gammas=(0.999,))
+    small = dict(s_range=(500, 501), a_range=(3, 3), k_range=(5, 5), gammas=(0.9,))
+    first = Request(0, DeviceRequest(0, 31, **big), tol=1e-8, alpha=1e-3)
+    flaky = Request(1, FlakyRequest(1, 31, fails=1, **small), tol=1e-8, alpha=1e-3)
+    svc = SolveService(slots=2).start()
+    svc.submit(first)
+    import time
+    time.sleep(0.002)
+    svc.submit(flaky)
+    res = svc.wait(2)
+    svc.close()
+    assert svc.oom_retries == 1
+    assert res[0].status == mdp.MDP_OK and res[1].status == mdp.MDP_OK
+    ref = solve_alone(Request(1, DeviceRequest(1, 31, **small), tol=1e-8, alpha=1e-3))
+    assert np.array_equal(res[1].V, ref.V)
+    lone = SolveService(slots=1).start()
+    lone.submit(Request(2, FlakyRequest(1, 31, fails=1, **small), tol=1e-8, alpha=1e-3))
+    out = lone.wait(1)
+    lone.close()
+    assert out[2].status == mdp.MDP_ERR_OOM and lone.oom_retries == 0
