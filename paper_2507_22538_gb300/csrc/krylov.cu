@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kVecThreads) rich_step_kernel(const double* __
     out[s] = fma(omega, r, th);
   }
   __shared__ double o[1];
-  if (grid_sum<1, false>(d, 0.0, partials, K->pstride, &K->counter, o) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(d, 0.0, partials, K->pstride, K->gcount, o) && threadIdx.x == 0) {
     const double rn = sqrt(o[0]);
     K->res2 = rn;
     if (!isfinite(rn)) {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kVecThreads) tf_init_kernel(const double* __re
     acc[0] = fma(r, r, acc[0]);
   }
   __shared__ double out[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, out) && threadIdx.x == 0) {
     const double tau = sqrt(out[0]);
     K->t_tau = tau;
     K->t_rho = out[0];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kVecThreads) tf_sigma_kernel(int64_t S, const 
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x)
     acc[0] = fma(rt[s], v[s], acc[0]);
   __shared__ double out[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, out) && threadIdx.x == 0) {
     const double sigma = out[0];
     if (sigma == 0.0 || K->t_rho == 0.0 || !isfinite(sigma)) {
       K->flags |= kSolveDone;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kVecThreads) tf_half_kernel(int64_t S, const d
     acc[0] = fma(ws, ws, acc[0]);
   }
   __shared__ double out[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, out) && threadIdx.x == 0) {
     const double theta = sqrt(out[0]) / K->t_tau;
     const double c = 1.0 / sqrt(1.0 + theta * theta);
     K->t_theta = theta;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kVecThreads) tf_xupd_kernel(int64_t S, int hal
   }
   if (!rho) return;
   __shared__ double out[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, out) && threadIdx.x == 0) {
     const double rn = out[0];
     if (rn == 0.0 || !isfinite(rn)) {
       K->flags |= kSolveDone;
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kVecThreads) true_residual_kernel(const double
     acc[0] = fma(r, r, acc[0]);
   }
   __shared__ double out[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, out) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, out) && threadIdx.x == 0) {
     K->res2 = sqrt(out[0]);
     if (!isfinite(K->res2)) K->flags |= kNumeric;
   }
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kVecThreads) jacobi_step_kernel(const double* 
     out[s] = th + omega * r / (1.0 - gamma * pdiag[s]);
   }
   __shared__ double o[1];
-  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, &K->counter, o) && threadIdx.x == 0) {
+  if (grid_sum<1, false>(acc, 0.0, partials, K->pstride, K->gcount, o) && threadIdx.x == 0) {
     const double rn = sqrt(o[0]);
     K->res2 = rn;
     if (!isfinite(rn)) {

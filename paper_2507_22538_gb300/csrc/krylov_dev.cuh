@@ -25,6 +25,9 @@ struct KrylovState {
   double t_rho, t_alpha, t_beta, t_theta, t_tau, t_eta;
   int it, maxit, m, jdone, flags, counter, result;  // result: Richardson buffer holding the answer
   int pstride;                                       // row stride of the transposed block partials
+  // arrival counters of the two-level grid reductions: [0] for the groups, [1 + g] for
+  // the blocks of group g (zero between kernels)
+  int gcount[kMaxGroups + 2];
 };
 
 struct KrylovHeader {  // host copy of the int tail of KrylovState
@@ -77,7 +80,9 @@ __device__ __forceinline__ T warp_reduce_scatter(T (&d)[N]) {
 }
 
 template <int NT>
-__device__ bool grid_finish(double* __restrict__ partials, int pstride, int* counter, double* out, int nb);
+__device__ bool grid_finish(double* __restrict__ partials, int pstride, int* gcount, double* out, int bid, int nb);
+template <int NT>
+__device__ bool grid_finish1(double* __restrict__ partials, int pstride, int* counter, double* out, int nb);
 
 // Block sums of NV per-thread values (NV a power of two) plus one extra value into
 // partials[i * pstride + bid] (block bid of the nb blocks that work on one problem) (the extra one as column NV when HAS_EXTRA);
@@ -104,15 +109,18 @@ __device__ bool grid_sum_at(TW (&d)[NV], double extra, double* __restrict__ part
     for (int w = 0; w < kWarps; ++w) t += red[w][threadIdx.x];
     partials[(int64_t)threadIdx.x * pstride + bid] = t;
   }
-  return grid_finish<NT>(partials, pstride, counter, out, nb);
+  if constexpr (sizeof(TW) == sizeof(double))
+    return grid_finish<NT>(partials, pstride, counter, out, bid, nb);
+  else
+    return grid_finish1<NT>(partials, pstride, counter, out, nb);
 }
 
-// After every block wrote its NT block sums into column bid of the transposed
-// partials: the last block to arrive adds each column over all blocks in block
-// order into out[] (shared memory) and returns true in all of its threads.  The
-// counter is left at zero for the next kernel.
+// Single-level tail: the last block to arrive adds each column over all blocks in
+// block order (lanes stride the blocks) into out[] and returns true in all of its
+// threads; the counter is left at zero.  Used by the binary32 passes of the mixed
+// solver, where it measured faster than the two-level tail below.
 template <int NT>
-__device__ bool grid_finish(double* __restrict__ partials, int pstride, int* counter, double* out, int nb) {
+__device__ bool grid_finish1(double* __restrict__ partials, int pstride, int* counter, double* out, int nb) {
   constexpr int kWarps = kVecThreads / 32;
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -152,6 +160,54 @@ __device__ bool grid_finish(double* __restrict__ partials, int pstride, int* cou
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0;
+  return true;
+}
+
+// After every block wrote its NT block sums into column bid of the transposed
+// partials: blocks form groups of 32 in index order; the last block of a group to
+// arrive adds the group's sums per column (lane = block, fixed butterfly) into the
+// second-level rows (after the kPartialRows rows of the partials, kMaxGroups
+// apart), and the last group to arrive adds the group sums into out[] (shared
+// memory) and returns true in all of its threads.  Two short steps instead of one
+// block walking all nb columns: the latency of the tail stays near two L2 round
+// trips.  Deterministic for a fixed grid; the counters are left at zero.
+template <int NT>
+__device__ bool grid_finish(double* __restrict__ partials, int pstride, int* gcount, double* out, int bid, int nb) {
+  constexpr int kWarps = kVecThreads / 32;
+  __shared__ int stage;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ngroups = (nb + kGroup - 1) / kGroup;
+  const int g = bid / kGroup;
+  const int gsize = min(kGroup, nb - g * kGroup);
+  double* level2 = partials + (int64_t)kPartialRows * pstride;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) stage = (atomicAdd(gcount + 1 + g, 1) == gsize - 1) ? 1 : 0;
+  __syncthreads();
+  if (!stage) return false;
+  __threadfence();
+  for (int i = warp; i < NT; i += kWarps) {
+    double a = lane < gsize ? __ldcg(partials + (int64_t)i * pstride + g * kGroup + lane) : 0.0;
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) level2[i * kMaxGroups + g] = a;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gcount[1 + g] = 0;
+    stage = (atomicAdd(gcount, 1) == ngroups - 1) ? 2 : 0;
+  }
+  __syncthreads();
+  if (stage != 2) return false;
+  __threadfence();
+  for (int i = warp; i < NT; i += kWarps) {
+    double a = 0.0;
+    for (int q = lane; q < ngroups; q += 32) a += __ldcg(level2 + i * kMaxGroups + q);
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[i] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) gcount[0] = 0;
   return true;
 }
 
@@ -210,7 +266,7 @@ __device__ __forceinline__ void gm_residual_body(int bid, int nb, const double* 
     u0[s] = (T)r;
   }
   __shared__ double out[1];
-  if (grid_sum_at<1, false>(d, 0.0, partials, K->pstride, &K->counter, out, bid, nb) && threadIdx.x == 0) {
+  if (grid_sum_at<1, false>(d, 0.0, partials, K->pstride, K->gcount, out, bid, nb) && threadIdx.x == 0) {
     const double beta = sqrt(out[0]);
     K->res2 = beta;
     K->sigma[0] = beta > 0.0 ? 1.0 / beta : 0.0;
@@ -270,7 +326,7 @@ __device__ __forceinline__ void gm_dots_body(int bid, int nb, int64_t S, const T
     ww = fma(ws, ws, ww);
   }
   __shared__ double out[NP + 1];  // warp sums in T, block and grid sums in double
-  if (grid_sum_at<NP, true>(d, (double)ww, partials, K->pstride, &K->counter, out, bid, nb) && threadIdx.x == 0) {
+  if (grid_sum_at<NP, true>(d, (double)ww, partials, K->pstride, K->gcount, out, bid, nb) && threadIdx.x == 0) {
     for (int i = 0; i <= j; ++i) {
       const double h = K->sigma[i] * out[i];
       K->hc[i] = h;
@@ -328,10 +384,10 @@ __device__ __forceinline__ void gm_project_body(int bid, int nb, int64_t S, T* _
   __shared__ double out[NV + 1];
   bool last;
   if (DOTS) {
-    last = grid_sum_at<NV, true>(d, (double)uu, partials, K->pstride, &K->counter, out, bid, nb);
+    last = grid_sum_at<NV, true>(d, (double)uu, partials, K->pstride, K->gcount, out, bid, nb);
   } else {
     T n1[1] = {uu};
-    last = grid_sum_at<1, false>(n1, 0.0, partials, K->pstride, &K->counter, out, bid, nb);
+    last = grid_sum_at<1, false>(n1, 0.0, partials, K->pstride, K->gcount, out, bid, nb);
   }
   if (last && threadIdx.x == 0) {
     const double beta = sqrt(out[DOTS ? NV : 0]);

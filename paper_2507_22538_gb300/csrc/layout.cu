@@ -322,7 +322,7 @@ mdp_status ensure_basis(mdp_s* h, int nvec) {
 }
 
 // The stream-ordered pool that every device buffer of the library comes from
-// keeps up to an eighth of the device's memory across synchronisations (the
+// keeps up to a sixteenth of the device's memory across synchronisations (the
 // default returns all of it to the driver at each one), so handles created and
 // destroyed in turn reuse their buffers instead of mapping memory again.  This is
 // the process's default pool of the device: the setting ends with the process.
@@ -335,7 +335,7 @@ static mdp_status retain_pool(int device) {
   MDP_CUDA(cudaMemGetInfo(&free_b, &total_b));
   cudaMemPool_t pool;
   MDP_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
-  uint64_t keep = (uint64_t)(total_b / 8);
+  uint64_t keep = (uint64_t)(total_b / 16);
   MDP_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
   done[device] = true;
   return MDP_OK;
@@ -473,7 +473,8 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(h, &h->w, S, "w"));
   MDP_TRY(dalloc(h, &h->tmp, S, "tmp"));
   h->partial_stride = h->sm_count * kMaxBlocksPerSm;
-  MDP_TRY(dalloc(h, &h->partials, (size_t)kPartialRows * h->partial_stride, "partials"));
+  // block partials, then the second-level group sums of the grid reductions
+  MDP_TRY(dalloc(h, &h->partials, (size_t)kPartialRows * (h->partial_stride + kMaxGroups), "partials"));
   {
     char* ks = nullptr;
     MDP_TRY(dalloc(h, &ks, krylov_state_bytes(), "solver state"));

@@ -15,6 +15,8 @@ namespace mdp {
 
 constexpr int kMaxBasis = 32;    // GMRES basis vectors held per thread in registers (restart <= 32)
 constexpr int kPartialRows = 40;    // per-block partial sums (up to kMaxBasis + 1 values), transposed
+constexpr int kGroup = 32;          // blocks per first-level group of a grid reduction
+constexpr int kMaxGroups = 64;      // second-level sums per value: grids of up to 2048 blocks
 constexpr int kMaxBlocksPerSm = 8;  // 256-thread blocks: 2048 threads per SM
 enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 constexpr int kScalarSlots = 512;
@@ -99,7 +101,8 @@ struct mdp_s {
   int basis32_cap = 0;
   float* w32 = nullptr;      // [S]
   double* tfq = nullptr;     // TFQMR vectors [8 * S] (the first also holds the Jacobi diagonal)
-  double* partials = nullptr;  // [kPartialRows * partial_stride], row i holds value i of every block
+  double* partials = nullptr;  // [kPartialRows * (partial_stride + kMaxGroups)]: row i holds value i of every
+                               // block, then the second-level group sums (krylov_dev.cuh grid_finish)
   int partial_stride = 0;      // sm_count * kMaxBlocksPerSm, the largest grid of a reducing kernel
   void* kstate = nullptr;      // device state of the inner solver (krylov.cu)
   double* sc = nullptr;      // device scalars [kScalarSlots]
