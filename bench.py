@@ -263,6 +263,7 @@ def run_serving(n, slots=4, seed=5):
             a, b = alone[r.rid], out[r.rid]
             if not (a.status == b.status and np.array_equal(a.V, b.V) and np.array_equal(a.pi, b.pi)):
                 mism.append({"run": tag, "rid": r.rid, "status_alone": a.status, "status": b.status,
+                             "error": b.error or a.error,
                              "outer": [a.outer_iters, b.outer_iters], "inner": [a.inner_iters, b.inner_iters],
                              "max_dV": float(np.max(np.abs(a.V - b.V))) if a.V.shape == b.V.shape and a.V.size else None})
     same = not mism
@@ -372,13 +373,18 @@ def run_pendulum():
 
 
 def run_bellman_only(args):
-    """Time mdp_bellman alone on the banded workload (any size), one JSON line."""
+    """Time mdp_bellman alone on the banded workload, or (--workload random) on the
+    bandwidth-stress random workload's generator (A = 32, 32 entries per row,
+    Dirichlet(0.5) quantised to 2^-11, built on the device), at any size; one JSON line."""
     import torch
 
-    from mdpgen import banded_birth_death, random_value_vector
+    from mdpgen import MDPData, banded_birth_death, random_value_vector
     from paper_2507_22538_gb300 import mdp
     from paper_2507_22538_gb300.build import build
     build()
+    if args.workload == "random":
+        from mdpgen.torch_gen import random_sparse_device
+        return run_bellman_only_random(args, random_sparse_device, random_value_vector)
     m = banded_birth_death(args.states, A, H, GAMMA)
     stream = torch.cuda.current_stream()
     with mdp.MDP.from_data(m, stream) as M:
@@ -414,6 +420,39 @@ def run_bellman_only(args):
                       "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
                       "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes,
                       "tile_states": tile_states}), flush=True)
+    return 0
+
+
+def run_bellman_only_random(args, random_sparse_device, random_value_vector):
+    import torch
+
+    from paper_2507_22538_gb300 import mdp
+    Sx, Ax, Kx, gx = args.states, 32, 32, 0.99
+    rp, col, val, g = random_sparse_device(Sx, Ax, Kx, gx, 21, conc=0.5, quant_bits=11)
+    stream = torch.cuda.current_stream()
+    with mdp.MDP(Sx, Ax, rp, col, val, g, stream) as M:
+        del rp, col, val, g
+        torch.cuda.empty_cache()
+        st_t, tile_states, _ = mdp.mdp_tune(M.h, gx, stream)
+        mdp.check(st_t, "mdp_tune")
+        V = torch.from_numpy(random_value_vector(Sx, 1, 100.0)).cuda()
+        TV = torch.empty_like(V)
+        pi = torch.empty(Sx, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.bellman_only):
+            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.bellman_only
+    R = Sx * Ax
+    nbytes = R * Kx * 12 + R * 16 + Sx * 20
+    peak, _ = load_peaks()
+    print(json.dumps({"mode": "bellman_only", "workload": "random", "S": Sx, "A": Ax, "k": Kx, "ms_per_sweep": ms,
+                      "bytes": nbytes, "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
+                      "gathers_per_s": R * Kx / (ms * 1e-3), "tile_states": tile_states}), flush=True)
     return 0
 
 
@@ -507,6 +546,9 @@ def main():
                     help="requests of the continuous-batching measurement added to the line (0: skip)")
     ap.add_argument("--bellman-only", type=int, default=0, metavar="SWEEPS",
                     help="profiling aid: time SWEEPS mdp_bellman calls on the workload (no bench line)")
+    ap.add_argument("--workload", choices=["banded", "random"], default="banded",
+                    help="with --bellman-only: the banded workload, or the random bandwidth-stress generator "
+                         "(A = 32, k = 32) at --states states")
     ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only/--solve-only: number of states")
     ap.add_argument("--inner-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: ITERS GMRES(30) iterations of mdp_policy_eval on the rows of action 0 "

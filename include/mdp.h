@@ -238,8 +238,9 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
  * ||TV - V||_inf) computed straight from the caller's row-stacked CSR arrays,
  * with no handle and no device allocation.  The paper has no counterpart: it is
  * for callers that cannot allocate device memory at the point of the call, such
- * as code running under CUDA stream capture or inside an application that owns
- * every device allocation through its own pool.
+ * as an application that hands out every device allocation through its own pool,
+ * a plug-in whose host program forbids allocation inside the call, or a real-time
+ * loop that cannot afford the synchronisation an allocation may cause.
  *
  *  S, A          at most 2,097,152 states and 128 actions (else MDP_ERR_INVALID_ARG).
  *  row_ptr, col, val, g   device arrays laid out as for mdp_create; the caller

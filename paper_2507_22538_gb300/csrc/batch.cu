@@ -561,8 +561,7 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
       // Algorithm 1 steps 2-3 for every running problem, one residual read for all
       size_t smem = 0;
       MDP_TRY(upload(B, items, act, &smem));
-      if (smem > 48 * 1024)
-        MDP_CUDA(cudaFuncSetAttribute(bb_bellman_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MDP_TRY(raise_dyn_smem((const void*)bb_bellman_kernel, smem));
       bb_zero_resmax_kernel<<<(na + 255) / 256, 256, 0, st>>>(B.desc, na);
       ++launches;
       MDP_CUDA(cudaGetLastError());

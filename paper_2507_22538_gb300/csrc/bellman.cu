@@ -18,10 +18,8 @@ size_t bellman_smem_bytes(const mdp_s* h) { return bellman_smem(h); }
 
 mdp_status configure_bellman(mdp_s* h) {
   const size_t smem = bellman_smem(h);
-  if (smem > 48 * 1024) {
-    MDP_CUDA(cudaFuncSetAttribute(bellman_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    MDP_CUDA(cudaFuncSetAttribute(bellman_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
+  MDP_TRY(raise_dyn_smem((const void*)bellman_kernel<true>, smem));
+  MDP_TRY(raise_dyn_smem((const void*)bellman_kernel<false>, smem));
   int per_sm = 0;
   if (h->P.uniform)
     MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<true>, kBellThreads, smem));

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -21,6 +22,9 @@ mdp_status fail(mdp_status st, const std::string& msg) {
 
 mdp_status cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  // a non-sticky error (a refused launch or argument) is reported here once; clear
+  // the thread's error state so the next launch check does not report it again
+  cudaGetLastError();
   return (e == cudaErrorMemoryAllocation) ? MDP_ERR_OOM : MDP_ERR_CUDA;
 }
 
@@ -318,6 +322,24 @@ mdp_status ensure_basis(mdp_s* h, int nvec) {
   h->basis_cap = 0;
   MDP_TRY(dalloc(h, &h->basis, (size_t)nvec * (size_t)h->S, "GMRES basis"));
   h->basis_cap = nvec;
+  return MDP_OK;
+}
+
+// The dynamic shared memory cap of a kernel is one attribute per kernel and
+// device, shared by every handle and host thread of the process.  It is only ever
+// raised (under a lock): a handle whose tile needs less must not lower the cap
+// under a concurrent handle that needs more, whose next launch would then fail.
+mdp_status raise_dyn_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return MDP_OK;
+  int dev = 0;
+  MDP_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> caps;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cap = caps[{dev, func}];
+  if (bytes <= cap) return MDP_OK;
+  MDP_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cap = bytes;
   return MDP_OK;
 }
 

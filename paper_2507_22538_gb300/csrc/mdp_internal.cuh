@@ -124,6 +124,8 @@ namespace mdp {
 double* tls_pinned();
 
 // layout.cu
+// Raise (never lower) a kernel's dynamic shared memory cap on the current device to `bytes`.
+mdp_status raise_dyn_smem(const void* func, size_t bytes);
 mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t st);  // fill Ppi, gpi from pi
 
 // bellman.cu

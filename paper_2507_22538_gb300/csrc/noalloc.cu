@@ -1,12 +1,13 @@
 // mdp_bellman_csr_noalloc: one Bellman application computed straight from the
 // caller's CSR arrays, for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph, applications whose device memory is handed out
-// by their own pool or a framework's caching allocator and must not be
-// fragmented behind its back, or real-time loops where an allocation (and the
-// implicit synchronisation it can cause) is not allowed.  They also cannot
-// create an mdp_handle, because mdp_create allocates the device layout.
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// handed out by their own pool or a framework's caching allocator, which must
+// not be fragmented or exhausted behind its back; plug-ins called back from a
+// host program that owns the device and forbids allocation inside the call;
+// and real-time control loops where an allocation (and the device-wide
+// synchronisation it can cause) would break the loop's deadline.  They also
+// cannot create an mdp_handle, because mdp_create allocates the device layout.
 //
 // This entry point needs no handle and allocates nothing.  The only scratch it
 // uses (one residual maximum per 32-state tile, plus a completion counter) lives

@@ -50,6 +50,7 @@ class Result:
     arrival: float
     admitted: float
     finished: float
+    error: str = ""  # the library's message when status is not MDP_OK
 
     @property
     def latency(self) -> float:
@@ -203,7 +204,8 @@ class SolveService:
                 status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
                 oom = isinstance(exc, torch.cuda.OutOfMemoryError) or status == mdp.MDP_ERR_OOM
                 outs = [Result(r.rid, status if not oom else mdp.MDP_ERR_OOM, np.empty(0),
-                               np.empty(0, dtype=np.int32), 0, 0, float("nan"), r.arrival, 0.0, 0.0) for r in batch]
+                               np.empty(0, dtype=np.int32), 0, 0, float("nan"), r.arrival, 0.0, 0.0, str(exc))
+                        for r in batch]
                 retry = oom
                 if oom:
                     torch.cuda.empty_cache()  # hand torch's unused cached blocks back before the retry
@@ -247,11 +249,12 @@ class SolveService:
                 V = torch.zeros(d.S, dtype=torch.float64, device="cuda")
                 pi = torch.empty(d.S, dtype=torch.int32, device="cuda")
                 st, stats = mdp.mdp_solve(h, o, V, pi, stream)
+                err = mdp.mdp_last_error() if st != mdp.MDP_OK else ""
                 Vh, pih = V.cpu(), pi.cpu()  # on this stream: ordered after the solve
             finally:
                 mdp.mdp_destroy(h)
         return Result(req.rid, st, Vh.numpy(), pih.numpy(), stats.outer_iters, int(stats.inner_iters_total),
-                      stats.final_residual, req.arrival, 0.0, 0.0)
+                      stats.final_residual, req.arrival, 0.0, 0.0, err)
 
     @staticmethod
     def _solve_batch(batch, stream) -> list:

@@ -161,3 +161,25 @@ def test_tune_keeps_results(S, A, k):
         TV1, pi1, r1 = M.bellman(m.gamma, V)
         torch.cuda.synchronize()
     assert torch.equal(TV0, TV1) and torch.equal(pi0, pi1) and torch.equal(r0, r1)
+
+
+def test_live_handle_survives_a_handle_with_a_smaller_tile():
+    """The sweep's dynamic shared memory cap is one setting per kernel and device,
+    shared by all handles: creating a handle whose Q tile needs less (A = 29: 256
+    states x 29 actions x 8 B = 59 KB) must not lower it under a live handle whose
+    tile needs more (A = 31: 63.5 KB), whose sweeps would then be refused.  Requests
+    of different A solved concurrently by the serving loop meet exactly this."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    mx = random_sparse(600, 31, 4, 0.9, seed=21)
+    my = random_sparse(600, 29, 4, 0.9, seed=22)
+    with mdp.MDP.from_data(mx) as X, mdp.MDP.from_data(my) as Y:
+        for M, m in ((X, mx), (Y, my), (X, mx)):
+            V = random_value_vector(m.S, 1, scale=1.0 / (1 - m.gamma))
+            TV, pi, res = M.bellman(m.gamma, torch.from_numpy(V).cuda())
+            torch.cuda.synchronize()
+            P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+            TVo, _, reso = O.bellman(P, m.g, m.gamma, V, m.S, m.A)
+            tol = q_tolerance(m, V)
+            np.testing.assert_allclose(TV.cpu().numpy(), TVo, rtol=0, atol=tol)
+            assert abs(res.item() - reso) <= tol
