@@ -71,6 +71,39 @@ def bellman_source_sha():
     return h.hexdigest()[:16]
 
 
+def krylov_source_sha():
+    """sha256 (first 16 hex digits) of the sources that make the GMRES mat-vec kernel."""
+    h = hashlib.sha256()
+    for f in ("sell.cuh", "krylov_dev.cuh", "krylov.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2507_22538_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def summary_value(name, key, sha_key, sha):
+    """A number from a committed ncu summary under profiles/, if it was taken on the
+    current kernel source (else None)."""
+    summ = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(summ):
+        return None
+    vals = {}
+    for line in open(summ):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get(sha_key) != sha:
+        return None
+    try:
+        return float(vals[key])
+    except (KeyError, ValueError):
+        return None
+
+
+def matvec_bytes():
+    """Algorithmic bytes of one FP64 Arnoldi mat-vec w = sigma (u - gamma P_pi u): the
+    policy's rows (8 B value + 4 B column per entry), u read once, w written."""
+    return S * K_ROW * 12 + S * 16
+
+
 def sweep_traffic():
     """DRAM bytes per Bellman launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
@@ -278,6 +311,42 @@ def run_serving(n, slots=4, seed=5):
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same),
             "statuses_alone": {int(k): int(v) for k, v in zip(*np.unique([a.status for a in alone], return_counts=True))},
             "mismatches": mism[:8], "n_mismatches": len(mism)}
+
+
+def run_small(steps=20):
+    """The small random workload (S = 1000, A = 4, 8 entries per row, Dirichlet(1),
+    gamma = 0.9, GMRES(30), alpha = 1e-3, tol = 1e-10): time to solution of the
+    stream-driven mdp_solve against the graph-driven one (opts.graph: the whole of
+    Algorithm 1 in one CUDA graph launch), and the first graph call, which builds
+    and instantiates the graph.  Each time is the wall time of one blocking call."""
+    import torch
+
+    from mdpgen import random_sparse
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(1000, 4, 8, 0.9, seed=1)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "random sparse S=1000, A=4, k=8, Dirichlet(1), gamma=0.9, GMRES(30), alpha=1e-3, tol=1e-10",
+           "timing": "host wall time of each blocking mdp_solve call, median of %d" % steps}
+    with mdp.MDP.from_data(m, stream) as M:
+        V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+        pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+        o = mdp.mdp_default_opts()
+        o.gamma, o.atol_pi, o.alpha, o.gmres_restart = m.gamma, 1e-10, 1e-3, 30
+        for name, graph in (("stream", 0), ("graph", 1)):
+            o.graph = graph
+            times = []
+            for i in range(steps + 3):
+                V.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, stats = mdp.mdp_solve(M.h, o, V, pi, stream)
+                times.append(time.perf_counter() - t0)
+                mdp.check(st, "mdp_solve")
+            out[name] = {"ms": statistics.median(times[3:]) * 1e3, "first_call_ms": times[0] * 1e3,
+                         "outer": stats.outer_iters, "inner": stats.inner_iters_total,
+                         "launches": stats.kernel_launches, "final_residual": stats.final_residual}
+    out["speedup_graph"] = out["stream"]["ms"] / out["graph"]["ms"]
+    return out
 
 
 def run_stress(sweeps=10):
@@ -555,7 +624,15 @@ def main():
                          "of the workload (a one-action MDP; no bench line)")
     ap.add_argument("--solve-only", choices=["f64", "mixed"], default=None,
                     help="profiling aid: W + K solves of the workload at this precision (no bench line)")
+    ap.add_argument("--small-only", action="store_true",
+                    help="only the small-workload stream vs graph measurement (no bench line)")
     args = ap.parse_args()
+    if args.small_only:
+        import torch
+        from paper_2507_22538_gb300.build import build
+        build()
+        print(json.dumps({"mode": "small_only", **run_small()}), flush=True)
+        return 0
     if args.solve_only:
         return run_solve_only(args)
     if args.impl == "reference":
@@ -620,7 +697,7 @@ def main():
             ev.record(stream)
             marks.append(ev)
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
-                        "inner_ms", "inner_bytes"):
+                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
@@ -630,6 +707,26 @@ def main():
         dist.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     clocks = clk.summary()
+
+    # the same solves without per-sweep event timing, stream-driven and as one CUDA graph each
+    graph_cmp = {}
+    for name, graph in (("stream", 0), ("graph", 1)):
+        gopts = mdp.mdp_default_opts()
+        for f, _ in mdp.mdp_solve_opts._fields_:
+            setattr(gopts, f, getattr(opts, f))
+        gopts.record_timing, gopts.graph = 0, graph
+        for _ in range(max(1, args.warmup)):
+            step(gopts)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = step(gopts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_cmp[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+        graph_cmp[name + "_outer_inner"] = [s["outer_iters"], s["inner_iters_total"]]
+    graph_cmp["what"] = ("the timed solves without per-sweep event timing: stream-driven, and as one CUDA graph "
+                         "launch per solve (opts.graph)")
 
     # the same solves with the mixed-precision inner solver (FP32 Arnoldi, FP64 refinement)
     mopts = mdp.mdp_default_opts()
@@ -726,6 +823,17 @@ def main():
                 else "fallback 6.8 TB/s", "traffic": sweep_traffic(),
                 "bytes_per_launch": bellman_bytes(), "avg_launch_ms": bell_ms,
                 "share_of_step": share_bell, "tile_states": tile_states}
+    mv_ms = totals["matvec_ms"] / max(1, totals["matvecs_timed"])
+    mv_gbs = matvec_bytes() / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else None
+    roof_mv = {"bound": "hbm", "kernel": "gm_matvec_kernel (policy mat-vec of every FP64 Arnoldi step; the largest "
+                                         "share of the step among single kernels)",
+               "achieved": mv_gbs, "peak": peak, "unit": "GB/s", "frac": mv_gbs / peak if mv_gbs else None,
+               "peak_kind": roofline["peak_kind"],
+               "traffic": summary_value("gm_matvec_banded_s1e6.txt", "dram_bytes_per_launch", "krylov_src_sha256_16",
+                                        krylov_source_sha()),
+               "bytes_per_launch": matvec_bytes(), "avg_launch_ms": mv_ms,
+               "launches_timed": int(totals["matvecs_timed"]),
+               "share_of_step": totals["matvec_ms"] / (ms * args.steps)}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
@@ -741,14 +849,16 @@ def main():
     line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
-            "roofline": roofline, "roofline_inner": inner_roof, "mixed_precision": mixed,
+            "roofline": roofline, "roofline_matvec": roof_mv, "roofline_inner": inner_roof, "mixed_precision": mixed,
             "mixed_precision_binary16": quant,
             "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
                            "inner_per_step": totals["inner_iters_total"] / args.steps,
                            "max_final_residual": totals["final_residual"]},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "graph_solve": graph_cmp,
             "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}
+    line["small"] = run_small()
     if args.serve > 0:
         line["serving"] = run_serving(args.serve)
     if args.stress:

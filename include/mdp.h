@@ -74,6 +74,14 @@ typedef struct {
   int32_t record_timing;   /* nonzero: time Bellman sweeps and inner solves (CUDA events) (0) */
   int32_t gmres_refine;    /* an mdp_refine value                          (MDP_REFINE_NEVER) */
   int32_t precision;       /* an mdp_precision value of the GMRES inner solve  (MDP_PREC_F64) */
+  int32_t graph;           /* nonzero: with the GMRES inner solver and record_timing off, run the
+                              whole of Algorithm 1 as one CUDA graph launch: conditional WHILE/IF
+                              nodes over the sweep, the stop tests and the restart cycles, decided
+                              on the device, with no host round trip until the solve ends.  Same
+                              kernels and results, bit for bit, as the stream-driven solve.  The
+                              instantiated graph stays in the handle and is rebuilt when V, pi,
+                              gamma, the options or the Bellman launch shape change.  Ignored by
+                              mdp_solve_batch.                                                    (0) */
 } mdp_solve_opts;
 
 /* Statistics of one mdp_solve call (host struct filled by the library). */
@@ -96,6 +104,9 @@ typedef struct {
   int32_t policy_value_bytes; /* bytes per probability the inner mat-vecs read: 8 (binary64), or with
                                  MDP_PREC_MIXED 4 (binary32) or 2 (binary16 / bfloat16, used when every
                                  probability of the MDP is exactly representable there) */
+  double matvec_ms;           /* summed device time of the GMRES steps' policy mat-vec kernels, each
+                                 between its own pair of CUDA events (record_timing only) */
+  int64_t matvecs_timed;      /* mat-vec kernels timed in matvec_ms (steps that ran) */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -1,0 +1,369 @@
+// Algorithm 1 as one CUDA graph (mdp_solve with opts->graph set and the GMRES
+// inner solver).  The stream-driven mdp_solve waits on the host for every Bellman
+// residual (Algorithm 1 step 3), for the set-up of every policy evaluation and for
+// the solver state after every GMRES restart cycle; on small problems these round
+// trips and the launches behind them take most of the time.  Here the whole loop
+// runs on the device:
+//
+//   init
+//   WHILE (outer)                         Algorithm 1, one policy evaluation per pass
+//     Bellman sweep; check                steps 2-3: TV, pi, ||TV - V||_inf; stop tests
+//     IF (go)                             set by the check
+//       policy rows; restart residual     step 4 and the first GMRES residual
+//       WHILE (inner)                     one GMRES(m) restart cycle per pass
+//         m Arnoldi steps; update; restart residual
+//       end of the evaluation             k += 1
+//
+// Small control kernels set the conditions (cudaGraphSetConditional) from the
+// residual and the solver's device flags.  The other nodes are the kernels the
+// stream-driven solve launches, with the same launch shapes, so both give the
+// same iterates bit for bit.  The instantiated graph is kept in the handle and
+// rebuilt only when something it bakes in changes (vectors, gamma, options,
+// the Bellman launch shape).
+#include <cstring>
+
+#include "krylov_dev.cuh"
+
+namespace mdp {
+
+// launch sequences of krylov.cu (same kernels as the stream-driven GMRES)
+mdp_status gmres_residual_launch(mdp_s* h, bool mixed, double gamma, const double* theta, cudaStream_t st);
+mdp_status gmres_cycle_launch(mdp_s* h, bool mixed, double gamma, double* theta, int m, int refine, cudaStream_t st);
+void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int64_t steps, int64_t tri);
+
+namespace {
+
+// Device record of one graph-driven solve.
+struct GraphSolveState {
+  double res;             // ||TV - V||_inf of the last sweep
+  long long inner_total;  // inner iterations of the completed evaluations
+  long long solves;       // GMRES solves started
+  long long cycles;       // restart cycles that ran at least one Arnoldi step
+  long long steps;        // Arnoldi steps
+  long long tri;          // sum over those cycles of n (n - 1) / 2, n = steps of the cycle
+  long long loops;        // passes of the inner WHILE body
+  int k;                  // policy evaluations completed
+  int status;             // MDP_OK, MDP_NOT_CONVERGED or MDP_ERR_NUMERIC
+  int converged;
+  int sweeps;
+  int it_prev;            // K->it after the previous restart residual
+  int numeric_inner;      // a non-finite value stopped GMRES
+  int passes;             // passes of the inner WHILE body in the current evaluation
+  int guard;              // a loop guard ended the solve (never expected: see the control kernels)
+};
+
+__global__ void gs_init_kernel(GraphSolveState* G) {
+  if (threadIdx.x == 0) *G = GraphSolveState{};
+}
+
+// Algorithm 1 step 3 after the sweep: the stop tests in the order of mdp_solve;
+// when the loop goes on, the solver state of the next GMRES solve (what
+// init_state writes from the host: zeros, tol = alpha * res, the caps).
+__global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long long* __restrict__ resmax,
+                                                             GraphSolveState* G, KrylovState* K, double atol,
+                                                             double alpha, int max_iter_pi, int max_iter_ksp, int m,
+                                                             int pstride, cudaGraphConditionalHandle c_outer,
+                                                             cudaGraphConditionalHandle c_go) {
+  const double res = __longlong_as_double((long long)*resmax);
+  // k grows by one per evaluation, so at most max_iter_pi + 1 sweeps run; the guard
+  // on the sweep count bounds the outer loop even if that ever failed
+  const bool guard = G->sweeps > max_iter_pi + 1;
+  const bool go = isfinite(res) && !(res <= atol) && G->k < max_iter_pi && !guard;
+  if (go) {
+    unsigned long long* words = reinterpret_cast<unsigned long long*>(K);
+    for (size_t i = threadIdx.x; i < sizeof(KrylovState) / sizeof(unsigned long long); i += blockDim.x) words[i] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  G->sweeps += 1;
+  G->res = res;
+  if (guard)
+    G->guard = 1;
+  else if (!isfinite(res))
+    G->status = MDP_ERR_NUMERIC;
+  else if (res <= atol)
+    G->converged = 1;
+  else if (G->k >= max_iter_pi)
+    G->status = MDP_NOT_CONVERGED;
+  if (go) {
+    K->tol = alpha * res;
+    K->maxit = max_iter_ksp;
+    K->m = m;
+    K->pstride = pstride;
+    G->it_prev = 0;
+    G->passes = 0;
+    G->solves += 1;
+  }
+  cudaGraphSetConditional(c_go, go ? 1u : 0u);
+  if (!go) cudaGraphSetConditional(c_outer, 0u);
+}
+
+// After a restart residual: count the cycle that just ended and go on while the
+// GMRES solve is not over.  Every cycle runs at least one Arnoldi step (the
+// restart residual clears the cycle's stop flag) and the solve ends at max_it
+// steps, so at most max_it + 1 passes run; the guard bounds the loop regardless.
+__global__ void gs_inner_cond_kernel(KrylovState* K, GraphSolveState* G, int in_loop, int max_passes,
+                                     cudaGraphConditionalHandle c_inner) {
+  if (threadIdx.x != 0) return;
+  if (in_loop && ++G->passes > max_passes) {
+    G->guard = 1;
+    K->flags |= kSolveDone | kNumeric;
+  }
+  const long long n = K->it - G->it_prev;
+  if (n > 0) {
+    G->cycles += 1;
+    G->steps += n;
+    G->tri += n * (n - 1) / 2;
+  }
+  G->it_prev = K->it;
+  if (in_loop) G->loops += 1;
+  cudaGraphSetConditional(c_inner, (K->flags & kSolveDone) ? 0u : 1u);
+}
+
+// End of one policy evaluation (Algorithm 1 steps 12-13): V_{k+1} = theta is
+// already in V; k += 1.  A non-finite value inside GMRES ends the solve as the
+// stream-driven mdp_solve does (no increment).
+__global__ void gs_outer_end_kernel(const KrylovState* K, GraphSolveState* G, cudaGraphConditionalHandle c_outer) {
+  if (threadIdx.x != 0) return;
+  if (K->flags & kNumeric) {
+    G->status = MDP_ERR_NUMERIC;
+    G->numeric_inner = 1;
+    cudaGraphSetConditional(c_outer, 0u);
+    return;
+  }
+  G->inner_total += K->it;
+  G->k += 1;
+}
+
+// What the graph bakes in.
+struct GraphKey {
+  const void* V;
+  const void* pi;
+  const void* basis;
+  const void* basis32;
+  double gamma, atol, alpha;
+  int max_pi, max_ksp, m, refine, precision, tile, blocks, pstore;
+};
+
+struct GraphCache {
+  GraphKey key{};
+  bool valid = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the segments are captured on
+  GraphSolveState* G = nullptr;
+  // kernels per segment, for the launch count
+  int64_t n_init = 0, n_sweep = 0, n_go = 0, n_cycle = 0, n_end = 0;
+};
+
+bool same_key(const GraphKey& a, const GraphKey& b) { return std::memcmp(&a, &b, sizeof(GraphKey)) == 0; }
+
+void drop_graph(GraphCache* c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->exec = nullptr;
+  c->graph = nullptr;
+  c->valid = false;
+}
+
+// Capture what `f` launches on the private stream into a new graph; *kernels
+// receives the number of kernels it launched.
+template <typename F>
+mdp_status capture(mdp_s* h, cudaStream_t cs, cudaGraph_t* out, int64_t* kernels, F f) {
+  *out = nullptr;
+  const int64_t l0 = h->launches;
+  MDP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const mdp_status s = f();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  *kernels = h->launches - l0;
+  h->launches = l0;
+  if (s != MDP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  *out = g;
+  return MDP_OK;
+}
+
+// Add a captured segment to `parent` as a child-graph node after `deps`.
+mdp_status add_segment(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps, cudaGraph_t seg,
+                       cudaGraphNode_t* node) {
+  const cudaError_t e = cudaGraphAddChildGraphNode(node, parent, deps, ndeps, seg);
+  cudaGraphDestroy(seg);  // the node holds its own copy
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddChildGraphNode");
+  return MDP_OK;
+}
+
+mdp_status add_conditional(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps,
+                           cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type, cudaGraphNode_t* node,
+                           cudaGraph_t* body) {
+  // zero-filled storage: the parameter union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = c;
+  p->conditional.type = type;
+  p->conditional.size = 1;
+  MDP_CUDA(cudaGraphAddNode(node, parent, deps, nullptr, ndeps, p));
+  *body = p->conditional.phGraph_out[0];
+  return MDP_OK;
+}
+
+mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double* V, int32_t* pi, bool mixed) {
+  cudaStream_t cs = c->cap;
+  KrylovState* K = (KrylovState*)h->kstate;
+  GraphSolveState* G = c->G;
+  const double gamma = o->gamma;
+  const int m = o->gmres_restart;
+  cudaGraph_t graph = nullptr;
+  MDP_CUDA(cudaGraphCreate(&graph, 0));
+  c->graph = graph;
+  cudaGraphConditionalHandle c_outer, c_go, c_inner;
+  MDP_CUDA(cudaGraphConditionalHandleCreate(&c_outer, graph, 1u, cudaGraphCondAssignDefault));
+  MDP_CUDA(cudaGraphConditionalHandleCreate(&c_go, graph, 0u, cudaGraphCondAssignDefault));
+  MDP_CUDA(cudaGraphConditionalHandleCreate(&c_inner, graph, 0u, cudaGraphCondAssignDefault));
+
+  cudaGraph_t seg = nullptr;
+  cudaGraphNode_t n_init, n_outer;
+  MDP_TRY(capture(h, cs, &seg, &c->n_init, [&]() -> mdp_status {
+    gs_init_kernel<<<1, 32, 0, cs>>>(G);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  }));
+  MDP_TRY(add_segment(graph, nullptr, 0, seg, &n_init));
+  cudaGraph_t outer_body = nullptr;
+  MDP_TRY(add_conditional(graph, &n_init, 1, c_outer, cudaGraphCondTypeWhile, &n_outer, &outer_body));
+
+  // outer body: the sweep and the stop tests, then IF (go) the evaluation
+  cudaGraphNode_t n_sweep, n_if;
+  MDP_TRY(capture(h, cs, &seg, &c->n_sweep, [&]() -> mdp_status {
+    MDP_TRY(launch_bellman(h, gamma, V, h->TV, pi, cs));
+    gs_outer_check_kernel<<<1, 256, 0, cs>>>(h->resmax, G, K, o->atol_pi, o->alpha, o->max_iter_pi, o->max_iter_ksp,
+                                            m, h->partial_stride, c_outer, c_go);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  }));
+  MDP_TRY(add_segment(outer_body, nullptr, 0, seg, &n_sweep));
+  cudaGraph_t go_body = nullptr;
+  MDP_TRY(add_conditional(outer_body, &n_sweep, 1, c_go, cudaGraphCondTypeIf, &n_if, &go_body));
+
+  // evaluation: policy rows, the first restart residual, WHILE (inner) cycles, the end
+  cudaGraphNode_t n_go, n_inner, n_end;
+  MDP_TRY(capture(h, cs, &seg, &c->n_go, [&]() -> mdp_status {
+    MDP_TRY(extract_policy(h, pi, mixed, cs));
+    MDP_TRY(gmres_residual_launch(h, mixed, gamma, V, cs));
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, G, 0, o->max_iter_ksp + 1, c_inner);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  }));
+  MDP_TRY(add_segment(go_body, nullptr, 0, seg, &n_go));
+  cudaGraph_t inner_body = nullptr;
+  MDP_TRY(add_conditional(go_body, &n_go, 1, c_inner, cudaGraphCondTypeWhile, &n_inner, &inner_body));
+  cudaGraphNode_t n_cycle;
+  MDP_TRY(capture(h, cs, &seg, &c->n_cycle, [&]() -> mdp_status {
+    MDP_TRY(gmres_cycle_launch(h, mixed, gamma, V, m, o->gmres_refine, cs));
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, G, 1, o->max_iter_ksp + 1, c_inner);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  }));
+  MDP_TRY(add_segment(inner_body, nullptr, 0, seg, &n_cycle));
+  MDP_TRY(capture(h, cs, &seg, &c->n_end, [&]() -> mdp_status {
+    gs_outer_end_kernel<<<1, 32, 0, cs>>>(K, G, c_outer);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  }));
+  MDP_TRY(add_segment(go_body, &n_inner, 1, seg, &n_end));
+
+  MDP_CUDA(cudaGraphInstantiate(&c->exec, graph, 0));
+  return MDP_OK;
+}
+
+}  // namespace
+
+void graph_cache_free(mdp_s* h) {
+  GraphCache* c = (GraphCache*)h->gcache;
+  if (!c) return;
+  drop_graph(c);
+  if (c->G) cudaFreeAsync(c->G, 0);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+  h->gcache = nullptr;
+}
+
+// mdp_solve with the GMRES inner solver as one graph launch (arguments checked by
+// mdp_solve; stream already bound).  Fills *local like the stream-driven loop.
+mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* local,
+                       cudaStream_t st) {
+  const bool mixed = (o->precision == MDP_PREC_MIXED);
+  MDP_TRY(mixed ? ensure_mixed(h, o->gmres_restart + 1) : ensure_basis(h, o->gmres_restart + 1));
+  GraphCache* c = (GraphCache*)h->gcache;
+  if (!c) {
+    c = new GraphCache();
+    h->gcache = c;
+    MDP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    if (cudaMallocAsync((void**)&c->G, sizeof(GraphSolveState), st) != cudaSuccess) {
+      cudaGetLastError();
+      c->G = nullptr;
+      return fail(MDP_ERR_OOM, "device allocation failed: graph solve state");
+    }
+  }
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  key.V = V;
+  key.pi = pi;
+  key.basis = mixed ? nullptr : (const void*)h->basis;
+  key.basis32 = mixed ? (const void*)h->basis32 : nullptr;
+  key.gamma = o->gamma;
+  key.atol = o->atol_pi;
+  key.alpha = o->alpha;
+  key.max_pi = o->max_iter_pi;
+  key.max_ksp = o->max_iter_ksp;
+  key.m = o->gmres_restart;
+  key.refine = o->gmres_refine;
+  key.precision = o->precision;
+  key.tile = h->bell_tile_states;
+  key.blocks = h->bell_blocks;
+  key.pstore = h->pstore;
+  if (!c->valid || !same_key(c->key, key)) {
+    drop_graph(c);
+    const mdp_status s = build_graph(h, c, o, V, pi, mixed);
+    if (s != MDP_OK) {
+      drop_graph(c);
+      return s;
+    }
+    c->key = key;
+    c->valid = true;
+  }
+  double* pin = tls_pinned();
+  if (!pin) return fail(MDP_ERR_OOM, "pinned host allocation failed");
+  MDP_CUDA(cudaGraphLaunch(c->exec, st));
+  GraphSolveState* out = reinterpret_cast<GraphSolveState*>(pin + 8);
+  static_assert(sizeof(GraphSolveState) <= 48 * sizeof(double), "pinned scratch");
+  MDP_CUDA(cudaMemcpyAsync(out, c->G, sizeof(GraphSolveState), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaEventRecord(h->done, st));
+  MDP_CUDA(cudaStreamSynchronize(st));
+  const GraphSolveState g = *out;
+  local->outer_iters = g.k;
+  local->converged = g.converged;
+  local->inner_iters_total = g.inner_total;
+  local->final_residual = g.res;
+  local->bellman_sweeps = g.sweeps;
+  h->launches += c->n_init + (int64_t)g.sweeps * c->n_sweep + g.solves * (c->n_go + c->n_end) +
+                 g.loops * c->n_cycle;
+  gmres_count_work(h, mixed, g.solves, g.cycles, g.steps, g.tri);
+  if (g.guard) return fail(MDP_ERR_CUDA, "internal: a loop guard of the graph-driven solve ended it");
+  if (g.status == MDP_ERR_NUMERIC)
+    return fail(MDP_ERR_NUMERIC, g.numeric_inner ? "non-finite residual in GMRES" : "non-finite Bellman residual");
+  if (g.status == MDP_NOT_CONVERGED)
+    return fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
+  return MDP_OK;
+}
+
+}  // namespace mdp

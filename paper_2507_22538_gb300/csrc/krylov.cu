@@ -472,8 +472,10 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
+  if (h->timing) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j], st));
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
+  if (h->timing) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
   gm_dots_kernel<NB, T><<<MDP_WAVE((gm_dots_kernel<NB, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
@@ -627,9 +629,23 @@ static void count_cycle(mdp_s* h, int steps) {
   add_vector_bytes(h, 1, sizeof(T));
 }
 
+// record_timing: add the device time of the first n mat-vecs of the cycle that
+// just finished (their events completed before the host read the solver state).
+static mdp_status add_matvec_times(mdp_s* h, int n) {
+  for (int j = 0; j < n; ++j) {
+    float ms = 0.f;
+    MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j], h->mv_ev[2 * j + 1]));
+    h->mv_ms += ms;
+    h->mv_timed += 1;
+  }
+  return MDP_OK;
+}
+
 template <bool U, typename T>
 static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine, double tol, int maxit,
                         int* iters, double* res2, cudaStream_t st) {
+  if (h->timing && !h->mv_ev[0])
+    for (cudaEvent_t& e : h->mv_ev) MDP_CUDA(cudaEventCreate(&e));
   mdp_status r = (sizeof(T) == sizeof(double)) ? ensure_basis(h, m + 1) : ensure_mixed(h, m + 1);
   if (r != MDP_OK) return r;
   const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
@@ -652,6 +668,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
     if (r != MDP_OK) return r;
     if (hd.flags & kSolveDone) break;
     if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
+    if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before));
     it_before = hd.it;
     const int steps = std::min(m, maxit - hd.it);
     for (int j = 0; j < steps; ++j) {
@@ -664,6 +681,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
     if (r != MDP_OK) return r;
   }
   if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
+  if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before));
   if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
   *iters = hd.it;
   *res2 = rn;
@@ -851,6 +869,66 @@ mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* 
 }
 
 size_t krylov_state_bytes() { return sizeof(KrylovState); }
+
+// ---- launch sequences of the GMRES solve for the graph-driven mdp_solve ------------------
+
+// The restart residual r = g_pi - J_pi theta into basis slot 0 (and beta, the stop flags).
+mdp_status gmres_residual_launch(mdp_s* h, bool mixed, double gamma, const double* theta, cudaStream_t st) {
+  const bool U = h->Ppi.uniform;
+  if (mixed) {
+    const KrylovBuffers<float> B = buffers(h, (float*)nullptr);
+    return U ? gm_residual<true>(h, B, gamma, theta, st) : gm_residual<false>(h, B, gamma, theta, st);
+  }
+  const KrylovBuffers<double> B = buffers(h, (double*)nullptr);
+  return U ? gm_residual<true>(h, B, gamma, theta, st) : gm_residual<false>(h, B, gamma, theta, st);
+}
+
+template <bool U, typename T>
+static mdp_status cycle_launch(mdp_s* h, double gamma, double* theta, int m, int refine, cudaStream_t st) {
+  const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
+  for (int j = 0; j < m; ++j) MDP_TRY(arnoldi_dispatch<U>(h, B, gamma, j, refine, st));
+  gm_update_kernel<T><<<MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st>>>(h->S, B.basis, theta, kstate(h));
+  MDP_LAUNCH_CHECK(h);
+  return gm_residual<U>(h, B, gamma, theta, st);
+}
+
+// One restart cycle as gmres() queues it: m Arnoldi steps (the ones after the
+// cycle's stop return at once; the iteration cap stops a cycle on the device),
+// the update of theta and the next restart residual.
+mdp_status gmres_cycle_launch(mdp_s* h, bool mixed, double gamma, double* theta, int m, int refine,
+                              cudaStream_t st) {
+  const bool U = h->Ppi.uniform;
+  if (mixed)
+    return U ? cycle_launch<true, float>(h, gamma, theta, m, refine, st)
+             : cycle_launch<false, float>(h, gamma, theta, m, refine, st);
+  return U ? cycle_launch<true, double>(h, gamma, theta, m, refine, st)
+           : cycle_launch<false, double>(h, gamma, theta, m, refine, st);
+}
+
+// The work counters gmres() adds, summed over `solves` GMRES solves made of
+// `cycles` restart cycles with `steps` Arnoldi steps in all, where `tri` is the
+// sum over cycles of n (n - 1) / 2 for a cycle of n steps.
+void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int64_t steps, int64_t tri) {
+  const size_t sT = mixed ? sizeof(float) : sizeof(double);
+  const size_t vbytes = (!mixed || h->pstore == kStoreF32) ? sT : 2;
+  // the first restart residual of every solve
+  h->matvecs += solves;
+  h->vreads += solves;
+  h->vwrites += solves;
+  add_matvec_bytes(h, (int)solves, sizeof(double), sizeof(double));
+  add_vector_bytes(h, solves, sizeof(double));
+  add_vector_bytes(h, solves, sT);
+  // count_cycle summed in closed form: sum_j (2 j + 2) = n^2 + n over a cycle of n steps
+  const int64_t sq = 2 * tri + steps;
+  h->matvecs += steps + cycles;
+  h->vreads += sq + 2 * steps + 2 * cycles;
+  h->vwrites += 2 * steps + 2 * cycles;
+  add_matvec_bytes(h, (int)steps, vbytes, sT);
+  add_vector_bytes(h, 2 * tri + 5 * steps, sT);
+  add_vector_bytes(h, 3 * cycles, sizeof(double));
+  add_matvec_bytes(h, (int)cycles, sizeof(double), sizeof(double));
+  add_vector_bytes(h, cycles, sT);
+}
 
 mdp_status inner_solve(mdp_s* h, double gamma, double* theta, int inner, int restart, int refine, int precision,
                        double omega, double tol, int max_it, int* iters, double* res2, cudaStream_t st) {

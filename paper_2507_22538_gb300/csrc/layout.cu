@@ -270,6 +270,7 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
 static void destroy_handle(mdp_s* h) {
   if (!h) return;
   if (h->done) cudaEventSynchronize(h->done);  // the last call's work has finished
+  graph_cache_free(h);
   const cudaStream_t st = 0;
   free_sell(st, &h->P);
   free_sell(st, &h->Ppi);
@@ -295,6 +296,8 @@ static void destroy_handle(mdp_s* h) {
   if (h->ev2) cudaEventDestroy(h->ev2);
   if (h->ev3) cudaEventDestroy(h->ev3);
   if (h->done) cudaEventDestroy(h->done);
+  for (cudaEvent_t e : h->mv_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 

@@ -111,6 +111,12 @@ struct mdp_s {
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   cudaEvent_t done = nullptr;  // recorded after the work of every call; mdp_destroy waits on it
+  void* gcache = nullptr;      // instantiated graph of the graph-driven mdp_solve (graph.cu)
+  // record_timing: events around the Arnoldi mat-vec of every GMRES step (created on first use)
+  int timing = 0;
+  cudaEvent_t mv_ev[2 * mdp::kMaxBasis] = {};
+  double mv_ms = 0.0;
+  int64_t mv_timed = 0;
   int64_t launches = 0;
   // algorithmic work counters of the inner solver (see mdp_solve_stats)
   int64_t matvecs = 0, vreads = 0, vwrites = 0;
@@ -149,5 +155,11 @@ mdp_status ensure_basis(mdp_s* h, int nvec);
 mdp_status ensure_mixed(mdp_s* h, int nvec);  // FP32 policy values, basis and w for the mixed solver
 mdp_status ensure_tfqmr(mdp_s* h);            // TFQMR / Jacobi work vectors
 size_t krylov_state_bytes();
+
+// graph.cu: Algorithm 1 with the GMRES inner solver as one CUDA graph launch (fills the
+// iteration fields of *stats; returns MDP_OK, MDP_NOT_CONVERGED, MDP_ERR_NUMERIC or an error)
+mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* stats,
+                       cudaStream_t st);
+void graph_cache_free(mdp_s* h);
 
 }  // namespace mdp

@@ -140,10 +140,20 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
   const double ibytes0 = h->inner_bytes;
+  const double mv_ms0 = h->mv_ms;
+  const int64_t mv_timed0 = h->mv_timed;
   mdp_solve_stats local;
   std::memset(&local, 0, sizeof(local));
   mdp_status status = MDP_OK;
   int k = 0;
+  if (o->graph && o->inner == MDP_GMRES && !o->record_timing) {
+    // the whole loop below as one CUDA graph launch (graph.cu)
+    status = graph_solve(h, o, V, pi, &local, st);
+    if (status != MDP_OK && status != MDP_NOT_CONVERGED && status != MDP_ERR_NUMERIC) return status;
+    k = local.outer_iters;
+  } else {
+  h->timing = o->record_timing ? 1 : 0;
+  struct TimingOff { mdp_s* h; ~TimingOff() { h->timing = 0; } } timing_off{h};
   for (;;) {
     // Algorithm 1 steps 2-3: TV, pi_{k+1} and ||r(V_k)||_inf in one sweep
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev0, st));
@@ -201,12 +211,15 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   }
   MDP_CUDA(cudaEventRecord(h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));
+  }
   local.outer_iters = k;
   local.kernel_launches = h->launches - launches0;
   local.policy_matvecs = h->matvecs - matvecs0;
   local.vector_reads = h->vreads - vreads0;
   local.vector_writes = h->vwrites - vwrites0;
   local.inner_bytes = h->inner_bytes - ibytes0;
+  local.matvec_ms = h->mv_ms - mv_ms0;
+  local.matvecs_timed = h->mv_timed - mv_timed0;
   local.policy_value_bytes = !mixed ? 8 : (h->pstore == kStoreF32 ? 4 : 2);
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = local;

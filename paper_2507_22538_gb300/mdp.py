@@ -42,7 +42,8 @@ class mdp_solve_opts(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("atol_pi", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("richardson_scale", ctypes.c_double), ("max_iter_pi", ctypes.c_int32),
                 ("max_iter_ksp", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):
@@ -52,7 +53,8 @@ class mdp_solve_stats(ctypes.Structure):
                 ("bellman_sweeps", ctypes.c_int32), ("bellman_ms", ctypes.c_double),
                 ("inner_ms", ctypes.c_double), ("policy_matvecs", ctypes.c_int64),
                 ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double),
-                ("policy_value_bytes", ctypes.c_int32)]
+                ("policy_value_bytes", ctypes.c_int32), ("matvec_ms", ctypes.c_double),
+                ("matvecs_timed", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -277,7 +279,7 @@ class MDP:
 
     def solve(self, gamma, V0=None, tol=1e-8, alpha=1e-4, inner=MDP_GMRES, restart=30, omega=1.0,
               max_outer=1000, max_inner=1000, record_timing=False, refine=MDP_REFINE_NEVER, precision=MDP_PREC_F64,
-              stream=None, device="cuda"):
+              stream=None, device="cuda", graph=False):
         import torch
         o = mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.richardson_scale = gamma, tol, alpha, omega
@@ -285,6 +287,7 @@ class MDP:
         o.record_timing = 1 if record_timing else 0
         o.gmres_refine = refine
         o.precision = precision
+        o.graph = 1 if graph else 0
         V = torch.zeros(self.S, dtype=torch.float64, device=device) if V0 is None else V0.clone()
         pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
         st, stats = mdp_solve(self.h, o, V, pi, stream)

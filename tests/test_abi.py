@@ -56,7 +56,30 @@ def test_host_only_calls(lib):
     assert mdp.mdp_bellman(None, 0.9, 1, 2, 3, None, stream=0) == mdp.MDP_ERR_INVALID_ARG
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """Every field offset and the size of the option and statistics structs, as
+    the C compiler lays them out from include/mdp.h, equal the ctypes mirror's."""
+    import shutil
+    import subprocess
+
     from paper_2507_22538_gb300 import mdp
-    assert ctypes.sizeof(mdp.mdp_solve_opts) == 4 * 8 + 7 * 4 + 4  # padded to 8
-    assert ctypes.sizeof(mdp.mdp_solve_stats) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 8 + 8 + 3 * 8 + 8 + 4 + 4
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mdp.h"', "int main(void) {"]
+    for st in (mdp.mdp_solve_opts, mdp.mdp_solve_stats):
+        lines.append(f'  printf("{st.__name__} sizeof %zu\\n", sizeof({st.__name__}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{st.__name__} {f} %zu\\n", offsetof({st.__name__}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in (mdp.mdp_solve_opts, mdp.mdp_solve_stats):
+        assert c[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
+        for f, _ in st._fields_:
+            assert c[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
