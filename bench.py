@@ -833,7 +833,8 @@ def main():
                                         krylov_source_sha()),
                "bytes_per_launch": matvec_bytes(), "avg_launch_ms": mv_ms,
                "launches_timed": int(totals["matvecs_timed"]),
-               "share_of_step": totals["matvec_ms"] / (ms * args.steps)}
+               # every Arnoldi step launches one mat-vec; the timed ones are a sample of them
+               "share_of_step": mv_ms * totals["inner_iters_total"] / (ms * args.steps)}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}

@@ -104,9 +104,10 @@ typedef struct {
   int32_t policy_value_bytes; /* bytes per probability the inner mat-vecs read: 8 (binary64), or with
                                  MDP_PREC_MIXED 4 (binary32) or 2 (binary16 / bfloat16, used when every
                                  probability of the MDP is exactly representable there) */
-  double matvec_ms;           /* summed device time of the GMRES steps' policy mat-vec kernels, each
-                                 between its own pair of CUDA events (record_timing only) */
-  int64_t matvecs_timed;      /* mat-vec kernels timed in matvec_ms (steps that ran) */
+  double matvec_ms;           /* summed device time of the policy mat-vec kernels of GMRES steps
+                                 j = 0, 8, 16, ... of every restart cycle, each between its own pair
+                                 of CUDA events (record_timing only; all mat-vecs do the same work) */
+  int64_t matvecs_timed;      /* mat-vec kernels timed in matvec_ms */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -11,15 +11,22 @@
 //     IF (go)                             set by the check
 //       policy rows; restart residual     step 4 and the first GMRES residual
 //       WHILE (inner)                     one GMRES(m) restart cycle per pass
-//         m Arnoldi steps; update; restart residual
+//         steps 0-3; IF (go 1) steps 4-7; IF (go 2) steps 8-11; ...
+//         update; restart residual
 //       end of the evaluation             k += 1
 //
+// The Arnoldi steps of a cycle come in chunks of kChunkSteps.  Chunk q > 0 runs
+// under an IF with its own condition, which the control kernel after chunk q - 1
+// sets while the cycle goes on; the one after chunk 0 (which always runs) first
+// clears the conditions of chunks 2 and up.  The steps after a cycle's stop are
+// therefore skipped instead of launched as no-ops.
 // Small control kernels set the conditions (cudaGraphSetConditional) from the
 // residual and the solver's device flags.  The other nodes are the kernels the
 // stream-driven solve launches, with the same launch shapes, so both give the
 // same iterates bit for bit.  The instantiated graph is kept in the handle and
 // rebuilt only when something it bakes in changes (vectors, gamma, options,
 // the Bellman launch shape).
+#include <algorithm>
 #include <cstring>
 
 #include "krylov_dev.cuh"
@@ -28,10 +35,15 @@ namespace mdp {
 
 // launch sequences of krylov.cu (same kernels as the stream-driven GMRES)
 mdp_status gmres_residual_launch(mdp_s* h, bool mixed, double gamma, const double* theta, cudaStream_t st);
-mdp_status gmres_cycle_launch(mdp_s* h, bool mixed, double gamma, double* theta, int m, int refine, cudaStream_t st);
+mdp_status gmres_steps_launch(mdp_s* h, bool mixed, double gamma, int j0, int j1, int refine, cudaStream_t st);
+mdp_status gmres_tail_launch(mdp_s* h, bool mixed, double gamma, double* theta, cudaStream_t st);
 void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int64_t steps, int64_t tri);
 
 namespace {
+
+constexpr int kChunkSteps = 4;              // Arnoldi steps per IF-guarded chunk of a cycle
+constexpr int kMaxChunks = (kMaxBasis + kChunkSteps - 1) / kChunkSteps;
+constexpr int kSegments = 3 + kMaxChunks + 2;  // init, sweep, go, chunks, tail, end
 
 // Device record of one graph-driven solve.
 struct GraphSolveState {
@@ -50,20 +62,31 @@ struct GraphSolveState {
   int numeric_inner;      // a non-finite value stopped GMRES
   int passes;             // passes of the inner WHILE body in the current evaluation
   int guard;              // a loop guard ended the solve (never expected: see the control kernels)
+  long long launches;     // kernels that ran: every segment's control kernel adds its segment's count
 };
 
-__global__ void gs_init_kernel(GraphSolveState* G) {
-  if (threadIdx.x == 0) *G = GraphSolveState{};
+// The solve record and the kernels per captured segment (filled by the host after
+// the graph is built; each segment ends with its control kernel).
+struct GraphDevice {
+  GraphSolveState G;
+  int seg_kernels[kSegments];
+};
+
+__global__ void gs_init_kernel(GraphDevice* D, int seg) {
+  if (threadIdx.x != 0) return;
+  D->G = GraphSolveState{};
+  D->G.launches = D->seg_kernels[seg];
 }
 
 // Algorithm 1 step 3 after the sweep: the stop tests in the order of mdp_solve;
 // when the loop goes on, the solver state of the next GMRES solve (what
 // init_state writes from the host: zeros, tol = alpha * res, the caps).
 __global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long long* __restrict__ resmax,
-                                                             GraphSolveState* G, KrylovState* K, double atol,
+                                                             GraphDevice* D, int seg, KrylovState* K, double atol,
                                                              double alpha, int max_iter_pi, int max_iter_ksp, int m,
                                                              int pstride, cudaGraphConditionalHandle c_outer,
                                                              cudaGraphConditionalHandle c_go) {
+  GraphSolveState* G = &D->G;
   const double res = __longlong_as_double((long long)*resmax);
   // k grows by one per evaluation, so at most max_iter_pi + 1 sweeps run; the guard
   // on the sweep count bounds the outer loop even if that ever failed
@@ -75,6 +98,7 @@ __global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  G->launches += D->seg_kernels[seg];
   G->sweeps += 1;
   G->res = res;
   if (guard)
@@ -102,9 +126,11 @@ __global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long
 // GMRES solve is not over.  Every cycle runs at least one Arnoldi step (the
 // restart residual clears the cycle's stop flag) and the solve ends at max_it
 // steps, so at most max_it + 1 passes run; the guard bounds the loop regardless.
-__global__ void gs_inner_cond_kernel(KrylovState* K, GraphSolveState* G, int in_loop, int max_passes,
+__global__ void gs_inner_cond_kernel(KrylovState* K, GraphDevice* D, int seg, int in_loop, int max_passes,
                                      cudaGraphConditionalHandle c_inner) {
   if (threadIdx.x != 0) return;
+  GraphSolveState* G = &D->G;
+  G->launches += D->seg_kernels[seg];
   if (in_loop && ++G->passes > max_passes) {
     G->guard = 1;
     K->flags |= kSolveDone | kNumeric;
@@ -120,11 +146,27 @@ __global__ void gs_inner_cond_kernel(KrylovState* K, GraphSolveState* G, int in_
   cudaGraphSetConditional(c_inner, (K->flags & kSolveDone) ? 0u : 1u);
 }
 
+struct ChunkHandles {
+  cudaGraphConditionalHandle go[kMaxChunks];  // go[q] guards chunk q (q >= 1)
+};
+
+// After chunk q of Arnoldi steps: chunk q + 1 runs only while the cycle goes on.
+__global__ void gs_chunk_cond_kernel(const KrylovState* K, GraphDevice* D, int seg, ChunkHandles hs, int q,
+                                     int nchunks) {
+  if (threadIdx.x != 0) return;
+  D->G.launches += D->seg_kernels[seg];
+  if (q == 0)
+    for (int i = 2; i < nchunks; ++i) cudaGraphSetConditional(hs.go[i], 0u);
+  if (q + 1 < nchunks) cudaGraphSetConditional(hs.go[q + 1], (K->flags & (kCycleStop | kSolveDone)) ? 0u : 1u);
+}
+
 // End of one policy evaluation (Algorithm 1 steps 12-13): V_{k+1} = theta is
 // already in V; k += 1.  A non-finite value inside GMRES ends the solve as the
 // stream-driven mdp_solve does (no increment).
-__global__ void gs_outer_end_kernel(const KrylovState* K, GraphSolveState* G, cudaGraphConditionalHandle c_outer) {
+__global__ void gs_outer_end_kernel(const KrylovState* K, GraphDevice* D, int seg, cudaGraphConditionalHandle c_outer) {
   if (threadIdx.x != 0) return;
+  GraphSolveState* G = &D->G;
+  G->launches += D->seg_kernels[seg];
   if (K->flags & kNumeric) {
     G->status = MDP_ERR_NUMERIC;
     G->numeric_inner = 1;
@@ -151,9 +193,8 @@ struct GraphCache {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;  // private stream the segments are captured on
-  GraphSolveState* G = nullptr;
-  // kernels per segment, for the launch count
-  int64_t n_init = 0, n_sweep = 0, n_go = 0, n_cycle = 0, n_end = 0;
+  GraphDevice* D = nullptr;
+  int seg_kernels[kSegments] = {};  // host copy of the kernels per segment
 };
 
 bool same_key(const GraphKey& a, const GraphKey& b) { return std::memcmp(&a, &b, sizeof(GraphKey)) == 0; }
@@ -169,14 +210,14 @@ void drop_graph(GraphCache* c) {
 // Capture what `f` launches on the private stream into a new graph; *kernels
 // receives the number of kernels it launched.
 template <typename F>
-mdp_status capture(mdp_s* h, cudaStream_t cs, cudaGraph_t* out, int64_t* kernels, F f) {
+mdp_status capture(mdp_s* h, cudaStream_t cs, cudaGraph_t* out, int* kernels, F f) {
   *out = nullptr;
   const int64_t l0 = h->launches;
   MDP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   const mdp_status s = f();
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(cs, &g);
-  *kernels = h->launches - l0;
+  *kernels = (int)(h->launches - l0);
   h->launches = l0;
   if (s != MDP_OK) {
     if (g) cudaGraphDestroy(g);
@@ -211,12 +252,18 @@ mdp_status add_conditional(cudaGraph_t parent, const cudaGraphNode_t* deps, size
   return MDP_OK;
 }
 
-mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double* V, int32_t* pi, bool mixed) {
+mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double* V, int32_t* pi, bool mixed,
+                       cudaStream_t st) {
   cudaStream_t cs = c->cap;
   KrylovState* K = (KrylovState*)h->kstate;
-  GraphSolveState* G = c->G;
+  GraphDevice* D = c->D;
   const double gamma = o->gamma;
   const int m = o->gmres_restart;
+  const int nchunks = (m + kChunkSteps - 1) / kChunkSteps;
+  enum { kSegInit = 0, kSegSweep = 1, kSegGo = 2, kSegChunk0 = 3 };
+  const int seg_tail = kSegChunk0 + nchunks, seg_end = seg_tail + 1;
+  int* nk = c->seg_kernels;
+  std::memset(nk, 0, sizeof(c->seg_kernels));
   cudaGraph_t graph = nullptr;
   MDP_CUDA(cudaGraphCreate(&graph, 0));
   c->graph = graph;
@@ -224,14 +271,21 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
   MDP_CUDA(cudaGraphConditionalHandleCreate(&c_outer, graph, 1u, cudaGraphCondAssignDefault));
   MDP_CUDA(cudaGraphConditionalHandleCreate(&c_go, graph, 0u, cudaGraphCondAssignDefault));
   MDP_CUDA(cudaGraphConditionalHandleCreate(&c_inner, graph, 0u, cudaGraphCondAssignDefault));
-
-  cudaGraph_t seg = nullptr;
-  cudaGraphNode_t n_init, n_outer;
-  MDP_TRY(capture(h, cs, &seg, &c->n_init, [&]() -> mdp_status {
-    gs_init_kernel<<<1, 32, 0, cs>>>(G);
+  ChunkHandles hs;
+  std::memset(&hs, 0, sizeof(hs));
+  for (int q = 1; q < nchunks; ++q)
+    MDP_CUDA(cudaGraphConditionalHandleCreate(&hs.go[q], graph, 0u, cudaGraphCondAssignDefault));
+  auto control_done = [&]() -> mdp_status {
     h->launches++;
     MDP_CUDA(cudaGetLastError());
     return MDP_OK;
+  };
+
+  cudaGraph_t seg = nullptr;
+  cudaGraphNode_t n_init, n_outer;
+  MDP_TRY(capture(h, cs, &seg, &nk[kSegInit], [&]() -> mdp_status {
+    gs_init_kernel<<<1, 32, 0, cs>>>(D, kSegInit);
+    return control_done();
   }));
   MDP_TRY(add_segment(graph, nullptr, 0, seg, &n_init));
   cudaGraph_t outer_body = nullptr;
@@ -239,13 +293,11 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
 
   // outer body: the sweep and the stop tests, then IF (go) the evaluation
   cudaGraphNode_t n_sweep, n_if;
-  MDP_TRY(capture(h, cs, &seg, &c->n_sweep, [&]() -> mdp_status {
+  MDP_TRY(capture(h, cs, &seg, &nk[kSegSweep], [&]() -> mdp_status {
     MDP_TRY(launch_bellman(h, gamma, V, h->TV, pi, cs));
-    gs_outer_check_kernel<<<1, 256, 0, cs>>>(h->resmax, G, K, o->atol_pi, o->alpha, o->max_iter_pi, o->max_iter_ksp,
-                                            m, h->partial_stride, c_outer, c_go);
-    h->launches++;
-    MDP_CUDA(cudaGetLastError());
-    return MDP_OK;
+    gs_outer_check_kernel<<<1, 256, 0, cs>>>(h->resmax, D, kSegSweep, K, o->atol_pi, o->alpha, o->max_iter_pi,
+                                            o->max_iter_ksp, m, h->partial_stride, c_outer, c_go);
+    return control_done();
   }));
   MDP_TRY(add_segment(outer_body, nullptr, 0, seg, &n_sweep));
   cudaGraph_t go_body = nullptr;
@@ -253,35 +305,57 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
 
   // evaluation: policy rows, the first restart residual, WHILE (inner) cycles, the end
   cudaGraphNode_t n_go, n_inner, n_end;
-  MDP_TRY(capture(h, cs, &seg, &c->n_go, [&]() -> mdp_status {
+  MDP_TRY(capture(h, cs, &seg, &nk[kSegGo], [&]() -> mdp_status {
     MDP_TRY(extract_policy(h, pi, mixed, cs));
     MDP_TRY(gmres_residual_launch(h, mixed, gamma, V, cs));
-    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, G, 0, o->max_iter_ksp + 1, c_inner);
-    h->launches++;
-    MDP_CUDA(cudaGetLastError());
-    return MDP_OK;
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, kSegGo, 0, o->max_iter_ksp + 1, c_inner);
+    return control_done();
   }));
   MDP_TRY(add_segment(go_body, nullptr, 0, seg, &n_go));
   cudaGraph_t inner_body = nullptr;
   MDP_TRY(add_conditional(go_body, &n_go, 1, c_inner, cudaGraphCondTypeWhile, &n_inner, &inner_body));
-  cudaGraphNode_t n_cycle;
-  MDP_TRY(capture(h, cs, &seg, &c->n_cycle, [&]() -> mdp_status {
-    MDP_TRY(gmres_cycle_launch(h, mixed, gamma, V, m, o->gmres_refine, cs));
-    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, G, 1, o->max_iter_ksp + 1, c_inner);
-    h->launches++;
-    MDP_CUDA(cudaGetLastError());
-    return MDP_OK;
+
+  // one restart cycle: chunk 0, then chunks 1.. each under its own IF, in sequence
+  cudaGraphNode_t prev = nullptr;  // the last node of the cycle so far in inner_body
+  for (int q = 0; q < nchunks; ++q) {
+    const int j0 = q * kChunkSteps, j1 = std::min(m, j0 + kChunkSteps);
+    MDP_TRY(capture(h, cs, &seg, &nk[kSegChunk0 + q], [&]() -> mdp_status {
+      MDP_TRY(gmres_steps_launch(h, mixed, gamma, j0, j1, o->gmres_refine, cs));
+      gs_chunk_cond_kernel<<<1, 32, 0, cs>>>(K, D, kSegChunk0 + q, hs, q, nchunks);
+      return control_done();
+    }));
+    if (q == 0) {
+      MDP_TRY(add_segment(inner_body, nullptr, 0, seg, &prev));
+    } else {
+      cudaGraphNode_t n_if_chunk, n_chunk;
+      cudaGraph_t chunk_body = nullptr;
+      const mdp_status s_if = add_conditional(inner_body, &prev, 1, hs.go[q], cudaGraphCondTypeIf, &n_if_chunk,
+                                              &chunk_body);
+      if (s_if != MDP_OK) {
+        cudaGraphDestroy(seg);
+        return s_if;
+      }
+      MDP_TRY(add_segment(chunk_body, nullptr, 0, seg, &n_chunk));
+      prev = n_if_chunk;
+    }
+  }
+  cudaGraphNode_t n_tail;
+  MDP_TRY(capture(h, cs, &seg, &nk[seg_tail], [&]() -> mdp_status {
+    MDP_TRY(gmres_tail_launch(h, mixed, gamma, V, cs));
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, seg_tail, 1, o->max_iter_ksp + 1, c_inner);
+    return control_done();
   }));
-  MDP_TRY(add_segment(inner_body, nullptr, 0, seg, &n_cycle));
-  MDP_TRY(capture(h, cs, &seg, &c->n_end, [&]() -> mdp_status {
-    gs_outer_end_kernel<<<1, 32, 0, cs>>>(K, G, c_outer);
-    h->launches++;
-    MDP_CUDA(cudaGetLastError());
-    return MDP_OK;
+  MDP_TRY(add_segment(inner_body, &prev, 1, seg, &n_tail));
+  MDP_TRY(capture(h, cs, &seg, &nk[seg_end], [&]() -> mdp_status {
+    gs_outer_end_kernel<<<1, 32, 0, cs>>>(K, D, seg_end, c_outer);
+    return control_done();
   }));
   MDP_TRY(add_segment(go_body, &n_inner, 1, seg, &n_end));
 
   MDP_CUDA(cudaGraphInstantiate(&c->exec, graph, 0));
+  // the kernels per segment, read by the control kernels
+  MDP_CUDA(cudaMemcpyAsync(D->seg_kernels, nk, sizeof(c->seg_kernels), cudaMemcpyHostToDevice, st));
+  MDP_CUDA(cudaStreamSynchronize(st));
   return MDP_OK;
 }
 
@@ -291,7 +365,7 @@ void graph_cache_free(mdp_s* h) {
   GraphCache* c = (GraphCache*)h->gcache;
   if (!c) return;
   drop_graph(c);
-  if (c->G) cudaFreeAsync(c->G, 0);
+  if (c->D) cudaFreeAsync(c->D, 0);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   h->gcache = nullptr;
@@ -308,9 +382,9 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
     c = new GraphCache();
     h->gcache = c;
     MDP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    if (cudaMallocAsync((void**)&c->G, sizeof(GraphSolveState), st) != cudaSuccess) {
+    if (cudaMallocAsync((void**)&c->D, sizeof(GraphDevice), st) != cudaSuccess) {
       cudaGetLastError();
-      c->G = nullptr;
+      c->D = nullptr;
       return fail(MDP_ERR_OOM, "device allocation failed: graph solve state");
     }
   }
@@ -333,7 +407,7 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   key.pstore = h->pstore;
   if (!c->valid || !same_key(c->key, key)) {
     drop_graph(c);
-    const mdp_status s = build_graph(h, c, o, V, pi, mixed);
+    const mdp_status s = build_graph(h, c, o, V, pi, mixed, st);
     if (s != MDP_OK) {
       drop_graph(c);
       return s;
@@ -346,7 +420,7 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   MDP_CUDA(cudaGraphLaunch(c->exec, st));
   GraphSolveState* out = reinterpret_cast<GraphSolveState*>(pin + 8);
   static_assert(sizeof(GraphSolveState) <= 48 * sizeof(double), "pinned scratch");
-  MDP_CUDA(cudaMemcpyAsync(out, c->G, sizeof(GraphSolveState), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaMemcpyAsync(out, &c->D->G, sizeof(GraphSolveState), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaEventRecord(h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   const GraphSolveState g = *out;
@@ -355,8 +429,7 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   local->inner_iters_total = g.inner_total;
   local->final_residual = g.res;
   local->bellman_sweeps = g.sweeps;
-  h->launches += c->n_init + (int64_t)g.sweeps * c->n_sweep + g.solves * (c->n_go + c->n_end) +
-                 g.loops * c->n_cycle;
+  h->launches += g.launches;
   gmres_count_work(h, mixed, g.solves, g.cycles, g.steps, g.tri);
   if (g.guard) return fail(MDP_ERR_CUDA, "internal: a loop guard of the graph-driven solve ended it");
   if (g.status == MDP_ERR_NUMERIC)

@@ -472,10 +472,11 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
-  if (h->timing) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j], st));
+  const bool timed = h->timing && (j % kMatvecTimingStride) == 0;
+  if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j], st));
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
-  if (h->timing) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
+  if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
   gm_dots_kernel<NB, T><<<MDP_WAVE((gm_dots_kernel<NB, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
@@ -629,10 +630,13 @@ static void count_cycle(mdp_s* h, int steps) {
   add_vector_bytes(h, 1, sizeof(T));
 }
 
-// record_timing: add the device time of the first n mat-vecs of the cycle that
-// just finished (their events completed before the host read the solver state).
+// record_timing: add the device time of the timed mat-vecs among the first n
+// steps of the cycle that just finished (their events completed before the host
+// read the solver state).  Every kMatvecTimingStride-th step of a cycle is timed:
+// all mat-vecs do the same work, and an event pair around every one of them cost
+// about 2% of the solve.
 static mdp_status add_matvec_times(mdp_s* h, int n) {
-  for (int j = 0; j < n; ++j) {
+  for (int j = 0; j < n; j += kMatvecTimingStride) {
     float ms = 0.f;
     MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j], h->mv_ev[2 * j + 1]));
     h->mv_ms += ms;
@@ -884,25 +888,36 @@ mdp_status gmres_residual_launch(mdp_s* h, bool mixed, double gamma, const doubl
 }
 
 template <bool U, typename T>
-static mdp_status cycle_launch(mdp_s* h, double gamma, double* theta, int m, int refine, cudaStream_t st) {
+static mdp_status steps_launch(mdp_s* h, double gamma, int j0, int j1, int refine, cudaStream_t st) {
   const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
-  for (int j = 0; j < m; ++j) MDP_TRY(arnoldi_dispatch<U>(h, B, gamma, j, refine, st));
+  for (int j = j0; j < j1; ++j) MDP_TRY(arnoldi_dispatch<U>(h, B, gamma, j, refine, st));
+  return MDP_OK;
+}
+
+template <bool U, typename T>
+static mdp_status tail_launch(mdp_s* h, double gamma, double* theta, cudaStream_t st) {
+  const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
   gm_update_kernel<T><<<MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st>>>(h->S, B.basis, theta, kstate(h));
   MDP_LAUNCH_CHECK(h);
   return gm_residual<U>(h, B, gamma, theta, st);
 }
 
-// One restart cycle as gmres() queues it: m Arnoldi steps (the ones after the
-// cycle's stop return at once; the iteration cap stops a cycle on the device),
-// the update of theta and the next restart residual.
-mdp_status gmres_cycle_launch(mdp_s* h, bool mixed, double gamma, double* theta, int m, int refine,
-                              cudaStream_t st) {
+// Arnoldi steps j0..j1-1 of a restart cycle as gmres() queues them (steps after
+// the cycle's stop return at once; the iteration cap stops a cycle on the device).
+mdp_status gmres_steps_launch(mdp_s* h, bool mixed, double gamma, int j0, int j1, int refine, cudaStream_t st) {
   const bool U = h->Ppi.uniform;
   if (mixed)
-    return U ? cycle_launch<true, float>(h, gamma, theta, m, refine, st)
-             : cycle_launch<false, float>(h, gamma, theta, m, refine, st);
-  return U ? cycle_launch<true, double>(h, gamma, theta, m, refine, st)
-           : cycle_launch<false, double>(h, gamma, theta, m, refine, st);
+    return U ? steps_launch<true, float>(h, gamma, j0, j1, refine, st)
+             : steps_launch<false, float>(h, gamma, j0, j1, refine, st);
+  return U ? steps_launch<true, double>(h, gamma, j0, j1, refine, st)
+           : steps_launch<false, double>(h, gamma, j0, j1, refine, st);
+}
+
+// The end of a restart cycle: the update of theta and the next restart residual.
+mdp_status gmres_tail_launch(mdp_s* h, bool mixed, double gamma, double* theta, cudaStream_t st) {
+  const bool U = h->Ppi.uniform;
+  if (mixed) return U ? tail_launch<true, float>(h, gamma, theta, st) : tail_launch<false, float>(h, gamma, theta, st);
+  return U ? tail_launch<true, double>(h, gamma, theta, st) : tail_launch<false, double>(h, gamma, theta, st);
 }
 
 // The work counters gmres() adds, summed over `solves` GMRES solves made of

@@ -155,8 +155,11 @@ def test_graph_solve_certified_by_oracle():
     m = random_sparse(1000, 4, 8, 0.9, seed=1)
     with mdp.MDP.from_data(m) as M:
         V, pi, stats, st = M.solve(m.gamma, tol=1e-10, alpha=1e-3, graph=True)
+        _, _, stats_stream, _ = M.solve(m.gamma, tol=1e-10, alpha=1e-3)
         torch.cuda.synchronize()
     assert st == mdp.MDP_OK and stats.converged == 1
+    # the cycles stop after ~13 of 30 steps: the graph skips the rest, the stream path launches them as no-ops
+    assert 0 < stats.kernel_launches < stats_stream.kernel_launches
     Vs, ps, _ = O.policy_iteration(m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma)
     Vg = V.cpu().numpy()
     assert float(np.max(np.abs(Vg - Vs))) <= 1e-8 * float(np.max(np.abs(Vs)))
