@@ -39,7 +39,12 @@ typedef enum {
   MDP_ERR_NUMERIC = 6         /* NaN or Inf appeared in a residual */
 } mdp_status;
 
-typedef enum { MDP_F64 = 0 } mdp_dtype; /* storage type of the P values passed to mdp_create */
+/* Storage type of the P values passed to mdp_create.  The library widens every value
+   exactly to binary64 on the device, so an MDP whose probabilities are exact in a
+   narrower type (multiples of 2^-11 summing to 1 are exact in binary16, of 2^-8 in
+   bfloat16) gives the same handle, and the same results bit for bit, from either
+   type; the narrower one only moves fewer bytes at upload. */
+typedef enum { MDP_F64 = 0, MDP_F32 = 1, MDP_F16 = 2, MDP_BF16 = 3 } mdp_dtype;
 
 /* Inner solvers of Algorithm 1 (Sec. III-B.3, Table 2): restarted GMRES (the
    default), Richardson (VI, OPI(W), beta-VI), TFQMR (used for the pendulum and
@@ -120,7 +125,10 @@ void mdp_default_opts(mdp_solve_opts* opts);
  *  S, A          number of states (1 .. 2^31-1) and actions (1 .. 8192), S*A < 2^36.
  *  row_ptr       int64[S*A + 1], row_ptr[0] = 0, nondecreasing.
  *  col           int32[nnz] column (successor state) of each entry, in [0, S).
- *  val           P values, nnz entries of val_type (MDP_F64: double).
+ *  val           P values, nnz entries of val_type: double (MDP_F64), float (MDP_F32),
+ *                IEEE binary16 (MDP_F16) or bfloat16 (MDP_BF16) bit patterns; widened
+ *                exactly to binary64, so the row-sum test below applies to the widened
+ *                values (MDP_ERR_INVALID_ARG for any other val_type).
  *  g             double[S*A] stage costs, finite.
  *  inputs_on_device  nonzero: the four arrays are device pointers; zero: host pointers
  *                (pinned host memory gives the fastest upload).

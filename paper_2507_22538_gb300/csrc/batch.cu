@@ -501,6 +501,7 @@ extern "C" {
 
 mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve_opts* opts, double* const* V,
                            int32_t* const* pi, mdp_solve_stats* stats, mdp_status* status, void* stream) {
+  NvtxRange range("mdp_solve_batch");
   const auto t0 = std::chrono::steady_clock::now();
   if (n < 1 || !handles || !opts || !V || !pi || !status) return fail(MDP_ERR_INVALID_ARG, "null argument or n < 1");
   cudaStream_t st = (cudaStream_t)stream;

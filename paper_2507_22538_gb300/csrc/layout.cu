@@ -54,11 +54,19 @@ __device__ __forceinline__ bool exact_in(uint64_t bits, int p, int emin, int ema
   return (bits & dropped) == 0;
 }
 
+// Exact widening of the caller's value type to binary64.
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return (double)v; }
+__device__ __forceinline__ double widen(__half v) { return (double)__half2float(v); }
+__device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
 // One thread per row of Eq. 5: check the CSR invariants, record the row length and
 // whether every probability is exact in binary16 / bfloat16 (the narrowest exact
-// storage for the mixed solver's copies of the policy rows).
+// storage for the mixed solver's copies of the policy rows).  Values of type TV are
+// widened to binary64 first.
+template <typename TV>
 __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                     const double* __restrict__ val, const double* __restrict__ g, int64_t R,
+                                     const TV* __restrict__ val, const double* __restrict__ g, int64_t R,
                                      int64_t S, int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
                                      int* __restrict__ kmin, int* __restrict__ kmax, int* __restrict__ f16_ok,
                                      int* __restrict__ bf16_ok) {
@@ -79,7 +87,7 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
       double sum = 0.0;
       for (int64_t j = lo; j < hi; ++j) {
         int c = col[j];
-        double v = val[j];
+        double v = widen(val[j]);
         if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
         if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
         const uint64_t bits = (uint64_t)__double_as_longlong(v);
@@ -123,9 +131,11 @@ __global__ void state_maxlen_kernel(const int32_t* __restrict__ len, int64_t S, 
   }
 }
 
-// CSR -> sliced ELL: one thread per row copies its entries into their chunked slice positions.
+// CSR -> sliced ELL: one thread per row copies its entries (widened to binary64)
+// into their chunked slice positions.
+template <typename TV>
 __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                   const double* __restrict__ val, int64_t R, const int64_t* __restrict__ off,
+                                   const TV* __restrict__ val, int64_t R, const int64_t* __restrict__ off,
                                    int uniform_k, double* __restrict__ sval, int32_t* __restrict__ scol) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
     int64_t q = r / kSlice;
@@ -136,7 +146,7 @@ __global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t
     for (int j = 0; j < (int)width; ++j) {
       const int64_t d = sell_at(base, (int)width, lane, j);
       if (j < n) {
-        sval[d] = val[lo + j];
+        sval[d] = widen(val[lo + j]);
         scol[d] = col[lo + j];
       } else {
         sval[d] = 0.0;
@@ -389,24 +399,26 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
     return fail(MDP_ERR_NOT_STOCHASTIC, "row_ptr[S*A] must be between S*A (no empty rows) and 2^40");
   h->nnz = nnz;
 
-  // device views of the CSR input (temporary copies when it lives on the host)
+  // device views of the CSR input (temporary copies when it lives on the host; the
+  // values keep the caller's type, so a narrow type also uploads fewer bytes)
+  const size_t vbytes = val_type == MDP_F64 ? 8 : val_type == MDP_F32 ? 4 : 2;
   const int64_t* drp = row_ptr;
   const int32_t* dcol = col;
-  const double* dval = (const double*)val;
+  const void* dval = val;
   int64_t* trp = nullptr;
   int32_t* tcol = nullptr;
-  double* tval = nullptr;
+  uint16_t* tval = nullptr;  // nnz * vbytes bytes
   struct Temps {
-    cudaStream_t st; int64_t** a; int32_t** b; double** c;
+    cudaStream_t st; int64_t** a; int32_t** b; uint16_t** c;
     ~Temps() { dfree(st, *a); dfree(st, *b); dfree(st, *c); }
   } temps{st, &trp, &tcol, &tval};
   if (!on_device) {
     MDP_TRY(dalloc(h, &trp, R + 1, "row pointers"));
     MDP_TRY(dalloc(h, &tcol, nnz, "columns"));
-    MDP_TRY(dalloc(h, &tval, nnz, "values"));
+    MDP_TRY(dalloc(h, &tval, nnz * (vbytes / 2), "values"));
     MDP_CUDA(cudaMemcpyAsync(trp, row_ptr, (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     MDP_CUDA(cudaMemcpyAsync(tcol, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MDP_CUDA(cudaMemcpyAsync(tval, val, nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    MDP_CUDA(cudaMemcpyAsync(tval, val, nnz * vbytes, cudaMemcpyHostToDevice, st));
     drp = trp;
     dcol = tcol;
     dval = tval;
@@ -423,9 +435,26 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   int* dflags = (int*)h->sc;
   int init[5] = {0, 0x7fffffff, 0, 1, 1};
   MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
-  validate_rows_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, dcol, dval, h->g, R, S, nnz, dlen,
-                                                                    dflags, dflags + 1, dflags + 2, dflags + 3,
-                                                                    dflags + 4);
+  {
+    const int vb = grid_for(R, 256, h->sm_count);
+    switch (val_type) {
+      case MDP_F32:
+        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const float*)dval, h->g, R, S, nnz, dlen, dflags,
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+        break;
+      case MDP_F16:
+        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __half*)dval, h->g, R, S, nnz, dlen, dflags,
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+        break;
+      case MDP_BF16:
+        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __nv_bfloat16*)dval, h->g, R, S, nnz, dlen,
+                                                 dflags, dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+        break;
+      default:
+        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const double*)dval, h->g, R, S, nnz, dlen, dflags,
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+    }
+  }
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   int res[5];
@@ -450,8 +479,24 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
 
   // stacked matrix in sliced layout
   MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));
-  csr_to_sell_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, dcol, dval, R, h->P.off,
-                                                                  h->P.uniform ? kmax : 0, h->P.val, h->P.col);
+  {
+    const int cb = grid_for(R, 256, h->sm_count);
+    const int uk = h->P.uniform ? kmax : 0;
+    switch (val_type) {
+      case MDP_F32:
+        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const float*)dval, R, h->P.off, uk, h->P.val, h->P.col);
+        break;
+      case MDP_F16:
+        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const __half*)dval, R, h->P.off, uk, h->P.val, h->P.col);
+        break;
+      case MDP_BF16:
+        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const __nv_bfloat16*)dval, R, h->P.off, uk, h->P.val,
+                                               h->P.col);
+        break;
+      default:
+        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const double*)dval, R, h->P.off, uk, h->P.val, h->P.col);
+    }
+  }
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   if (!h->P.uniform)
@@ -542,13 +587,15 @@ const char* mdp_last_error(void) { return g_last_error.c_str(); }
 mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
                       mdp_dtype val_type, const double* g, int32_t inputs_on_device, void* stream,
                       mdp_handle* out) {
+  NvtxRange range("mdp_create");
   if (!out) return fail(MDP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (S < 1 || A < 1 || A > 8192) return fail(MDP_ERR_INVALID_ARG, "need S >= 1 and 1 <= A <= 8192");
   if (S > (int64_t(1) << 31) - 1 || S * (int64_t)A > (int64_t(1) << 36))
     return fail(MDP_ERR_INVALID_ARG, "S must fit int32 and S*A must be below 2^36");
   if (!row_ptr || !col || !val || !g) return fail(MDP_ERR_INVALID_ARG, "null input array");
-  if (val_type != MDP_F64) return fail(MDP_ERR_INVALID_ARG, "val_type must be MDP_F64");
+  if (val_type != MDP_F64 && val_type != MDP_F32 && val_type != MDP_F16 && val_type != MDP_BF16)
+    return fail(MDP_ERR_INVALID_ARG, "val_type must be MDP_F64, MDP_F32, MDP_F16 or MDP_BF16");
   mdp_s* h = new mdp_s();
   mdp_status st = create_impl(S, A, row_ptr, col, val, val_type, g, inputs_on_device, (cudaStream_t)stream, h);
   if (st != MDP_OK) {

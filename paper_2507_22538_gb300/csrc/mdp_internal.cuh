@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -26,6 +27,16 @@ constexpr int kScalarSlots = 512;
 void set_error(const std::string& msg);
 mdp_status fail(mdp_status st, const std::string& msg);
 mdp_status cuda_fail(cudaError_t e, const char* what);
+
+// An NVTX range over a scope: the library's calls and the phases of Algorithm 1
+// show up by name in Nsight Systems and can select kernels in Nsight Compute
+// (--nvtx --nvtx-include).  Without an attached tool a range costs a branch.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define MDP_TRY(x)                 \
   do {                             \

@@ -10,6 +10,7 @@ using namespace mdp;
 extern "C" {
 mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
                                   double* residual_inf, void* stream) {
+  NvtxRange range("mdp_bellman");
   if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
   if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
   if (!V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
@@ -42,6 +43,7 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
 mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const double* v0, double* v,
                            mdp_inner inner, int32_t restart, double omega, double abs_tol_2norm, int32_t max_it,
                            int32_t* iters, double* res_2norm, void* stream) {
+  NvtxRange range("mdp_policy_eval");
   if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
   if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
   if (!pi || !v0 || !v) return fail(MDP_ERR_INVALID_ARG, "null vector");
@@ -68,6 +70,7 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
 }
 
 mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_per_sweep, void* stream) {
+  NvtxRange range("mdp_tune");
   if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
   if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
   cudaStream_t st = (cudaStream_t)stream;
@@ -116,6 +119,7 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
 mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* stats,
                      void* stream) {
   const auto t0 = std::chrono::steady_clock::now();
+  NvtxRange range("mdp_solve");
   if (!h || !o) return fail(MDP_ERR_INVALID_ARG, "null handle or options");
   if (!V || !pi) return fail(MDP_ERR_INVALID_ARG, "null vector");
   if (!(o->gamma > 0.0 && o->gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
@@ -148,6 +152,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   int k = 0;
   if (o->graph && o->inner == MDP_GMRES && !o->record_timing) {
     // the whole loop below as one CUDA graph launch (graph.cu)
+    NvtxRange graph_range("graph launch (Algorithm 1)");
     status = graph_solve(h, o, V, pi, &local, st);
     if (status != MDP_OK && status != MDP_NOT_CONVERGED && status != MDP_ERR_NUMERIC) return status;
     k = local.outer_iters;
@@ -156,6 +161,8 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   struct TimingOff { mdp_s* h; ~TimingOff() { h->timing = 0; } } timing_off{h};
   for (;;) {
     // Algorithm 1 steps 2-3: TV, pi_{k+1} and ||r(V_k)||_inf in one sweep
+    nvtxRangePushA("Bellman sweep and stop test");
+    struct PopSweep { bool on = true; void pop() { if (on) nvtxRangePop(); on = false; } ~PopSweep() { pop(); } } sweep_range;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev0, st));
     mdp_status s = launch_bellman(h, o->gamma, V, h->TV, pi, st);
     if (s != MDP_OK) return s;
@@ -183,7 +190,9 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
       status = fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
       break;
     }
+    sweep_range.pop();
     // step 4: the policy's rows P_pi and costs g_pi, gathered into the per-state layout
+    NvtxRange eval_range("policy evaluation");
     s = extract_policy(h, pi, mixed, st);
     if (s != MDP_OK) {
       status = s;

@@ -26,7 +26,7 @@ MDP_ERR_NUMERIC = 6
 STATUS_NAMES = {0: "MDP_OK", 1: "MDP_ERR_INVALID_ARG", 2: "MDP_ERR_NOT_STOCHASTIC", 3: "MDP_ERR_OOM",
                 4: "MDP_ERR_CUDA", 5: "MDP_NOT_CONVERGED", 6: "MDP_ERR_NUMERIC"}
 
-MDP_F64 = 0
+MDP_F64, MDP_F32, MDP_F16, MDP_BF16 = 0, 1, 2, 3  # mdp_dtype: storage type of the P values
 MDP_GMRES = 0
 MDP_RICHARDSON = 1
 MDP_TFQMR = 2
@@ -147,10 +147,20 @@ def mdp_last_error() -> str:
     return load().mdp_last_error().decode()
 
 
-def mdp_create(S, A, row_ptr, col, val, g, inputs_on_device: bool, stream=None):
-    """Returns (status, handle)."""
+def value_dtype(val) -> int:
+    """The mdp_dtype of a numpy array or torch tensor of P values."""
+    name = str(getattr(val, "dtype", "float64")).replace("torch.", "")
+    codes = {"float64": MDP_F64, "float32": MDP_F32, "float16": MDP_F16, "bfloat16": MDP_BF16}
+    if name not in codes:
+        raise TypeError(f"P values of dtype {name}: expected float64, float32, float16 or bfloat16")
+    return codes[name]
+
+
+def mdp_create(S, A, row_ptr, col, val, g, inputs_on_device: bool, stream=None, val_type=None):
+    """Returns (status, handle).  val_type defaults to the dtype of val."""
     h = _P()
-    st = load().mdp_create(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), MDP_F64, _ptr(g),
+    vt = value_dtype(val) if val_type is None else int(val_type)
+    st = load().mdp_create(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), vt, _ptr(g),
                            1 if inputs_on_device else 0, _stream(stream), ctypes.byref(h))
     return st, h
 
