@@ -313,6 +313,56 @@ def run_serving(n, slots=4, seed=5):
             "mismatches": mism[:8], "n_mismatches": len(mism)}
 
 
+def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01):
+    """The full serving stream: n requests of the counter-based mix (S log-uniform in
+    [1e3, 1e6], A in [2, 32], k in [4, 64], gamma in {0.9, 0.99, 0.999, 0.9999}, drawn
+    on the device at admission) under Poisson arrivals at 0.8 of the one-at-a-time
+    rate measured on the first `calib` requests, admitted by a 120 GB budget into
+    `slots` concurrent solves.  Results of the calibration requests and of a seeded
+    sample of verify_frac of the rest are compared bit for bit with the same
+    request solved alone."""
+    import numpy as np
+
+    from mdpgen.cuda_gen import load as load_gen
+    from paper_2507_22538_gb300.serve import Request, SolveService, latency_summary, solve_alone
+    load_gen()
+    reqs = [Request(i, DeviceRequest(i, seed, **SERVE_MIX), tol=1e-8, alpha=1e-3) for i in range(n)]
+    for r in reqs[:3]:
+        solve_alone(r)  # warm-up
+    alone = {r.rid: solve_alone(r) for r in reqs[:calib]}
+    service = np.array([a.finished for a in alone.values()])
+    rate = 0.8 / float(service.mean())
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    rng = np.random.default_rng(seed + 1)
+    sample = [int(i) for i in rng.choice(np.arange(calib, n), size=max(1, int(verify_frac * (n - calib))),
+                                         replace=False)] if n > calib else []
+    checked = set(alone) | set(sample)
+    svc = SolveService(slots=slots, hbm_budget=120 << 30, keep=lambda rid: rid in checked).start()
+    t0 = svc.now()
+    for r, a in zip(reqs, arrivals):
+        wait = t0 + a - svc.now()
+        if wait > 0:
+            time.sleep(wait)
+        svc.submit(r)
+    out = svc.wait(n, timeout=4 * 3600)
+    svc.close()
+    summ = latency_summary(out)
+    for i in sample:
+        alone[i] = solve_alone(reqs[i])
+    mism = [rid for rid, a in alone.items()
+            if not (a.status == out[rid].status and np.array_equal(a.V, out[rid].V) and np.array_equal(a.pi, out[rid].pi))]
+    statuses = {int(k): int(v) for k, v in zip(*np.unique([r.status for r in out.values()], return_counts=True))}
+    nnz = np.array([r.data.nnz for r in reqs], dtype=np.float64)
+    return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
+            "mix": "S log-uniform 1e3..1e6, A 2..32, k 4..64, gamma in {0.9,0.99,0.999,0.9999}, Dirichlet(1), "
+                   "GMRES(30), alpha 1e-3, tol 1e-8; drawn on the device at admission (counted in the latency)",
+            "entries_per_request": {"mean": float(nnz.mean()), "max": float(nnz.max())},
+            "calibration": {"requests": calib, "mean_solve_alone_s": float(service.mean())},
+            "continuous": summ, "oom_retries": svc.oom_retries, "peak_in_flight": svc.peak_in_flight,
+            "statuses": statuses, "verified_alone": len(alone), "mismatches": mism[:8], "n_mismatches": len(mism)}
+
+
 def run_small(steps=20):
     """The small random workload (S = 1000, A = 4, 8 entries per row, Dirichlet(1),
     gamma = 0.9, GMRES(30), alpha = 1e-3, tol = 1e-10): time to solution of the
@@ -624,9 +674,17 @@ def main():
                          "of the workload (a one-action MDP; no bench line)")
     ap.add_argument("--solve-only", choices=["f64", "mixed"], default=None,
                     help="profiling aid: W + K solves of the workload at this precision (no bench line)")
+    ap.add_argument("--serve-stream", type=int, default=0, metavar="N",
+                    help="only the full serving stream of N requests (no bench line)")
     ap.add_argument("--small-only", action="store_true",
                     help="only the small-workload stream vs graph measurement (no bench line)")
     args = ap.parse_args()
+    if args.serve_stream:
+        import torch
+        from paper_2507_22538_gb300.build import build
+        build()
+        print(json.dumps({"mode": "serve_stream", **run_serving_stream(args.serve_stream)}), flush=True)
+        return 0
     if args.small_only:
         import torch
         from paper_2507_22538_gb300.build import build
@@ -778,9 +836,36 @@ def main():
                            "inner": its[-1][1], "policy_value_bytes": its[-1][2],
                            "max_final_residual": max(i[3] for i in its)}
         quant["speedup_mixed_vs_f64"] = quant["f64"]["ms_per_step"] / quant["mixed"]["ms_per_step"]
+        Mq.close()
+        # end to end from pinned host buffers with the values in binary16 (exact for this MDP)
+        # against the same values in binary64: create + mixed solve + read back
+        qe = {}
+        for tag, vals in (("binary16_values", torch.from_numpy(mq.val).to(torch.float16)),
+                          ("binary64_values", torch.from_numpy(mq.val))):
+            host = [torch.from_numpy(mq.row_ptr).pin_memory(), torch.from_numpy(mq.col).pin_memory(),
+                    vals.pin_memory(), torch.from_numpy(mq.g).pin_memory()]
+            times = []
+            for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, hq = mdp.mdp_create(S, A, *host, False, stream)
+                mdp.check(st, "mdp_create")
+                V.zero_()
+                st, _ = mdp.mdp_solve(hq, mopts, V, pi, stream)
+                mdp.check(st, "mdp_solve")
+                Vh_q = V.to("cpu", non_blocking=True)
+                pih_q = pi.to("cpu", non_blocking=True)
+                torch.cuda.synchronize()
+                mdp.mdp_destroy(hq)
+                if i:
+                    times.append(time.perf_counter() - t0)
+            if times:
+                qe[tag] = {"s": sum(times) / len(times),
+                           "h2d_bytes": int(sum(t.numel() * t.element_size() for t in host))}
+            del host
+        quant["e2e_mixed_solve"] = qe
         quant["what"] = ("banded workload with the band's probabilities rounded to multiples of 2^-11 "
                          "(exact in binary16); the mixed path reads binary16 policy rows")
-        Mq.close()
         del mq
         M = None
 
@@ -793,13 +878,18 @@ def main():
     if M is not None:
         M.close()
     torch.cuda.synchronize()
+    # the call a user makes: the graph-driven solve, without per-sweep event timing
+    eopts = mdp.mdp_default_opts()
+    for f, _ in mdp.mdp_solve_opts._fields_:
+        setattr(eopts, f, getattr(opts, f))
+    eopts.record_timing, eopts.graph = 0, 1
     e2e_times = []
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         t0 = time.perf_counter()
         st, h = mdp.mdp_create(S, A, pinned["row_ptr"], pinned["col"], pinned["val"], pinned["g"], False, stream)
         mdp.check(st, "mdp_create")
         V.zero_()
-        st, _ = mdp.mdp_solve(h, opts, V, pi, stream)
+        st, _ = mdp.mdp_solve(h, eopts, V, pi, stream)
         mdp.check(st, "mdp_solve")
         Vh.copy_(V, non_blocking=True)
         pih.copy_(pi, non_blocking=True)
@@ -855,7 +945,9 @@ def main():
             "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
                            "inner_per_step": totals["inner_iters_total"] / args.steps,
                            "max_final_residual": totals["final_residual"]},
-            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "what": "mdp_create from pinned host CSR (binary64 values) + graph-driven mdp_solve + read back "
+                            "of V and pi"},
             "graph_solve": graph_cmp,
             "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}

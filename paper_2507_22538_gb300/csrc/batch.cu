@@ -136,14 +136,14 @@ template <int NB>
 __global__ void __launch_bounds__(kVecThreads) bb_dots_kernel(const BatchProblem* __restrict__ P,
                                                                const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
-  gm_dots_body<NB, double>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
+  gm_dots_body<NB, double, true>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
 }
 
 template <int NB>
 __global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) bb_project_kernel(const BatchProblem* __restrict__ P,
                                                                   const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
-  gm_project_body<NB, kPlain, double>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
+  gm_project_body<NB, kPlain, double, true>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
 }
 
 __global__ void __launch_bounds__(kVecThreads) bb_update_kernel(const BatchProblem* __restrict__ P,

@@ -70,18 +70,18 @@ __global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const TP* __rest
   gm_matvec_body<U, TP, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w, K);
 }
 
-template <int NB, typename T>
+template <int NB, typename T, bool FINE>
 __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T* __restrict__ basis, int j,
                                                                const T* __restrict__ w, double* partials,
                                                                KrylovState* K) {
-  gm_dots_body<NB, T>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
+  gm_dots_body<NB, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
-template <int NB, int MODE, typename T>
+template <int NB, int MODE, typename T, bool FINE>
 __global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
                                                                   const T* __restrict__ w, double* partials,
                                                                   KrylovState* K) {
-  gm_project_body<NB, MODE, T>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
+  gm_project_body<NB, MODE, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
 template <typename T>
@@ -465,11 +465,9 @@ static mdp_status launch_matvec(mdp_s* h, const KrylovBuffers<T>& B, double gamm
   return MDP_OK;
 }
 
-template <bool U, int NB, typename T>
+template <bool U, int NB, bool FINE, typename T>
 static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, int refine,
                                cudaStream_t st) {
-  const Sell& Q = h->Ppi;
-  const int k = U ? Q.kmax : 0;
   const int64_t S = h->S;
   KrylovState* K = kstate(h);
   const bool timed = h->timing && (j % kMatvecTimingStride) == 0;
@@ -477,20 +475,22 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
   if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
-  gm_dots_kernel<NB, T><<<MDP_WAVE((gm_dots_kernel<NB, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+  gm_dots_kernel<NB, T, FINE><<<MDP_WAVE((gm_dots_kernel<NB, T, FINE>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w,
+                                                                                              h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
-    gm_project_kernel<NB, kPlain, T><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
+        S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   }
-  if constexpr (NB == 8 || NB == 16 || NB == 32) {  // re-orthogonalised steps use the coarse widths only
+  if constexpr (!FINE && (NB == 8 || NB == 16 || NB == 32)) {  // re-orthogonalised steps use the coarse widths only
     if (refine == MDP_REFINE_IFNEEDED)
-      gm_project_kernel<NB, kDgks, T><<<MDP_WAVE((gm_project_kernel<NB, kDgks, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+      gm_project_kernel<NB, kDgks, T, false><<<MDP_WAVE((gm_project_kernel<NB, kDgks, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
     else
-      gm_project_kernel<NB, kAlways, T><<<MDP_WAVE((gm_project_kernel<NB, kAlways, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+      gm_project_kernel<NB, kAlways, T, false><<<MDP_WAVE((gm_project_kernel<NB, kAlways, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
-    gm_project_kernel<NB, kSecond, T><<<MDP_WAVE((gm_project_kernel<NB, kSecond, T>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    gm_project_kernel<NB, kSecond, T, false><<<MDP_WAVE((gm_project_kernel<NB, kSecond, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   } else {
@@ -516,6 +516,8 @@ static int matvec_grid(mdp_s* h, bool U) {
 
 template <typename T>
 static int pass_grid(mdp_s* h, GmresPass pass, int NB) {
+  // the FP64 passes the batched solver mirrors run at the fine widths (exact tails)
+  constexpr bool FINE_T = sizeof(T) == sizeof(double);
   const bool U = h->Ppi.uniform;
   switch (pass) {
     case kPassResidual:
@@ -526,25 +528,25 @@ static int pass_grid(mdp_s* h, GmresPass pass, int NB) {
       return MDP_WAVE(gm_update_kernel<T>);
     case kPassDots:
       switch (NB) {
-        case 4: return MDP_WAVE((gm_dots_kernel<4, T>));
-        case 8: return MDP_WAVE((gm_dots_kernel<8, T>));
-        case 12: return MDP_WAVE((gm_dots_kernel<12, T>));
-        case 16: return MDP_WAVE((gm_dots_kernel<16, T>));
-        case 20: return MDP_WAVE((gm_dots_kernel<20, T>));
-        case 24: return MDP_WAVE((gm_dots_kernel<24, T>));
-        case 28: return MDP_WAVE((gm_dots_kernel<28, T>));
-        default: return MDP_WAVE((gm_dots_kernel<32, T>));
+        case 4: return MDP_WAVE((gm_dots_kernel<4, T, FINE_T>));
+        case 8: return MDP_WAVE((gm_dots_kernel<8, T, FINE_T>));
+        case 12: return MDP_WAVE((gm_dots_kernel<12, T, FINE_T>));
+        case 16: return MDP_WAVE((gm_dots_kernel<16, T, FINE_T>));
+        case 20: return MDP_WAVE((gm_dots_kernel<20, T, FINE_T>));
+        case 24: return MDP_WAVE((gm_dots_kernel<24, T, FINE_T>));
+        case 28: return MDP_WAVE((gm_dots_kernel<28, T, FINE_T>));
+        default: return MDP_WAVE((gm_dots_kernel<32, T, FINE_T>));
       }
     case kPassProject:
       switch (NB) {
-        case 4: return MDP_WAVE((gm_project_kernel<4, kPlain, T>));
-        case 8: return MDP_WAVE((gm_project_kernel<8, kPlain, T>));
-        case 12: return MDP_WAVE((gm_project_kernel<12, kPlain, T>));
-        case 16: return MDP_WAVE((gm_project_kernel<16, kPlain, T>));
-        case 20: return MDP_WAVE((gm_project_kernel<20, kPlain, T>));
-        case 24: return MDP_WAVE((gm_project_kernel<24, kPlain, T>));
-        case 28: return MDP_WAVE((gm_project_kernel<28, kPlain, T>));
-        default: return MDP_WAVE((gm_project_kernel<32, kPlain, T>));
+        case 4: return MDP_WAVE((gm_project_kernel<4, kPlain, T, FINE_T>));
+        case 8: return MDP_WAVE((gm_project_kernel<8, kPlain, T, FINE_T>));
+        case 12: return MDP_WAVE((gm_project_kernel<12, kPlain, T, FINE_T>));
+        case 16: return MDP_WAVE((gm_project_kernel<16, kPlain, T, FINE_T>));
+        case 20: return MDP_WAVE((gm_project_kernel<20, kPlain, T, FINE_T>));
+        case 24: return MDP_WAVE((gm_project_kernel<24, kPlain, T, FINE_T>));
+        case 28: return MDP_WAVE((gm_project_kernel<28, kPlain, T, FINE_T>));
+        default: return MDP_WAVE((gm_project_kernel<32, kPlain, T, FINE_T>));
       }
   }
   return 1;
@@ -563,20 +565,23 @@ template <bool U, typename T>
 static mdp_status arnoldi_dispatch(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, int refine,
                                    cudaStream_t st) {
   if (refine != MDP_REFINE_NEVER || sizeof(T) != sizeof(double)) {
-    if (j + 1 <= 8) return arnoldi_step<U, 8>(h, B, gamma, j, refine, st);
-    if (j + 1 <= 16) return arnoldi_step<U, 16>(h, B, gamma, j, refine, st);
-    return arnoldi_step<U, 32>(h, B, gamma, j, refine, st);
+    if (j + 1 <= 8) return arnoldi_step<U, 8, false>(h, B, gamma, j, refine, st);
+    if (j + 1 <= 16) return arnoldi_step<U, 16, false>(h, B, gamma, j, refine, st);
+    return arnoldi_step<U, 32, false>(h, B, gamma, j, refine, st);
   }
-  switch ((j + 4) / 4) {
-    case 1: return arnoldi_step<U, 4>(h, B, gamma, j, refine, st);
-    case 2: return arnoldi_step<U, 8>(h, B, gamma, j, refine, st);
-    case 3: return arnoldi_step<U, 12>(h, B, gamma, j, refine, st);
-    case 4: return arnoldi_step<U, 16>(h, B, gamma, j, refine, st);
-    case 5: return arnoldi_step<U, 20>(h, B, gamma, j, refine, st);
-    case 6: return arnoldi_step<U, 24>(h, B, gamma, j, refine, st);
-    case 7: return arnoldi_step<U, 28>(h, B, gamma, j, refine, st);
-    default: return arnoldi_step<U, 32>(h, B, gamma, j, refine, st);
+  if constexpr (sizeof(T) == sizeof(double)) {
+    switch ((j + 4) / 4) {  // j + 1 in (NB - 4, NB]: the exact-tail (FINE) passes
+      case 1: return arnoldi_step<U, 4, true>(h, B, gamma, j, refine, st);
+      case 2: return arnoldi_step<U, 8, true>(h, B, gamma, j, refine, st);
+      case 3: return arnoldi_step<U, 12, true>(h, B, gamma, j, refine, st);
+      case 4: return arnoldi_step<U, 16, true>(h, B, gamma, j, refine, st);
+      case 5: return arnoldi_step<U, 20, true>(h, B, gamma, j, refine, st);
+      case 6: return arnoldi_step<U, 24, true>(h, B, gamma, j, refine, st);
+      case 7: return arnoldi_step<U, 28, true>(h, B, gamma, j, refine, st);
+      default: return arnoldi_step<U, 32, true>(h, B, gamma, j, refine, st);
+    }
   }
+  return fail(MDP_ERR_INVALID_ARG, "internal: fine Gram-Schmidt widths are FP64 only");
 }
 
 // FP64 residual of the policy system (the refinement residual in the mixed

@@ -303,12 +303,28 @@ __device__ __forceinline__ void gm_matvec_body(int bid, int nb, const TP* __rest
 // NB accumulators.
 __host__ __device__ constexpr int pow2_up(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
+// The dots of exactly NA basis vectors with w over this block's states.
+template <int NA, int NP, typename T>
+__device__ __forceinline__ void dots_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
+                                          const T* __restrict__ w, T (&d)[NP]) {
+  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+    const T ws = w[s];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
+  }
+}
+
 // Arnoldi step, part 2: raw dots u_i . w (i <= j) and ||w||^2; the last block
 // turns them into the Hessenberg column h_i = v_i . w and the projection
 // coefficients.  NB (>= j + 1) is the number of unrolled accumulators: the
-// slots above j are predicated off but still issue, so the caller picks the
-// smallest multiple of 4 that holds the step.
-template <int NB, typename T>
+// slots above j are predicated off but still issue.  FINE (the FP64 steps
+// without re-orthogonalisation): NB is the smallest multiple of 4 that holds
+// j + 1, and a uniform switch runs exactly j + 1 products per state, without
+// ||w|| (read only by the re-orthogonalising modes).  Per thread each dot is the
+// same chain of FMAs either way; the grid follows the kernel's occupancy, so the
+// states a thread sums (and the last bits of the sums) depend on the variant, and
+// the batched solver launches the same variant with the same grid.
+template <int NB, typename T, bool FINE = false>
 __device__ __forceinline__ void gm_dots_body(int bid, int nb, int64_t S, const T* __restrict__ basis, int j,
                                                                const T* __restrict__ w, double* partials,
                                                                KrylovState* K) {
@@ -318,21 +334,40 @@ __device__ __forceinline__ void gm_dots_body(int bid, int nb, int64_t S, const T
   T ww = T(0);
 #pragma unroll
   for (int i = 0; i < NP; ++i) d[i] = T(0);
-  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
-    const T ws = w[s];
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
-    ww = fma(ws, ws, ww);
-  }
-  __shared__ double out[NP + 1];  // warp sums in T, block and grid sums in double
-  if (grid_sum_at<NP, true>(d, (double)ww, partials, K->pstride, K->gcount, out, bid, nb) && threadIdx.x == 0) {
-    for (int i = 0; i <= j; ++i) {
-      const double h = K->sigma[i] * out[i];
-      K->hc[i] = h;
-      K->coef[i] = h * K->sigma[i];
+  if constexpr (FINE) {
+    static_assert(NB % 4 == 0, "fine widths are multiples of 4");
+    switch (j + 1 - (NB - 4)) {  // 1..4: the caller picks NB from j
+      case 1: dots_rows<NB - 3>(bid, nb, S, basis, w, d); break;
+      case 2: dots_rows<NB - 2>(bid, nb, S, basis, w, d); break;
+      case 3: dots_rows<NB - 1>(bid, nb, S, basis, w, d); break;
+      default: dots_rows<NB>(bid, nb, S, basis, w, d); break;
     }
-    K->wnorm = sqrt(out[NP]);
+    __shared__ double fout[NP];
+    if (grid_sum_at<NP, false>(d, 0.0, partials, K->pstride, K->gcount, fout, bid, nb) && threadIdx.x == 0) {
+      for (int i = 0; i <= j; ++i) {
+        const double h = K->sigma[i] * fout[i];
+        K->hc[i] = h;
+        K->coef[i] = h * K->sigma[i];
+      }
+      K->wnorm = 0.0;
+    }
+  } else {
+    for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+      const T ws = w[s];
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
+      ww = fma(ws, ws, ww);
+    }
+    __shared__ double out[NP + 1];  // warp sums in T, block and grid sums in double
+    if (grid_sum_at<NP, true>(d, (double)ww, partials, K->pstride, K->gcount, out, bid, nb) && threadIdx.x == 0) {
+      for (int i = 0; i <= j; ++i) {
+        const double h = K->sigma[i] * out[i];
+        K->hc[i] = h;
+        K->coef[i] = h * K->sigma[i];
+      }
+      K->wnorm = sqrt(out[NP]);
+    }
   }
 }
 
@@ -350,12 +385,29 @@ enum { kPlain = 0, kDgks = 1, kAlways = 2, kSecond = 3 };
 // faster on the whole FP64 solve.
 constexpr int kProjectMinBlocks = 4;
 
-template <int NB, int MODE, typename T>
+// u = src - sum of exactly NA coefficient-scaled basis vectors over this block's
+// states; returns this thread's share of ||u||^2.
+template <int NA, typename T>
+__device__ __forceinline__ T project_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
+                                          const T* __restrict__ src, T* __restrict__ u, const T* c) {
+  T uu = T(0);
+  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+    T x = src[s];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) x = fma(-c[i], basis[(int64_t)i * S + s], x);
+    u[s] = x;
+    uu = fma(x, x, uu);
+  }
+  return uu;
+}
+
+template <int NB, int MODE, typename T, bool FINE = false>
 __device__ __forceinline__ void gm_project_body(int bid, int nb, int64_t S, T* __restrict__ basis, int j,
                                                                   const T* __restrict__ w, double* partials,
                                                                   KrylovState* K) {
   constexpr bool SECOND = (MODE == kSecond);
   constexpr bool DOTS = (MODE == kDgks || MODE == kAlways);
+  static_assert(!FINE || MODE == kPlain, "fine widths are for the single-pass projection");
   if (K->flags & (kCycleStop | kSolveDone)) return;
   if (SECOND && !(K->flags & kReorth)) return;
   __shared__ T c[NB];
@@ -363,47 +415,65 @@ __device__ __forceinline__ void gm_project_body(int bid, int nb, int64_t S, T* _
   __syncthreads();
   T* u = basis + (int64_t)(j + 1) * S;
   const T* src = SECOND ? u : w;
-  constexpr int NV = DOTS ? pow2_up(NB) : 1;  // dots u_i . u_{j+1} (first pass with dots); ||u||^2 goes last
-  T d[NV];
-  T uu = T(0);
-#pragma unroll
-  for (int i = 0; i < NV; ++i) d[i] = T(0);
-  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
-    T x = src[s];
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i <= j) x = fma(-c[i], basis[(int64_t)i * S + s], x);
-    u[s] = x;
-    uu = fma(x, x, uu);
-    if (DOTS) {
-#pragma unroll
-      for (int i = 0; i < NB; ++i)
-        if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], x, d[i]);
+  if constexpr (FINE) {
+    // as gm_dots_body: exactly j + 1 terms per state, in the order of the predicated loop
+    T uu = T(0);
+    switch (j + 1 - (NB - 4)) {
+      case 1: uu = project_rows<NB - 3>(bid, nb, S, basis, src, u, c); break;
+      case 2: uu = project_rows<NB - 2>(bid, nb, S, basis, src, u, c); break;
+      case 3: uu = project_rows<NB - 1>(bid, nb, S, basis, src, u, c); break;
+      default: uu = project_rows<NB>(bid, nb, S, basis, src, u, c); break;
     }
-  }
-  __shared__ double out[NV + 1];
-  bool last;
-  if (DOTS) {
-    last = grid_sum_at<NV, true>(d, (double)uu, partials, K->pstride, K->gcount, out, bid, nb);
-  } else {
     T n1[1] = {uu};
-    last = grid_sum_at<1, false>(n1, 0.0, partials, K->pstride, K->gcount, out, bid, nb);
-  }
-  if (last && threadIdx.x == 0) {
-    const double beta = sqrt(out[DOTS ? NV : 0]);
-    K->beta = beta;
-    const bool again = (MODE == kAlways && beta > 0.0) ||
-                       (MODE == kDgks && beta > 0.0 && beta < 0.70710678118654752 * K->wnorm);
-    if (again) {
-      for (int i = 0; i <= j; ++i) {
-        const double h2 = K->sigma[i] * out[i];
-        K->hc[i] += h2;
-        K->coef[i] = h2 * K->sigma[i];
-      }
-      K->flags |= kReorth;
-    } else {
+    __shared__ double fout[1];
+    if (grid_sum_at<1, false>(n1, 0.0, partials, K->pstride, K->gcount, fout, bid, nb) && threadIdx.x == 0) {
+      K->beta = sqrt(fout[0]);
       K->flags &= ~kReorth;
       finish_step(K, j);
+    }
+  } else {
+    constexpr int NV = DOTS ? pow2_up(NB) : 1;  // dots u_i . u_{j+1} (first pass with dots); ||u||^2 goes last
+    T d[NV];
+    T uu = T(0);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) d[i] = T(0);
+    for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+      T x = src[s];
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (i <= j) x = fma(-c[i], basis[(int64_t)i * S + s], x);
+      u[s] = x;
+      uu = fma(x, x, uu);
+      if (DOTS) {
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+          if (i <= j) d[i] = fma(basis[(int64_t)i * S + s], x, d[i]);
+      }
+    }
+    __shared__ double out[NV + 1];
+    bool last;
+    if (DOTS) {
+      last = grid_sum_at<NV, true>(d, (double)uu, partials, K->pstride, K->gcount, out, bid, nb);
+    } else {
+      T n1[1] = {uu};
+      last = grid_sum_at<1, false>(n1, 0.0, partials, K->pstride, K->gcount, out, bid, nb);
+    }
+    if (last && threadIdx.x == 0) {
+      const double beta = sqrt(out[DOTS ? NV : 0]);
+      K->beta = beta;
+      const bool again = (MODE == kAlways && beta > 0.0) ||
+                         (MODE == kDgks && beta > 0.0 && beta < 0.70710678118654752 * K->wnorm);
+      if (again) {
+        for (int i = 0; i <= j; ++i) {
+          const double h2 = K->sigma[i] * out[i];
+          K->hc[i] += h2;
+          K->coef[i] = h2 * K->sigma[i];
+        }
+        K->flags |= kReorth;
+      } else {
+        K->flags &= ~kReorth;
+        finish_step(K, j);
+      }
     }
   }
 }

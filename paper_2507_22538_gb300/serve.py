@@ -92,10 +92,15 @@ def _create(d, stream):
 class SolveService:
     """A fixed pool of worker slots with an HBM admission budget."""
 
-    def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0, batch_max: int = 1):
+    def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0, batch_max: int = 1,
+                 keep=None):
+        """keep: optional predicate on a request id; results of other requests drop V and
+        the policy (status, iteration counts and latency stay), to bound host memory on
+        long streams."""
         import torch
         self.slots = slots
         self.batch_max = max(1, int(batch_max))
+        self.keep = keep
         self.budget = int(hbm_budget)
         self.device = device
         self._free = self.budget
@@ -231,6 +236,8 @@ class SolveService:
                 for res in outs:
                     res.admitted = admitted
                     res.finished = done
+                    if self.keep is not None and not self.keep(res.rid):
+                        res.V, res.pi = np.empty(0), np.empty(0, dtype=np.int32)
                     self._results[res.rid] = res
                 self.batches.append(len(batch))
                 self._cv.notify_all()
