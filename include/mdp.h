@@ -182,7 +182,8 @@ mdp_status mdp_policy_apply(mdp_handle h, double gamma, const int32_t* pi, const
  *
  *  pi            int32[S] policy, 0 <= pi[s] < A.
  *  v0, v         double[S] start vector and result (may alias).
- *  inner         MDP_GMRES (restart = `restart`) or MDP_RICHARDSON (step scale `omega`).
+ *  inner         an mdp_inner value: MDP_GMRES (restart = `restart`), MDP_RICHARDSON or
+ *                MDP_RICHARDSON_JACOBI (step scale `omega`), MDP_TFQMR.
  *  abs_tol_2norm stop when ||g_pi - J_pi v||_2 < abs_tol_2norm (Sec. III-B.3).
  *  max_it        at most this many iterations (a GMRES Arnoldi step or a Richardson step);
  *                GMRES uses classical Gram-Schmidt without refinement (MDP_REFINE_NEVER).
@@ -204,7 +205,9 @@ mdp_status mdp_policy_eval(mdp_handle h, double gamma, const int32_t* pi, const 
  *  pi     int32[S]: out the greedy policy of the returned V (ties: lowest action).
  *  stats  host struct (may be NULL).
  * Blocks until done.  MDP_NOT_CONVERGED when max_iter_pi evaluations did not
- * reach atol_pi (V, pi and stats are still filled).
+ * reach atol_pi (V, pi and stats are still filled).  With opts->graph set (GMRES,
+ * record_timing off) the loop runs as one CUDA graph launch decided on the device,
+ * with the same results bit for bit.
  */
 mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_t* pi,
                      mdp_solve_stats* stats, void* stream);

@@ -70,7 +70,7 @@ struct BatchReport {
 // blocks and the binary32 passes (suffix F) give FP64 problems none.
 enum : int { kRangeBellman = 0, kRangeExtract, kRangeResidual, kRangeMatvec, kRangeUpdate, kRangeDots0,
              kRangeProject0 = kRangeDots0 + 8, kRangeResidualF = kRangeProject0 + 8, kRangeMatvecF, kRangeUpdateF,
-             kRangeDotsF0, kRangeProjectF0 = kRangeDotsF0 + 3, kRanges = kRangeProjectF0 + 3 };
+             kRangeDotsF0, kRangeProjectF0 = kRangeDotsF0 + 8, kRanges = kRangeProjectF0 + 8 };
 
 // Largest i with start[i] <= b: the problem whose range holds block b (problems
 // with an empty range share their start with the next one and are skipped).
@@ -195,14 +195,14 @@ template <int NB>
 __global__ void __launch_bounds__(kVecThreads) bb_dots_f_kernel(const BatchProblem* __restrict__ P,
                                                                  const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
-  gm_dots_body<NB, float>(bid, nb, p.S, p.basis32, j, p.w32, p.partials, p.K);
+  gm_dots_body<NB, float, true>(bid, nb, p.S, p.basis32, j, p.w32, p.partials, p.K);
 }
 
 template <int NB>
 __global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) bb_project_f_kernel(const BatchProblem* __restrict__ P,
                                                                     const int32_t* __restrict__ start, int n, int j) {
   BATCH_PROLOGUE
-  gm_project_body<NB, kPlain, float>(bid, nb, p.S, p.basis32, j, p.w32, p.partials, p.K);
+  gm_project_body<NB, kPlain, float, true>(bid, nb, p.S, p.basis32, j, p.w32, p.partials, p.K);
 }
 
 __global__ void __launch_bounds__(kVecThreads) bb_update_f_kernel(const BatchProblem* __restrict__ P,
@@ -289,8 +289,7 @@ struct Item {
   mdp_solve_stats stats{};
 };
 
-constexpr int kNB[8] = {4, 8, 12, 16, 20, 24, 28, 32};  // FP64 Gram-Schmidt widths
-constexpr int kNBF[3] = {8, 16, 32};                      // binary32 Gram-Schmidt widths
+constexpr int kNB[8] = {4, 8, 12, 16, 20, 24, 28, 32};  // Gram-Schmidt widths (FP64 and binary32)
 
 // Device and pinned buffers of one batched call.
 struct BatchBuffers {
@@ -374,8 +373,8 @@ int blocks_for(const Item& it, int kind) {
   }
   if (kind < kRangeProject0) return gmres_grid(h, kPassDots, kNB[kind - kRangeDots0], false);
   if (kind < kRangeResidualF) return gmres_grid(h, kPassProject, kNB[kind - kRangeProject0], false);
-  if (kind < kRangeProjectF0) return gmres_grid(h, kPassDots, kNBF[kind - kRangeDotsF0], true);
-  return gmres_grid(h, kPassProject, kNBF[kind - kRangeProjectF0], true);
+  if (kind < kRangeProjectF0) return gmres_grid(h, kPassDots, kNB[kind - kRangeDotsF0], true);
+  return gmres_grid(h, kPassProject, kNB[kind - kRangeProjectF0], true);
 }
 
 // Upload the descriptors and block ranges of the problems in `act`.
@@ -438,17 +437,17 @@ mdp_status arnoldi_batch(BatchBuffers& B, int na, int j, int64_t& launches) {
     case 7: BB_LAUNCH(bb_dots_kernel<28>, kRangeDots0 + 6, j); BB_LAUNCH(bb_project_kernel<28>, kRangeProject0 + 6, j); break;
     default: BB_LAUNCH(bb_dots_kernel<32>, kRangeDots0 + 7, j); BB_LAUNCH(bb_project_kernel<32>, kRangeProject0 + 7, j); break;
   }
-  // the mixed problems' binary32 step at the coarse widths of the single-problem mixed solver
+  // the mixed problems' binary32 step at the widths of the single-problem mixed solver
   BB_LAUNCH(bb_matvec_f_kernel, kRangeMatvecF, j);
-  if (j + 1 <= 8) {
-    BB_LAUNCH(bb_dots_f_kernel<8>, kRangeDotsF0 + 0, j);
-    BB_LAUNCH(bb_project_f_kernel<8>, kRangeProjectF0 + 0, j);
-  } else if (j + 1 <= 16) {
-    BB_LAUNCH(bb_dots_f_kernel<16>, kRangeDotsF0 + 1, j);
-    BB_LAUNCH(bb_project_f_kernel<16>, kRangeProjectF0 + 1, j);
-  } else {
-    BB_LAUNCH(bb_dots_f_kernel<32>, kRangeDotsF0 + 2, j);
-    BB_LAUNCH(bb_project_f_kernel<32>, kRangeProjectF0 + 2, j);
+  switch ((j + 4) / 4) {
+    case 1: BB_LAUNCH(bb_dots_f_kernel<4>, kRangeDotsF0 + 0, j); BB_LAUNCH(bb_project_f_kernel<4>, kRangeProjectF0 + 0, j); break;
+    case 2: BB_LAUNCH(bb_dots_f_kernel<8>, kRangeDotsF0 + 1, j); BB_LAUNCH(bb_project_f_kernel<8>, kRangeProjectF0 + 1, j); break;
+    case 3: BB_LAUNCH(bb_dots_f_kernel<12>, kRangeDotsF0 + 2, j); BB_LAUNCH(bb_project_f_kernel<12>, kRangeProjectF0 + 2, j); break;
+    case 4: BB_LAUNCH(bb_dots_f_kernel<16>, kRangeDotsF0 + 3, j); BB_LAUNCH(bb_project_f_kernel<16>, kRangeProjectF0 + 3, j); break;
+    case 5: BB_LAUNCH(bb_dots_f_kernel<20>, kRangeDotsF0 + 4, j); BB_LAUNCH(bb_project_f_kernel<20>, kRangeProjectF0 + 4, j); break;
+    case 6: BB_LAUNCH(bb_dots_f_kernel<24>, kRangeDotsF0 + 5, j); BB_LAUNCH(bb_project_f_kernel<24>, kRangeProjectF0 + 5, j); break;
+    case 7: BB_LAUNCH(bb_dots_f_kernel<28>, kRangeDotsF0 + 6, j); BB_LAUNCH(bb_project_f_kernel<28>, kRangeProjectF0 + 6, j); break;
+    default: BB_LAUNCH(bb_dots_f_kernel<32>, kRangeDotsF0 + 7, j); BB_LAUNCH(bb_project_f_kernel<32>, kRangeProjectF0 + 7, j); break;
   }
   return MDP_OK;
 }
