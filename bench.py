@@ -35,6 +35,8 @@ METRIC = ("iPI time to ‖TV−V‖∞≤1e-8; Bellman SpMV+min GB/s vs HBM peak
 S, A, H, GAMMA = 1_000_000, 20, 16, 0.999
 K_ROW = 2 * H + 1
 TOL, ALPHA, RESTART = 1e-8, 0.01, 30
+# FP64 FMA peak of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 CPU_SAMPLE_DIV = 10  # the CPU oracle solves the same generator at S / 10 and is scaled by 10
 
 
@@ -72,10 +74,17 @@ def bellman_source_sha():
 
 
 def krylov_source_sha():
-    """sha256 (first 16 hex digits) of the sources that make the GMRES mat-vec kernel."""
+    """sha256 (first 16 hex digits) of the code that makes the GMRES mat-vec kernel:
+    sell.cuh and krylov_dev.cuh (the row layout and the kernel body) and the
+    kernel's own definition in krylov.cu (host code there does not change it)."""
+    csrc = os.path.join(ROOT, "paper_2507_22538_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("sell.cuh", "krylov_dev.cuh", "krylov.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2507_22538_gb300", "csrc", f), "rb").read())
+    for f in ("sell.cuh", "krylov_dev.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    src = open(os.path.join(csrc, "krylov.cu"), "rb").read()
+    start = src.index(b"__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(")
+    start = src.rindex(b"template", 0, start)
+    h.update(src[start:src.index(b"\n}\n", start) + 3])
     return h.hexdigest()[:16]
 
 
@@ -755,7 +764,7 @@ def main():
             ev.record(stream)
             marks.append(ev)
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
-                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed"):
+                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed", "gs_ms", "gs_flops", "gs_timed"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
@@ -925,6 +934,16 @@ def main():
                "launches_timed": int(totals["matvecs_timed"]),
                # every Arnoldi step launches one mat-vec; the timed ones are a sample of them
                "share_of_step": mv_ms * totals["inner_iters_total"] / (ms * args.steps)}
+    # FP64 single-pass classical Gram-Schmidt of the sampled steps: bound by the FP64 pipe
+    gs_tflops = totals["gs_flops"] / (totals["gs_ms"] * 1e-3) / 1e12 if totals["gs_ms"] > 0 else None
+    fp64_peak = FP64_PEAK_TFLOPS
+    roof_gs = {"bound": "alu", "kernel": "gm_dots_kernel + gm_project_kernel (FP64 single-pass classical "
+                                        "Gram-Schmidt of an Arnoldi step: 2 (j+1) + 1 FMA per state)",
+               "achieved": gs_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+               "frac": gs_tflops / fp64_peak if gs_tflops else None,
+               "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+               "traffic": None, "pairs_timed": int(totals["gs_timed"]),
+               "avg_pair_ms": totals["gs_ms"] / max(1, totals["gs_timed"])}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
@@ -940,7 +959,7 @@ def main():
     line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
-            "roofline": roofline, "roofline_matvec": roof_mv, "roofline_inner": inner_roof, "mixed_precision": mixed,
+            "roofline": roofline, "roofline_matvec": roof_mv, "roofline_gs": roof_gs, "roofline_inner": inner_roof, "mixed_precision": mixed,
             "mixed_precision_binary16": quant,
             "iterations": {"outer_per_step": totals["outer_iters"] / args.steps,
                            "inner_per_step": totals["inner_iters_total"] / args.steps,

@@ -113,6 +113,10 @@ typedef struct {
                                  j = 0, 8, 16, ... of every restart cycle, each between its own pair
                                  of CUDA events (record_timing only; all mat-vecs do the same work) */
   int64_t matvecs_timed;      /* mat-vec kernels timed in matvec_ms */
+  double gs_ms;               /* summed device time of the FP64 single-pass Gram-Schmidt (dots and
+                                 projection) of the same steps (record_timing only) */
+  double gs_flops;            /* their FP64 flops: 2 (2 (j + 1) + 1) S for step j */
+  int64_t gs_timed;           /* Gram-Schmidt pairs timed in gs_ms */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -482,6 +482,7 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
     gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
         S, B.basis, j, B.w, h->partials, K);
     MDP_LAUNCH_CHECK(h);
+    if (timed && h->gs_on) MDP_CUDA(cudaEventRecord(h->gs_ev[j], st));
     return MDP_OK;
   }
   if constexpr (!FINE && (NB == 8 || NB == 16 || NB == 32)) {  // re-orthogonalised steps use the coarse widths only
@@ -637,12 +638,22 @@ static void count_cycle(mdp_s* h, int steps) {
 // read the solver state).  Every kMatvecTimingStride-th step of a cycle is timed:
 // all mat-vecs do the same work, and an event pair around every one of them cost
 // about 2% of the solve.
+//
+// The FP64 single-pass Gram-Schmidt of the same steps (dots, then projection) is
+// timed from the mat-vec's end event to one after the projection; it does
+// 2 (j + 1) + 1 FP64 FMAs per state (j + 1 dots, j + 1 projection terms, ||u||^2).
 static mdp_status add_matvec_times(mdp_s* h, int n) {
   for (int j = 0; j < n; j += kMatvecTimingStride) {
     float ms = 0.f;
     MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j], h->mv_ev[2 * j + 1]));
     h->mv_ms += ms;
     h->mv_timed += 1;
+    if (h->gs_on) {
+      MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j + 1], h->gs_ev[j]));
+      h->gs_ms += ms;
+      h->gs_flops += 2.0 * (double)(2 * (j + 1) + 1) * (double)h->S;
+      h->gs_timed += 1;
+    }
   }
   return MDP_OK;
 }
@@ -650,8 +661,11 @@ static mdp_status add_matvec_times(mdp_s* h, int n) {
 template <bool U, typename T>
 static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine, double tol, int maxit,
                         int* iters, double* res2, cudaStream_t st) {
-  if (h->timing && !h->mv_ev[0])
+  if (h->timing && !h->mv_ev[0]) {
     for (cudaEvent_t& e : h->mv_ev) MDP_CUDA(cudaEventCreate(&e));
+    for (cudaEvent_t& e : h->gs_ev) MDP_CUDA(cudaEventCreate(&e));
+  }
+  h->gs_on = refine == MDP_REFINE_NEVER && sizeof(T) == sizeof(double);
   mdp_status r = (sizeof(T) == sizeof(double)) ? ensure_basis(h, m + 1) : ensure_mixed(h, m + 1);
   if (r != MDP_OK) return r;
   const KrylovBuffers<T> B = buffers(h, (T*)nullptr);

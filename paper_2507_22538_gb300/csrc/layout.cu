@@ -308,6 +308,8 @@ static void destroy_handle(mdp_s* h) {
   if (h->done) cudaEventDestroy(h->done);
   for (cudaEvent_t e : h->mv_ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->gs_ev)
+    if (e) cudaEventDestroy(e);
   delete h;
 }
 

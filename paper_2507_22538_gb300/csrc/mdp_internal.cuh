@@ -129,6 +129,11 @@ struct mdp_s {
   cudaEvent_t mv_ev[2 * mdp::kMaxBasis] = {};
   double mv_ms = 0.0;
   int64_t mv_timed = 0;
+  // and after the Gram-Schmidt passes of the same steps (FP64 single-pass steps only)
+  cudaEvent_t gs_ev[mdp::kMaxBasis] = {};
+  bool gs_on = false;
+  double gs_ms = 0.0, gs_flops = 0.0;
+  int64_t gs_timed = 0;
   int64_t launches = 0;
   // algorithmic work counters of the inner solver (see mdp_solve_stats)
   int64_t matvecs = 0, vreads = 0, vwrites = 0;

@@ -146,6 +146,8 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   const double ibytes0 = h->inner_bytes;
   const double mv_ms0 = h->mv_ms;
   const int64_t mv_timed0 = h->mv_timed;
+  const double gs_ms0 = h->gs_ms, gs_flops0 = h->gs_flops;
+  const int64_t gs_timed0 = h->gs_timed;
   mdp_solve_stats local;
   std::memset(&local, 0, sizeof(local));
   mdp_status status = MDP_OK;
@@ -229,6 +231,9 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   local.inner_bytes = h->inner_bytes - ibytes0;
   local.matvec_ms = h->mv_ms - mv_ms0;
   local.matvecs_timed = h->mv_timed - mv_timed0;
+  local.gs_ms = h->gs_ms - gs_ms0;
+  local.gs_flops = h->gs_flops - gs_flops0;
+  local.gs_timed = h->gs_timed - gs_timed0;
   local.policy_value_bytes = !mixed ? 8 : (h->pstore == kStoreF32 ? 4 : 2);
   local.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = local;

@@ -54,7 +54,8 @@ class mdp_solve_stats(ctypes.Structure):
                 ("inner_ms", ctypes.c_double), ("policy_matvecs", ctypes.c_int64),
                 ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double),
                 ("policy_value_bytes", ctypes.c_int32), ("matvec_ms", ctypes.c_double),
-                ("matvecs_timed", ctypes.c_int64)]
+                ("matvecs_timed", ctypes.c_int64), ("gs_ms", ctypes.c_double), ("gs_flops", ctypes.c_double),
+                ("gs_timed", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
