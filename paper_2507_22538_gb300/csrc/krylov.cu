@@ -77,6 +77,25 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T
   gm_dots_body<NB, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
+// The binary32 dots pass (mixed solver) at 4 blocks per SM (64 registers): measured
+// 110.9 -> 107.1 ms per mixed solve.  The FP64 pass keeps the compiler's choice
+// (80 registers, 3 blocks), faster there (147.8 against 150.3 ms at 4 blocks).
+template <int NB, bool FINE>
+__global__ void __launch_bounds__(kVecThreads, 4) gm_dots32_kernel(int64_t S, const float* __restrict__ basis, int j,
+                                                                   const float* __restrict__ w, double* partials,
+                                                                   KrylovState* K) {
+  gm_dots_body<NB, float, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
+}
+
+// The dots kernel of value type T.
+template <int NB, typename T, bool FINE>
+constexpr auto dots_kernel() {
+  if constexpr (sizeof(T) == sizeof(float))
+    return gm_dots32_kernel<NB, FINE>;
+  else
+    return gm_dots_kernel<NB, T, FINE>;
+}
+
 template <int NB, int MODE, typename T, bool FINE>
 __global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
                                                                   const T* __restrict__ w, double* partials,
@@ -475,8 +494,8 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
   if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
-  gm_dots_kernel<NB, T, FINE><<<MDP_WAVE((gm_dots_kernel<NB, T, FINE>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w,
-                                                                                              h->partials, K);
+  dots_kernel<NB, T, FINE>()<<<MDP_WAVE((dots_kernel<NB, T, FINE>())), kVecThreads, 0, st>>>(S, B.basis, j, B.w,
+                                                                                            h->partials, K);
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
     gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
@@ -529,14 +548,14 @@ static int pass_grid(mdp_s* h, GmresPass pass, int NB) {
       return MDP_WAVE(gm_update_kernel<T>);
     case kPassDots:
       switch (NB) {
-        case 4: return MDP_WAVE((gm_dots_kernel<4, T, FINE_T>));
-        case 8: return MDP_WAVE((gm_dots_kernel<8, T, FINE_T>));
-        case 12: return MDP_WAVE((gm_dots_kernel<12, T, FINE_T>));
-        case 16: return MDP_WAVE((gm_dots_kernel<16, T, FINE_T>));
-        case 20: return MDP_WAVE((gm_dots_kernel<20, T, FINE_T>));
-        case 24: return MDP_WAVE((gm_dots_kernel<24, T, FINE_T>));
-        case 28: return MDP_WAVE((gm_dots_kernel<28, T, FINE_T>));
-        default: return MDP_WAVE((gm_dots_kernel<32, T, FINE_T>));
+        case 4: return MDP_WAVE((dots_kernel<4, T, FINE_T>()));
+        case 8: return MDP_WAVE((dots_kernel<8, T, FINE_T>()));
+        case 12: return MDP_WAVE((dots_kernel<12, T, FINE_T>()));
+        case 16: return MDP_WAVE((dots_kernel<16, T, FINE_T>()));
+        case 20: return MDP_WAVE((dots_kernel<20, T, FINE_T>()));
+        case 24: return MDP_WAVE((dots_kernel<24, T, FINE_T>()));
+        case 28: return MDP_WAVE((dots_kernel<28, T, FINE_T>()));
+        default: return MDP_WAVE((dots_kernel<32, T, FINE_T>()));
       }
     case kPassProject:
       switch (NB) {
