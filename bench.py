@@ -4,8 +4,8 @@ epidemic-like MDP (S = 1e6 infected counts, A = 20 intervention levels, 33-wide
 binomial bands, gamma = 0.999, GMRES(30), alpha = 0.01), synthetic inputs.
 
 One step = one full mdp_solve from V_0 = 0: every Bellman sweep, policy-row
-gather, Arnoldi/CGS2 pass and Givens update of Algorithm 1 until the stop test
-holds.  Inputs (8.3 GB) stay resident in HBM and are larger than L2, so no L2
+gather, Arnoldi step (mat-vec and classical Gram-Schmidt) and Givens update of
+Algorithm 1 until the stop test holds.  Inputs (8.3 GB) stay resident in HBM and are larger than L2, so no L2
 flush is needed between steps.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -916,7 +916,7 @@ def main():
     bell_gbs = bellman_bytes() / (bell_ms * 1e-3) / 1e9
     inner_gbs = totals["inner_bytes"] / (totals["inner_ms"] * 1e-3) / 1e9 if totals["inner_ms"] > 0 else None
     share_bell = totals["bellman_ms"] / (ms * args.steps)
-    roofline = {"bound": "hbm", "kernel": "bellman_kernel (fused SpMV + min/argmin + residual + policy-row gather)",
+    roofline = {"bound": "hbm", "kernel": "bellman_kernel (fused SpMV + stage cost + min/argmin + residual)",
                 "achieved": bell_gbs, "peak": peak, "unit": "GB/s", "frac": bell_gbs / peak,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "traffic": sweep_traffic(),
