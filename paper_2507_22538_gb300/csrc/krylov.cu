@@ -1,13 +1,15 @@
 // Inexact policy evaluation (Algorithm 1 steps 6-12): the matrix-free operator
-// J_pi x = x - gamma P_pi x (Sec. III-B.3) over the policy's rows, and the two
-// inner solvers, Richardson (theta += omega (g_pi - J_pi theta)) and restarted
-// GMRES(m) (Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.5).
+// J_pi x = x - gamma P_pi x (Sec. III-B.3) over the policy's rows, and the inner
+// solvers: Richardson (theta += omega (g_pi - J_pi theta)), Jacobi-Richardson,
+// TFQMR (Freund 1993) and restarted GMRES(m) (Saad, Iterative Methods for Sparse
+// Linear Systems, Sec. 6.5).
 //
 // GMRES runs a whole restart cycle without the host: classical Gram-Schmidt
-// with a second pass only when the DGKS test asks for it (Daniel, Gragg,
-// Kaufman and Stewart, Math. Comp. 1976: re-orthogonalise when the norm after
-// projection falls below 1/sqrt(2) of the norm before), the Givens rotations,
-// the residual estimate and the stop test all on the device.  Each kernel
+// (one pass by default, PETSc's choice; optionally a second pass when the DGKS
+// test asks for it -- Daniel, Gragg, Kaufman and Stewart, Math. Comp. 1976:
+// re-orthogonalise when the norm after projection falls below 1/sqrt(2) of the
+// norm before -- or always), the Givens rotations, the residual estimate and the
+// stop test all on the device.  Each kernel
 // reduces its dot products in its last finishing block (fixed order, so
 // results are deterministic) and checks device flags on entry, so steps queued
 // after the stop test fired return at once.  The host waits once per cycle.
