@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long
   const double res = __longlong_as_double((long long)*resmax);
   // k grows by one per evaluation, so at most max_iter_pi + 1 sweeps run; the guard
   // on the sweep count bounds the outer loop even if that ever failed
-  const bool guard = G->sweeps > max_iter_pi + 1;
+  const bool guard = (long long)G->sweeps > (long long)max_iter_pi + 1;  // 64-bit: max_iter_pi may be INT_MAX
   const bool go = isfinite(res) && !(res <= atol) && G->k < max_iter_pi && !guard;
   if (go) {
     unsigned long long* words = reinterpret_cast<unsigned long long*>(K);
@@ -126,12 +126,12 @@ __global__ void __launch_bounds__(256) gs_outer_check_kernel(const unsigned long
 // GMRES solve is not over.  Every cycle runs at least one Arnoldi step (the
 // restart residual clears the cycle's stop flag) and the solve ends at max_it
 // steps, so at most max_it + 1 passes run; the guard bounds the loop regardless.
-__global__ void gs_inner_cond_kernel(KrylovState* K, GraphDevice* D, int seg, int in_loop, int max_passes,
+__global__ void gs_inner_cond_kernel(KrylovState* K, GraphDevice* D, int seg, int in_loop, long long max_passes,
                                      cudaGraphConditionalHandle c_inner) {
   if (threadIdx.x != 0) return;
   GraphSolveState* G = &D->G;
   G->launches += D->seg_kernels[seg];
-  if (in_loop && ++G->passes > max_passes) {
+  if (in_loop && (long long)(++G->passes) > max_passes) {
     G->guard = 1;
     K->flags |= kSolveDone | kNumeric;
   }
@@ -308,7 +308,7 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
   MDP_TRY(capture(h, cs, &seg, &nk[kSegGo], [&]() -> mdp_status {
     MDP_TRY(extract_policy(h, pi, mixed, cs));
     MDP_TRY(gmres_residual_launch(h, mixed, gamma, V, cs));
-    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, kSegGo, 0, o->max_iter_ksp + 1, c_inner);
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, kSegGo, 0, (long long)o->max_iter_ksp + 1, c_inner);
     return control_done();
   }));
   MDP_TRY(add_segment(go_body, nullptr, 0, seg, &n_go));
@@ -342,7 +342,7 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
   cudaGraphNode_t n_tail;
   MDP_TRY(capture(h, cs, &seg, &nk[seg_tail], [&]() -> mdp_status {
     MDP_TRY(gmres_tail_launch(h, mixed, gamma, V, cs));
-    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, seg_tail, 1, o->max_iter_ksp + 1, c_inner);
+    gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, seg_tail, 1, (long long)o->max_iter_ksp + 1, c_inner);
     return control_done();
   }));
   MDP_TRY(add_segment(inner_body, &prev, 1, seg, &n_tail));

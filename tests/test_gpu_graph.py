@@ -167,3 +167,16 @@ def test_graph_solve_certified_by_oracle():
     Q = O.q_values(P, m.g, m.gamma, Vs, m.S, m.A)
     sure = O.action_gaps(Q) > 1e-9
     assert np.array_equal(pi.cpu().numpy()[sure], ps[sure])
+
+
+def test_graph_solve_with_uncapped_iterations():
+    """Caps at INT_MAX (no cap in practice): the loop guards, which allow caps + 1 and
+    + 2 passes, must not overflow and end a converging solve early."""
+    from paper_2507_22538_gb300 import mdp
+    m = random_sparse(1000, 4, 8, 0.9, seed=1)
+    big = 2**31 - 1
+    with mdp.MDP.from_data(m) as M:
+        ref = _solve(mdp, M, m, False, tol=1e-10, alpha=1e-3, max_outer=big, max_inner=big)
+        got = _solve(mdp, M, m, True, tol=1e-10, alpha=1e-3, max_outer=big, max_inner=big)
+    assert ref[3] == mdp.MDP_OK
+    _assert_same(ref, got)
