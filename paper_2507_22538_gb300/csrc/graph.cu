@@ -53,7 +53,6 @@ struct GraphSolveState {
   long long cycles;       // restart cycles that ran at least one Arnoldi step
   long long steps;        // Arnoldi steps
   long long tri;          // sum over those cycles of n (n - 1) / 2, n = steps of the cycle
-  long long loops;        // passes of the inner WHILE body
   int k;                  // policy evaluations completed
   int status;             // MDP_OK, MDP_NOT_CONVERGED or MDP_ERR_NUMERIC
   int converged;
@@ -142,7 +141,6 @@ __global__ void gs_inner_cond_kernel(KrylovState* K, GraphDevice* D, int seg, in
     G->tri += n * (n - 1) / 2;
   }
   G->it_prev = K->it;
-  if (in_loop) G->loops += 1;
   cudaGraphSetConditional(c_inner, (K->flags & kSolveDone) ? 0u : 1u);
 }
 
