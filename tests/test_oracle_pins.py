@@ -284,14 +284,29 @@ def _pins_hold():
         test_single_state_closed_form()
         for s in range(3):
             test_brute_force_tiny(s)
+        test_unrestarted_gmres_is_exact_in_n_steps()
+        test_tfqmr_solves_policy_system()
+        test_jacobi_diagonal_and_one_step_identity()
     except AssertionError:
         return False
     return True
 
 
-@pytest.mark.parametrize("mutant", ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign"])
+def _q_without_cost(P, g, gamma, V, S, A):
+    return gamma * (P @ np.asarray(V, dtype=np.float64)).reshape(S, A)
+
+
+MUTANTS = ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign", "policy_row_action_major",
+           "J_gamma_squared", "evaluation_sign", "jacobi_diagonal_sign", "dropped_cost"]
+
+
+@pytest.mark.parametrize("mutant", MUTANTS)
 def test_planted_mistakes_are_caught(monkeypatch, mutant):
-    """Plausible mistakes planted in the oracle make at least one pin fail."""
+    """Plausible mistakes planted in the oracle make at least one pin fail: a wrong
+    tie-break, discount, layout or sign in the Bellman operator and in J_pi, the
+    policy rows taken action-major (pi(s) S + s instead of s A + pi(s)), the policy
+    evaluated with the wrong sign, the Jacobi diagonal with the wrong sign, the
+    stage cost dropped from Q."""
     assert _pins_hold()
     if mutant == "argmax_ties":
         monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
@@ -302,6 +317,20 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
         monkeypatch.setattr(O, "bellman", _bellman_transposed)
     elif mutant == "inner_sign":
         monkeypatch.setattr(O, "apply_J", lambda Ppi, gamma, x: x + gamma * (Ppi @ x))
+    elif mutant == "policy_row_action_major":
+        monkeypatch.setattr(O, "policy_rows", lambda pi, A: np.asarray(pi, dtype=np.int64) * np.asarray(pi).size
+                            + np.arange(np.asarray(pi).size, dtype=np.int64))
+    elif mutant == "J_gamma_squared":
+        monkeypatch.setattr(O, "apply_J", lambda Ppi, gamma, x: x - gamma * gamma * (Ppi @ x))
+    elif mutant == "evaluation_sign":
+        monkeypatch.setattr(O, "evaluate_policy",
+                            lambda Ppi, gpi, gamma, dense_limit=5000, tol_rel=1e-14:
+                            np.linalg.solve(np.eye(gpi.size) + gamma * Ppi.toarray(), gpi))
+    elif mutant == "jacobi_diagonal_sign":
+        monkeypatch.setattr(O, "jacobi_diagonal",
+                            lambda Ppi, gamma: 1.0 + gamma * np.asarray(Ppi.diagonal(), dtype=np.float64))
+    elif mutant == "dropped_cost":
+        monkeypatch.setattr(O, "q_values", _q_without_cost)
     assert not _pins_hold()
 
 
