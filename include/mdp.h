@@ -272,7 +272,10 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
  *  S, A          at most 2,097,152 states and 128 actions (else MDP_ERR_INVALID_ARG).
  *  row_ptr, col, val, g   device arrays laid out as for mdp_create; the caller
  *                guarantees they are valid (this call does not check them).
- *  V, TV, pi, residual_inf   as for mdp_bellman (residual_inf may be NULL).
+ *  V, TV, pi, residual_inf   as for mdp_bellman (residual_inf may be NULL).  The outputs
+ *                TV, pi and residual_inf must not share any byte with one another or
+ *                with V, g or row_ptr (MDP_ERR_INVALID_ARG); col and val, whose length the
+ *                call does not know, must not overlap them either.
  * Scratch: a fixed 512 KB array in the library's device memory, present on every
  * GPU that loads the library until the process exits.  Its device address is
  * looked up on the first call made on each device (that first call must not be

@@ -150,6 +150,31 @@ def random_sparse(S: int, A: int, k: int, gamma: float, seed: int, conc: float =
     return MDPData(S, A, row_ptr, col, val, g, gamma, f"random_sparse(S={S},A={A},k={k})")
 
 
+def ragged_sparse(S: int, A: int, kmax: int, gamma: float, seed: int, long_frac: float = 0.02,
+                  quant_bits: int | None = None) -> MDPData:
+    """Random sparse MDP whose rows have different lengths: 1..kmax distinct uniform
+    columns (sorted), plus a fraction long_frac of rows with 3 kmax entries (capped
+    at S), Dirichlet(1) weights (optionally quantised to 2**-quant_bits), costs
+    U[-1, 2).  Every row of the stacked matrix and of any policy's rows has its own
+    length, which exercises the non-uniform sliced layouts.  Drawn with numpy's
+    PCG64 from `seed` (test inputs; rows are not regenerated one by one)."""
+    rng = np.random.default_rng(seed)
+    R = S * A
+    lens = rng.integers(1, kmax + 1, size=R)
+    lens[rng.integers(0, R, size=max(1, int(R * long_frac)))] = 3 * kmax
+    lens = np.minimum(lens, S)
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    val = np.empty(int(row_ptr[-1]))
+    for r in range(R):
+        lo, hi = int(row_ptr[r]), int(row_ptr[r + 1])
+        col[lo:hi] = np.sort(rng.choice(S, size=hi - lo, replace=False))
+        w = -np.log1p(-rng.random(hi - lo))
+        val[lo:hi] = w / w.sum() if quant_bits is None else quantize_rows(w[None, :], quant_bits)[0]
+    g = rng.random(R) * 3.0 - 1.0
+    return MDPData(S, A, row_ptr, col, val, g, gamma, f"ragged_sparse({S},{A},{kmax})")
+
+
 def sis_band_centres(s: np.ndarray, a: np.ndarray, S: int, A: int, half_width: int,
                      r0_max: float = 2.5) -> np.ndarray:
     """Band centre of row (s, a): the expected infected count after one SIS step.

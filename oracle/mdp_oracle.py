@@ -346,29 +346,17 @@ def value_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, V0=None,
     return SolveResult(V, pi, False, max_iter, [1] * max_iter, residuals)
 
 
-def evaluate_policy(Ppi, gpi, gamma: float, dense_limit: int = 5000, tol_rel: float = 1e-14) -> np.ndarray:
-    """V_pi solving (I - gamma P_pi) V = g_pi (Eq. 2).
+def evaluate_policy(Ppi, gpi, gamma: float, dense_limit: int = 5000) -> np.ndarray:
+    """V_pi solving (I - gamma P_pi) V = g_pi (Eq. 2) by a dense LAPACK solve.
 
-    Up to dense_limit states: a dense LAPACK solve.  Above it: GMRES(50) from
-    V = 0 to a relative residual of tol_rel, then fixed-point sweeps
-    V <- T_pi V while ||T_pi V - V||_inf keeps shrinking.
+    Only systems of up to dense_limit states are solved (ValueError above it):
+    the oracle's exact evaluation is the plain definition, nothing iterative.
     """
     S = gpi.size
-    if S <= dense_limit:
-        J = np.eye(S) - gamma * Ppi.toarray()
-        return np.linalg.solve(J, gpi)
-    mv = lambda x: apply_J(Ppi, gamma, x)
-    bn = float(np.linalg.norm(gpi))
-    V = gmres(mv, gpi, np.zeros(S), 50, tol_rel * max(bn, 1e-300), 100000).x
-    last = math.inf
-    for _ in range(200):
-        TV = policy_operator(Ppi, gpi, gamma, V)
-        d = float(np.max(np.abs(TV - V)))
-        V = TV
-        if d >= last:
-            break
-        last = d
-    return V
+    if S > dense_limit:
+        raise ValueError(f"exact policy evaluation is dense: S = {S} > dense_limit = {dense_limit}")
+    J = np.eye(S) - gamma * Ppi.toarray()
+    return np.linalg.solve(J, gpi)
 
 
 def policy_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, max_iter: int = 1000,
@@ -432,7 +420,9 @@ def bellman_states(states, row_cols, row_vals, row_g, gamma: float, V, A: int):
 
 
 def action_gaps(Q: np.ndarray) -> np.ndarray:
-    """Second-smallest minus smallest Q per state (inf when A == 1)."""
+    """Action gap per state: the second-smallest Q(s, .) minus the smallest one,
+    counting repeated values (an exact tie gives 0); inf when A == 1.  It decides
+    where the greedy policy of Eq. 4 is unique beyond a given rounding band."""
     if Q.shape[1] == 1:
         return np.full(Q.shape[0], np.inf)
     part = np.partition(Q, 1, axis=1)

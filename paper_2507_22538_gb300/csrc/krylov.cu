@@ -418,7 +418,8 @@ static int wave_grid(mdp_s* h, Kern kernel, int max_per_sm = kMaxBlocksPerSm) {
     }
   }
   const int64_t chunks = (h->S + kVecThreads - 1) / kVecThreads;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)h->sm_count * std::min(per_sm, max_per_sm)));
+  const int64_t wave = std::min<int64_t>((int64_t)h->sm_count * std::min(per_sm, max_per_sm), h->partial_stride);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, wave));
 }
 
 #define MDP_WAVE(kern) wave_grid(h, kern)  // kern in parentheses when it has template commas

@@ -544,7 +544,7 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(h, &h->piw, S, "policy"));
   MDP_TRY(dalloc(h, &h->w, S, "w"));
   MDP_TRY(dalloc(h, &h->tmp, S, "tmp"));
-  h->partial_stride = h->sm_count * kMaxBlocksPerSm;
+  h->partial_stride = std::min(h->sm_count * kMaxBlocksPerSm, kMaxReduceBlocks);
   // block partials, then the second-level group sums of the grid reductions
   MDP_TRY(dalloc(h, &h->partials, (size_t)kPartialRows * (h->partial_stride + kMaxGroups), "partials"));
   {

@@ -19,6 +19,10 @@ constexpr int kPartialRows = 40;    // per-block partial sums (up to kMaxBasis +
 constexpr int kGroup = 32;          // blocks per first-level group of a grid reduction
 constexpr int kMaxGroups = 64;      // second-level sums per value: grids of up to 2048 blocks
 constexpr int kMaxBlocksPerSm = 8;  // 256-thread blocks: 2048 threads per SM
+// Largest grid of a reducing kernel: the two-level tail holds kMaxGroups group sums
+// of kGroup blocks each.  Grids are clamped to it (a part with more than 256 SMs
+// runs fewer blocks per SM instead of overrunning the group rows).
+constexpr int kMaxReduceBlocks = kGroup * kMaxGroups;
 constexpr int kMatvecTimingStride = 8;  // record_timing times the mat-vec of steps j = 0, 8, 16, ... of a cycle
 enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 constexpr int kScalarSlots = 512;

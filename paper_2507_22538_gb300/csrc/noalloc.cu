@@ -143,7 +143,26 @@ extern "C" mdp_status mdp_bellman_csr_noalloc(int64_t S, int32_t A, const int64_
                 "mdp_bellman_csr_noalloc supports at most 2097152 states (65536 tiles of 32 in its fixed scratch)");
   if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_ERR_INVALID_ARG, "gamma must lie in (0, 1)");
   if (!row_ptr || !col || !val || !g || !V || !TV || !pi) return fail(MDP_ERR_INVALID_ARG, "null array");
-  if ((const void*)V == (const void*)TV) return fail(MDP_ERR_INVALID_ARG, "V and TV may not alias");
+  // the outputs are written while other tiles still read V, g and the row pointers:
+  // no output may share a byte with another output or with those inputs
+  {
+    const uint64_t R = (uint64_t)S * (uint64_t)A;
+    const struct { const void* p; uint64_t n; } in[] = {{V, (uint64_t)S * 8}, {g, R * 8}, {row_ptr, (R + 1) * 8}},
+                                                 out[] = {{TV, (uint64_t)S * 8}, {pi, (uint64_t)S * 4},
+                                                          {residual_inf, residual_inf ? 8u : 0u}};
+    auto overlap = [](const void* a, uint64_t na, const void* b, uint64_t nb) {
+      const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+      return na && nb && x < y + nb && y < x + na;
+    };
+    for (int i = 0; i < 3; ++i) {
+      for (const auto& r : in)
+        if (overlap(out[i].p, out[i].n, r.p, r.n))
+          return fail(MDP_ERR_INVALID_ARG, "TV, pi and residual_inf may not overlap V, g or row_ptr");
+      for (int j = i + 1; j < 3; ++j)
+        if (overlap(out[i].p, out[i].n, out[j].p, out[j].n))
+          return fail(MDP_ERR_INVALID_ARG, "TV, pi and residual_inf may not overlap one another");
+    }
+  }
   unsigned long long* scratch = nullptr;
   mdp_status s = noalloc_scratch(&scratch);
   if (s != MDP_OK) return s;

@@ -83,3 +83,21 @@ def test_struct_layouts_match_header(tmp_path):
         assert c[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
         for f, _ in st._fields_:
             assert c[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
+
+
+def test_noalloc_rejects_overlapping_buffers(lib):
+    """mdp_bellman_csr_noalloc refuses outputs that share bytes with each other or with
+    V, g or row_ptr on the host, before it touches the device (the addresses below are
+    never dereferenced; without a GPU a missed overlap would end in a CUDA error, not
+    in a launch)."""
+    from paper_2507_22538_gb300 import mdp
+    S, A = 100, 3
+    base = 1 << 20
+    V, g, rp = base, base + 10_000, base + 20_000
+    TV, pi, res = base + 40_000, base + 50_000, base + 60_000
+    for bad in (dict(TV=V + 8), dict(TV=g + S * A * 8 - 8), dict(pi=rp), dict(res=TV + 8 * (S - 1)),
+                dict(pi=TV + 4), dict(res=pi + 4 * S - 4)):
+        a = dict(V=V, TV=TV, pi=pi, res=res)
+        a.update(bad)
+        st = mdp.mdp_bellman_csr_noalloc(S, A, rp, 7, 7, g, 0.9, a["V"], a["TV"], a["pi"], a["res"], stream=0)
+        assert st == mdp.MDP_ERR_INVALID_ARG and "overlap" in mdp.mdp_last_error(), bad

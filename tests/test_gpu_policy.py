@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from mdpgen import banded_birth_death, pendulum_grid, random_sparse, random_value_vector
+from mdpgen import banded_birth_death, pendulum_grid, ragged_sparse, random_sparse, random_value_vector
 from oracle import mdp_oracle as O
 from tests._util import EPS, to_device
 
@@ -14,6 +14,9 @@ CASES = [
     ("banded", lambda: banded_birth_death(4000, 20, 16, 0.999)),
     ("pendulum", lambda: pendulum_grid(40, 40, 9, 0.9999, seed=3)),
     ("tiny", lambda: random_sparse(5, 2, 3, 0.7, seed=9)),
+    # rows of 1..40 entries and a few of 120: the non-uniform policy-row gather and row dot
+    ("ragged_rows", lambda: ragged_sparse(1500, 4, 40, 0.99, seed=21)),
+    ("ragged_rows_f16_exact", lambda: ragged_sparse(1100, 3, 24, 0.97, seed=22, quant_bits=11)),
 ]
 
 

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from mdpgen import banded_birth_death, maze, pendulum_grid, random_sparse
+from mdpgen import banded_birth_death, maze, pendulum_grid, ragged_sparse, random_sparse
 from oracle import mdp_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -33,6 +33,9 @@ SOLVE_CASES = [
     ("pendulum_40x40_a9", lambda: pendulum_grid(40, 40, 9, 0.99, seed=3), 1e-3, 1e-8),
     ("random_s3000_a32_k32", lambda: random_sparse(3000, 32, 32, 0.99, seed=4, conc=0.5, quant_bits=11), 1e-4, 1e-8),
     ("maze_40x40", lambda: maze(40, 40, 0.2, seed=7, gamma=0.99)[0], 1e-4, 1e-8),
+    # rows of 1..40 entries (and a few of 120): the non-uniform layouts on both the sweep
+    # and the policy side, against the oracle
+    ("ragged_s1200_a5_k1to40", lambda: ragged_sparse(1200, 5, 40, 0.97, seed=13), 1e-3, 1e-8),
 ]
 
 

@@ -263,6 +263,36 @@ def test_bellman_states_matches_stacked(mid_mdp):
     np.testing.assert_array_equal(p, pi[states])
 
 
+def test_action_gaps_hand_computed():
+    """The action gap (second-smallest minus smallest Q per state, Eq. 4's margin of
+    uniqueness) on hand-computed cases: the three-state fixture at V*, where
+    Q(0, .) = (2, 9/11), Q(1, .) = (1, 10/11) and Q(2, .) = (0, 0) give gaps 13/11,
+    1/11 and an exact tie 0; unsorted and repeated values; negative costs; and
+    A = 1, which has no second action (inf)."""
+    d = _load("three_state.json")
+    args = _fixture_args(d)
+    P = O.stacked_matrix(d["S"], d["A"], args[2], args[3], args[4])
+    Q = O.q_values(P, args[5], d["gamma"], np.array(d["V_star"]), d["S"], d["A"])
+    np.testing.assert_allclose(Q, [[2.0, 9 / 11], [1.0, 10 / 11], [0.0, 0.0]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(O.action_gaps(Q), [13 / 11, 1 / 11, 0.0], rtol=0, atol=1e-15)
+    hand = np.array([[3.0, 1.0, 2.0], [5.0, 5.0, 7.0], [4.0, 2.0, 2.0], [-1.0, -3.0, 0.0], [9.0, 8.5, 0.25]])
+    np.testing.assert_array_equal(O.action_gaps(hand), [1.0, 0.0, 0.0, 2.0, 8.25])
+    assert np.all(O.action_gaps(np.array([[0.7], [-2.0]])) == np.inf)
+
+
+def test_check_policy_rejects_a_wrong_policy():
+    """The GPU tests' policy check (tests/_util.py) fails a planted wrong action where
+    the gap is resolvable and accepts any minimiser at an exact tie."""
+    from tests._util import check_policy
+    Q = np.array([[2.0, 9 / 11], [1.0, 10 / 11], [0.0, 0.0]])
+    check_policy(np.array([1, 1, 0]), Q, 1e-12)
+    check_policy(np.array([1, 1, 1]), Q, 1e-12)  # state 2 is a tie: either action is greedy
+    with pytest.raises(AssertionError):
+        check_policy(np.array([0, 1, 0]), Q, 1e-12)
+    with pytest.raises(AssertionError):
+        check_policy(np.array([1, 0, 0]), Q, 1e-12)
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def _bellman_argmax_ties(P, g, gamma, V, S, A):
@@ -287,7 +317,9 @@ def _pins_hold():
         test_unrestarted_gmres_is_exact_in_n_steps()
         test_tfqmr_solves_policy_system()
         test_jacobi_diagonal_and_one_step_identity()
-    except AssertionError:
+        test_action_gaps_hand_computed()
+        test_check_policy_rejects_a_wrong_policy()
+    except (AssertionError, pytest.fail.Exception):
         return False
     return True
 
@@ -297,7 +329,8 @@ def _q_without_cost(P, g, gamma, V, S, A):
 
 
 MUTANTS = ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign", "policy_row_action_major",
-           "J_gamma_squared", "evaluation_sign", "jacobi_diagonal_sign", "dropped_cost"]
+           "J_gamma_squared", "evaluation_sign", "jacobi_diagonal_sign", "dropped_cost", "gaps_reversed",
+           "gaps_zero", "gaps_inf", "gaps_largest"]
 
 
 @pytest.mark.parametrize("mutant", MUTANTS)
@@ -324,13 +357,22 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
         monkeypatch.setattr(O, "apply_J", lambda Ppi, gamma, x: x - gamma * gamma * (Ppi @ x))
     elif mutant == "evaluation_sign":
         monkeypatch.setattr(O, "evaluate_policy",
-                            lambda Ppi, gpi, gamma, dense_limit=5000, tol_rel=1e-14:
+                            lambda Ppi, gpi, gamma, dense_limit=5000:
                             np.linalg.solve(np.eye(gpi.size) + gamma * Ppi.toarray(), gpi))
     elif mutant == "jacobi_diagonal_sign":
         monkeypatch.setattr(O, "jacobi_diagonal",
                             lambda Ppi, gamma: 1.0 + gamma * np.asarray(Ppi.diagonal(), dtype=np.float64))
     elif mutant == "dropped_cost":
         monkeypatch.setattr(O, "q_values", _q_without_cost)
+    elif mutant == "gaps_reversed":
+        monkeypatch.setattr(O, "action_gaps", lambda Q: (lambda p: p[:, 0] - p[:, 1])(np.partition(Q, 1, axis=1))
+                            if Q.shape[1] > 1 else np.full(Q.shape[0], np.inf))
+    elif mutant == "gaps_zero":
+        monkeypatch.setattr(O, "action_gaps", lambda Q: np.zeros(Q.shape[0]))
+    elif mutant == "gaps_inf":
+        monkeypatch.setattr(O, "action_gaps", lambda Q: np.full(Q.shape[0], np.inf))
+    elif mutant == "gaps_largest":
+        monkeypatch.setattr(O, "action_gaps", lambda Q: Q.max(axis=1) - Q.min(axis=1))
     assert not _pins_hold()
 
 

@@ -23,7 +23,11 @@ def lib():
 
 
 @pytest.mark.parametrize("make", [lambda: random_sparse(1037, 5, 8, 0.95, seed=31),
-                                  lambda: banded_birth_death(20000, 20, 16, 0.999)], ids=["random_ragged", "banded"])
+                                  lambda: banded_birth_death(20000, 20, 16, 0.999),
+                                  # the largest size the fixed scratch takes: 65536 tiles of 32 states,
+                                  # where the last tile's slot sits next to the completion counter
+                                  lambda: random_sparse(2_097_152, 2, 2, 0.9, seed=41)],
+                         ids=["random_ragged", "banded", "max_states"])
 def test_noalloc_matches_bellman_on_two_calls(lib, make):
     import torch
     mdp = lib
@@ -57,3 +61,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     assert st == mdp.MDP_ERR_INVALID_ARG and "2097152" in mdp.mdp_last_error()
     st = mdp.mdp_bellman_csr_noalloc(100, 129, 1, 1, 1, 1, 0.9, 1, 2, 3, None, stream=0)
     assert st == mdp.MDP_ERR_INVALID_ARG and "128" in mdp.mdp_last_error()
+
+
+def test_noalloc_allocates_nothing(lib):
+    """The point of the entry point: once its first call on the device has looked up
+    the scratch address, later calls change neither torch's allocator nor the
+    device's free memory (cudaMemGetInfo)."""
+    import torch
+    mdp = lib
+    m = random_sparse(5000, 4, 8, 0.9, seed=32)
+    d = to_device(m)
+    V = torch.from_numpy(random_value_vector(m.S, 5, 10.0)).cuda()
+    TV = torch.empty_like(V)
+    pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+    res = torch.empty(1, dtype=torch.float64, device="cuda")
+    args = (m.S, m.A, d["row_ptr"], d["col"], d["val"], d["g"], m.gamma, V, TV, pi, res)
+    assert mdp.mdp_bellman_csr_noalloc(*args) == mdp.MDP_OK, mdp.mdp_last_error()  # first call: set-up
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(3):
+        assert mdp.mdp_bellman_csr_noalloc(*args) == mdp.MDP_OK, mdp.mdp_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
