@@ -37,7 +37,6 @@ K_ROW = 2 * H + 1
 TOL, ALPHA, RESTART = 1e-8, 0.01, 30
 # FP64 FMA peak of GB300: 152 SMs x 2 FP64 FMA per SM per clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-CPU_SAMPLE_DIV = 10  # the CPU oracle solves the same generator at S / 10 and is scaled by 10
 
 
 def workload_config():
@@ -200,37 +199,113 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_oracle_solve(div=CPU_SAMPLE_DIV):
-    """Time the FP64 oracle's Algorithm 1 on the same generator at S / div."""
+def certified_bound(res, gamma, kmax, gnorm, vnorm):
+    """Bound on ||V - V*||_inf from a computed Bellman residual res = ||TV - V||_inf
+    (Sec. II: T is a gamma-contraction, so ||V - V*|| <= ||TV - V|| / (1 - gamma)),
+    widened by the rounding of the residual's own computation: each Q is a
+    length-kmax recursive dot product plus cost, off by at most
+    gamma_{k+2} (|g| + gamma |V|) with gamma_n = n u / (1 - n u) (Higham, Sec. 3.1)."""
+    u = 2.0 ** -53
+    n = kmax + 2
+    q = n * u / (1 - n * u) * (gnorm + gamma * vnorm)
+    return (res + q) / (1 - gamma)
+
+
+def error_statement(V, pi, res, gamma, kmax, gnorm, ref=None, ref_name="fp64_gpu"):
+    """The error of one solve's result: the certified bound against the exact V*, and
+    (when a reference result is given) its distance to it and the policy mismatches."""
+    import numpy as np
+    vn = float(np.max(np.abs(V)))
+    out = {"certified_bound_vs_Vstar": certified_bound(res, gamma, kmax, gnorm, vn),
+           "relative_certified_bound": certified_bound(res, gamma, kmax, gnorm, vn) / vn if vn else None}
+    if ref is not None:
+        rV, rpi = ref
+        out[f"max_abs_diff_vs_{ref_name}"] = float(np.max(np.abs(V - rV)))
+        out[f"policy_mismatches_vs_{ref_name}"] = int(np.sum(pi != rpi))
+    return out
+
+
+def cpu_info():
+    """The host the CPU oracle runs on: logical cores and the CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def cpu_oracle_solve(save_v=None):
+    """Time the FP64 oracle's Algorithm 1 on the bench workload itself (S = 1e6, same
+    generator, gamma, tol, alpha and GMRES(30)): numpy/scipy with one thread (its
+    sparse products are single-threaded scipy; BLAS is pinned to one thread above).
+    Returns (seconds, iteration info); optionally saves V and pi (.npz) for the error
+    statement of the GPU results."""
+    import numpy as np
     from mdpgen import banded_birth_death
     from oracle import mdp_oracle as O
-    m = banded_birth_death(S // div, A, H, GAMMA)
+    m = banded_birth_death(S, A, H, GAMMA)
     t0 = time.perf_counter()
     r = O.ipi(m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma, tol=TOL, alpha=ALPHA, inner="gmres",
               restart=RESTART)
     dt = time.perf_counter() - t0
-    return dt * div, {"converged": r.converged, "outer": r.outer_iters, "inner": int(sum(r.inner_iters))}
+    if save_v:
+        np.savez(save_v, V=r.V, pi=r.pi)
+    return dt, {"converged": bool(r.converged), "outer": int(r.outer_iters), "inner": int(sum(r.inner_iters)),
+                "final_residual": float(r.residuals[-1])}
+
+
+def run_cpu_oracle_worker(args):
+    """Child process of the bench: one timed oracle solve of the full workload, run on
+    one host core while the GPU measurements proceed; prints one JSON line."""
+    t, info = cpu_oracle_solve(save_v=args.cpu_oracle_worker)
+    print(json.dumps({"seconds": t, "info": info, **cpu_info()}), flush=True)
+    return 0
+
+
+REFERENCE_BUDGET_S = 150.0  # the reference arm stops timing further solves after this much wall time
 
 
 def run_reference(args):
+    """The FP64 CPU oracle timed on the bench workload itself.  One solve takes about
+    100 s on one core, so the arm times solves back to back until `steps` are done or
+    REFERENCE_BUDGET_S has passed (at least one), runs no warm-up solve (the oracle
+    keeps no state between solves), and reports the number it timed as `steps`."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    times = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        t, info = cpu_oracle_solve(args.reference_div)
-        if i >= args.warmup:
-            times.append(t)
-    v = sum(times) / len(times)
-    sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the S={S // args.reference_div} "
-              f"instance of the same generator (same A, k, gamma, tol, alpha), wall time x{args.reference_div} "
-              f"(cost is linear in S at fixed iteration counts); last run {info}")
+    times, info = [], None
+    t_start = time.perf_counter()
+    while len(times) < max(1, args.steps):
+        t, info = cpu_oracle_solve()
+        times.append(t)
+        if time.perf_counter() - t_start + t > REFERENCE_BUDGET_S:
+            break
+    v = statistics.median(times)
+    host = cpu_info()
+    sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the bench workload itself "
+              f"(S={S}, same generator, gamma, tol, alpha), {len(times)} solve(s) timed of {args.steps} requested "
+              f"(one solve takes ~{v:.0f} s; the arm stops after {REFERENCE_BUDGET_S:.0f} s), no warm-up; "
+              f"one thread on a {host['nproc']}-core {host['cpu_model']} host; last run {info}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "steps": len(times), "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "runs_s": times, **host},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -448,6 +523,7 @@ def run_stress(sweeps=10):
         peak, _ = load_peaks()
         out["bellman"] = {"ms_per_sweep": ms, "bytes": nbytes, "GB/s": nbytes / ms / 1e6,
                           "frac": nbytes / ms / 1e6 / peak, "fp64_fma_per_s": R * Kx / (ms * 1e-3)}
+        ref = None
         for name, prec in (("solve_f64", mdp.MDP_PREC_F64), ("solve_mixed", mdp.MDP_PREC_MIXED)):
             o = mdp.mdp_default_opts()
             o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.precision = gx, 1e-8, 1e-4, 30, prec
@@ -461,6 +537,10 @@ def run_stress(sweeps=10):
             mdp.check(st, "mdp_solve")
             out[name] = {"s": dt, "outer": stats.outer_iters, "inner": stats.inner_iters_total,
                          "final_residual": stats.final_residual, "policy_value_bytes": stats.policy_value_bytes}
+            Vh, pih = V.cpu().numpy(), pi.cpu().numpy()
+            # costs lie in [0, 1): |g| < 1
+            out[name]["error"] = error_statement(Vh, pih, stats.final_residual, gx, Kx, 1.0, ref)
+            ref = ref or (Vh, pih)
     torch.cuda.empty_cache()
     return out
 
@@ -471,6 +551,7 @@ def run_pendulum():
     at most 1000 outer and 1000 inner iterations) and GMRES(30), FP64 and mixed, and
     with TFQMR; then the variant whose bilinear weights are rounded to 2^-8 (exact in
     bfloat16), FP64 against mixed with bfloat16 policy values."""
+    import numpy as np
     import torch
 
     from mdpgen import pendulum_grid
@@ -485,6 +566,8 @@ def run_pendulum():
         with mdp.MDP.from_data(m, stream) as M:
             V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
             pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+            ref = None
+            gnorm = float(np.max(np.abs(m.g)))
             for name, inner, prec in runs:
                 o = mdp.mdp_default_opts()
                 o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.inner, o.precision = 0.9999, 1e-8, 1e-4, 30, inner, prec
@@ -497,6 +580,9 @@ def run_pendulum():
                 out[tag + name] = {"s": dt, "status": st, "outer": stats.outer_iters, "inner": stats.inner_iters_total,
                                    "final_residual": stats.final_residual,
                                    "policy_value_bytes": stats.policy_value_bytes}
+                Vh, pih = V.cpu().numpy(), pi.cpu().numpy()
+                out[tag + name]["error"] = error_statement(Vh, pih, stats.final_residual, 0.9999, 4, gnorm, ref)
+                ref = ref or (Vh, pih)
     return out
 
 
@@ -661,8 +747,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--reference-div", type=int, default=CPU_SAMPLE_DIV,
-                    help="the CPU oracle solves the workload's generator at S / this and scales the time back")
+    ap.add_argument("--cpu-oracle-worker", default=None, metavar="NPZ",
+                    help=argparse.SUPPRESS)  # child process: one timed oracle solve, V and pi saved to NPZ
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quantized", dest="quantized", action="store_false",
                     help="skip the binary16-exact variant of the workload")
@@ -685,9 +771,13 @@ def main():
                     help="profiling aid: W + K solves of the workload at this precision (no bench line)")
     ap.add_argument("--serve-stream", type=int, default=0, metavar="N",
                     help="only the full serving stream of N requests (no bench line)")
+    ap.add_argument("--stream", type=int, default=10000, metavar="N",
+                    help="requests of the full serving stream added to the line (0: skip)")
     ap.add_argument("--small-only", action="store_true",
                     help="only the small-workload stream vs graph measurement (no bench line)")
     args = ap.parse_args()
+    if args.cpu_oracle_worker:
+        return run_cpu_oracle_worker(args)
     if args.serve_stream:
         import torch
         from paper_2507_22538_gb300.build import build
@@ -709,13 +799,22 @@ def main():
     if args.inner_only:
         return run_inner_only(args)
 
+    world, rank, local = dist_env()
+    oracle_child, oracle_npz = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle on the same workload, timed on one host core in a child process
+        # started before any GPU call, while the GPU measurements below proceed
+        fd, oracle_npz = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        oracle_child = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-oracle-worker",
+                                         oracle_npz], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+
     import numpy as np
     import torch
 
     from mdpgen import banded_birth_death
     from paper_2507_22538_gb300 import mdp
 
-    world, rank, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
@@ -774,6 +873,9 @@ def main():
         dist.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     clocks = clk.summary()
+    V64, pi64 = V.cpu().numpy().copy(), pi.cpu().numpy().copy()
+    s64_res = s["final_residual"]
+    gnorm = float(np.max(np.abs(m.g)))
 
     # the same solves without per-sweep event timing, stream-driven and as one CUDA graph each
     graph_cmp = {}
@@ -813,6 +915,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     mixed_ms = e0.elapsed_time(e1) / args.steps
+    Vmx, pimx = V.cpu().numpy().copy(), pi.cpu().numpy().copy()
+    mixed_res = s["final_residual"]
 
     # the quantised variant of the workload (binomial band rounded to multiples of 2^-11 so
     # that every probability is exact in binary16): FP64 path vs mixed path with binary16
@@ -830,6 +934,7 @@ def main():
             return stats.as_dict()
 
         quant = {}
+        qref = None
         for name, o in (("f64", opts), ("mixed", mopts)):
             for _ in range(args.warmup):
                 qstep(o)
@@ -844,6 +949,10 @@ def main():
             quant[name] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "outer": its[-1][0],
                            "inner": its[-1][1], "policy_value_bytes": its[-1][2],
                            "max_final_residual": max(i[3] for i in its)}
+            Vq, piq = V.cpu().numpy().copy(), pi.cpu().numpy().copy()
+            quant[name]["error"] = error_statement(Vq, piq, its[-1][3], GAMMA, K_ROW, float(np.max(np.abs(mq.g))),
+                                                   qref)
+            qref = qref or (Vq, piq)
         quant["speedup_mixed_vs_f64"] = quant["f64"]["ms_per_step"] / quant["mixed"]["ms_per_step"]
         Mq.close()
         # end to end from pinned host buffers with the values in binary16 (exact for this MDP)
@@ -954,7 +1063,8 @@ def main():
              "outer_per_step": mtot["outer_iters"] / args.steps, "inner_per_step": mtot["inner_iters_total"] / args.steps,
              "inner_ms_per_step": mtot["inner_ms"] / args.steps,
              "inner_GBps": mtot["inner_bytes"] / (mtot["inner_ms"] * 1e-3) / 1e9 if mtot["inner_ms"] > 0 else None,
-             "max_final_residual": mtot["final_residual"], "gpu_launches": int(mtot["kernel_launches"])}
+             "max_final_residual": mtot["final_residual"], "gpu_launches": int(mtot["kernel_launches"]),
+             "error": error_statement(Vmx, pimx, mixed_res, GAMMA, K_ROW, gnorm, (V64, pi64))}
 
     line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -977,11 +1087,30 @@ def main():
         line["bandwidth_stress"] = run_stress()
     if args.pendulum:
         line["pendulum"] = run_pendulum()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, info = cpu_oracle_solve()
-        line["cpu_baseline"] = {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
-                                "sample": f"FP64 oracle Algorithm 1 on the S={S // CPU_SAMPLE_DIV} instance of the "
-                                          f"same generator, wall time x{CPU_SAMPLE_DIV}; {info}"}
+    if args.stream > 0 and world == 1:
+        line["serving_stream"] = run_serving_stream(args.stream)
+    line["iterations"]["error"] = error_statement(V64, pi64, s64_res, GAMMA, K_ROW, gnorm)
+    if oracle_child is not None:
+        out, err = oracle_child.communicate()
+        try:
+            rec = json.loads(out.strip().splitlines()[-1])
+            ov = np.load(oracle_npz)
+            V_or, pi_or = ov["V"], ov["pi"]
+            line["cpu_baseline"] = {
+                "value": rec["seconds"], "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": ("the whole workload: one FP64 numpy/scipy oracle solve (Algorithm 1, MGS-GMRES(30)) of the "
+                           f"same S={S} instance, gamma, tol and alpha, no scaling; run on one host core in a child "
+                           f"process alongside the GPU measurements; {rec['info']}"),
+                "nproc": rec["nproc"], "cpu_model": rec["cpu_model"]}
+            line["iterations"]["error"].update(error_statement(V64, pi64, s64_res, GAMMA, K_ROW, gnorm,
+                                                               (V_or, pi_or), "oracle"))
+            line["mixed_precision"]["error"].update(error_statement(Vmx, pimx, mixed_res, GAMMA, K_ROW, gnorm,
+                                                                    (V_or, pi_or), "oracle"))
+        except (ValueError, IndexError, KeyError, OSError) as e:
+            line["cpu_baseline"] = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                                    "sample": f"oracle child failed: {e}; {err[-400:]}"}
+        finally:
+            os.unlink(oracle_npz)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
