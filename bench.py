@@ -247,7 +247,7 @@ def cpu_info():
     return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
 
 
-def cpu_oracle_solve(save_v=None):
+def cpu_oracle_solve(save_v=None, states=S):
     """Time the FP64 oracle's Algorithm 1 on the bench workload itself (S = 1e6, same
     generator, gamma, tol, alpha and GMRES(30)): numpy/scipy with one thread (its
     sparse products are single-threaded scipy; BLAS is pinned to one thread above).
@@ -256,7 +256,7 @@ def cpu_oracle_solve(save_v=None):
     import numpy as np
     from mdpgen import banded_birth_death
     from oracle import mdp_oracle as O
-    m = banded_birth_death(S, A, H, GAMMA)
+    m = banded_birth_death(states, A, H, GAMMA)
     t0 = time.perf_counter()
     r = O.ipi(m.S, m.A, m.row_ptr, m.col, m.val, m.g, m.gamma, tol=TOL, alpha=ALPHA, inner="gmres",
               restart=RESTART)
@@ -288,22 +288,23 @@ def run_reference(args):
         return 0
     times, info = [], None
     t_start = time.perf_counter()
+    states = args.reference_states or S
     while len(times) < max(1, args.steps):
-        t, info = cpu_oracle_solve()
+        t, info = cpu_oracle_solve(states=states)
         times.append(t)
         if time.perf_counter() - t_start + t > REFERENCE_BUDGET_S:
             break
     v = statistics.median(times)
     host = cpu_info()
     sample = (f"FP64 numpy/scipy oracle, Algorithm 1 with MGS-GMRES(30), on the bench workload itself "
-              f"(S={S}, same generator, gamma, tol, alpha), {len(times)} solve(s) timed of {args.steps} requested "
+              f"(S={states}, same generator, gamma, tol, alpha), {len(times)} solve(s) timed of {args.steps} requested "
               f"(one solve takes ~{v:.0f} s; the arm stops after {REFERENCE_BUDGET_S:.0f} s), no warm-up; "
               f"one thread on a {host['nproc']}-core {host['cpu_model']} host; last run {info}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
             "steps": len(times), "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(),
+            "config": dict(workload_config(), S=states, nnz=states * A * K_ROW),
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
                              "runs_s": times, **host},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -747,6 +748,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--reference-states", type=int, default=0, metavar="S",
+                    help="test aid for --impl reference: solve the workload's generator at S states instead of "
+                         "1e6 (the line's config names the size)")
     ap.add_argument("--cpu-oracle-worker", default=None, metavar="NPZ",
                     help=argparse.SUPPRESS)  # child process: one timed oracle solve, V and pi saved to NPZ
     ap.add_argument("--no-cpu-baseline", action="store_true")

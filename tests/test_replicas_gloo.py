@@ -58,9 +58,10 @@ def test_reference_arm_prints_on_rank0_only(rank, tmp_path):
         assert r.returncode == 0 and r.stdout.strip() == ""
         return
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--reference-div", "1000"], env=env, capture_output=True, text=True,
+                        "--warmup", "0", "--reference-states", "1000"], env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["unit"] == "s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"]["S"] == 1000 and line["steps"] == 1 and line["cpu_baseline"]["nproc"] >= 1
