@@ -106,6 +106,15 @@ def summary_value(name, key, sha_key, sha):
         return None
 
 
+def lowp_bytes(S_, A_, k_):
+    """Algorithmic bytes of one low-precision sweep (generic-CSR accounting): 16-bit
+    value (2) + column (4) per entry, row pointer (8) and cost (8) per row, V read once,
+    TV and pi written.  The binary64 re-evaluation of the candidate rows re-reads them
+    while they are still in L2 and is not counted."""
+    R = S_ * A_
+    return R * k_ * 6 + R * 16 + S_ * 20
+
+
 def matvec_bytes():
     """Algorithmic bytes of one FP64 Arnoldi mat-vec w = sigma (u - gamma P_pi u): the
     policy's rows (8 B value + 4 B column per entry), u read once, w written."""
@@ -600,7 +609,7 @@ def run_bellman_only(args):
     if args.workload == "random":
         from mdpgen.torch_gen import random_sparse_device
         return run_bellman_only_random(args, random_sparse_device, random_value_vector)
-    m = banded_birth_death(args.states, A, H, GAMMA)
+    m = banded_birth_death(args.states, A, H, GAMMA, quant_bits=args.quant_bits or None)
     stream = torch.cuda.current_stream()
     with mdp.MDP.from_data(m, stream) as M:
         st_t, tile_states, _ = mdp.mdp_tune(M.h, GAMMA, stream)
@@ -608,9 +617,19 @@ def run_bellman_only(args):
         V = torch.from_numpy(random_value_vector(m.S, 1, 1000.0)).cuda()
         TV = torch.empty_like(V)
         pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms_lowp = None
+        if args.quant_bits:  # the certified low-precision sweep on the binary16-exact variant
+            for _ in range(2):
+                mdp.check(mdp.mdp_bellman_lowp(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman_lowp")
+            e0.record(stream)
+            for _ in range(args.bellman_only):
+                mdp.check(mdp.mdp_bellman_lowp(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman_lowp")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_lowp = e0.elapsed_time(e1) / args.bellman_only
         for _ in range(2):
             mdp.check(mdp.mdp_bellman(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman")
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.bellman_only):
             mdp.check(mdp.mdp_bellman(M.h, GAMMA, V, TV, pi, None, stream), "mdp_bellman")
@@ -631,10 +650,14 @@ def run_bellman_only(args):
     # gather: read pi and the S chosen rows (12 B per entry) and g; write the rows and g_pi
     gather_bytes = m.S * (4 + 8 + 8) + 2 * m.S * K_ROW * 12
     peak, _ = load_peaks()
-    print(json.dumps({"mode": "bellman_only", "S": m.S, "ms_per_sweep": ms, "bytes": nbytes,
-                      "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
-                      "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes,
-                      "tile_states": tile_states}), flush=True)
+    out = {"mode": "bellman_only", "S": m.S, "ms_per_sweep": ms, "bytes": nbytes,
+           "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
+           "ms_per_gather_and_apply": ms_pa, "gather_bytes": gather_bytes, "tile_states": tile_states}
+    if ms_lowp:
+        lb = lowp_bytes(m.S, A, K_ROW)
+        out["lowp"] = {"ms_per_sweep": ms_lowp, "bytes": lb, "GB/s": lb / ms_lowp / 1e6,
+                       "frac": lb / ms_lowp / 1e6 / peak}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -653,21 +676,27 @@ def run_bellman_only_random(args, random_sparse_device, random_value_vector):
         V = torch.from_numpy(random_value_vector(Sx, 1, 100.0)).cuda()
         TV = torch.empty_like(V)
         pi = torch.empty(Sx, dtype=torch.int32, device="cuda")
-        for _ in range(2):
-            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.bellman_only):
-            mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.bellman_only
+        times = {}
+        for name, fn in (("f64", mdp.mdp_bellman), ("lowp", mdp.mdp_bellman_lowp)):
+            for _ in range(2):
+                mdp.check(fn(M.h, gx, V, TV, pi, None, stream), name)
+            e0.record(stream)
+            for _ in range(args.bellman_only):
+                mdp.check(fn(M.h, gx, V, TV, pi, None, stream), name)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / args.bellman_only
+        ms = times["f64"]
     R = Sx * Ax
     nbytes = R * Kx * 12 + R * 16 + Sx * 20
+    lb = lowp_bytes(Sx, Ax, Kx)
     peak, _ = load_peaks()
     print(json.dumps({"mode": "bellman_only", "workload": "random", "S": Sx, "A": Ax, "k": Kx, "ms_per_sweep": ms,
                       "bytes": nbytes, "GB/s": nbytes / ms / 1e6, "frac": nbytes / ms / 1e6 / peak,
-                      "gathers_per_s": R * Kx / (ms * 1e-3), "tile_states": tile_states}), flush=True)
+                      "gathers_per_s": R * Kx / (ms * 1e-3), "tile_states": tile_states,
+                      "lowp": {"ms_per_sweep": times["lowp"], "bytes": lb, "GB/s": lb / times["lowp"] / 1e6,
+                               "frac": lb / times["lowp"] / 1e6 / peak}}), flush=True)
     return 0
 
 
@@ -767,6 +796,9 @@ def main():
     ap.add_argument("--workload", choices=["banded", "random"], default="banded",
                     help="with --bellman-only: the banded workload, or the random bandwidth-stress generator "
                          "(A = 32, k = 32) at --states states")
+    ap.add_argument("--quant-bits", type=int, default=0,
+                    help="with --bellman-only on the banded workload: round the band to multiples of 2^-this "
+                         "(11: exact in binary16) and also time the certified low-precision sweep")
     ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only/--solve-only: number of states")
     ap.add_argument("--inner-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: ITERS GMRES(30) iterations of mdp_policy_eval on the rows of action 0 "

@@ -87,6 +87,12 @@ typedef struct {
                               instantiated graph stays in the handle and is rebuilt when V, pi,
                               gamma, the options or the Bellman launch shape change.  Ignored by
                               mdp_solve_batch.                                                    (0) */
+  int32_t lowp_sweep;      /* nonzero: when every probability of the MDP is exact in binary16 or
+                              bfloat16, run the Bellman sweeps as mdp_bellman_lowp does (16-bit
+                              values, binary32 screen, binary64 re-evaluation of the rows that can
+                              attain the minimum); V, pi, the iteration counts and the stop test are
+                              bit for bit those of the binary64 sweep.  Otherwise ignored.  Ignored
+                              by mdp_solve_batch.                                                 (0) */
 } mdp_solve_opts;
 
 /* Statistics of one mdp_solve call (host struct filled by the library). */
@@ -117,6 +123,9 @@ typedef struct {
                                  projection) of the same steps (record_timing only) */
   double gs_flops;            /* their FP64 flops: 2 (2 (j + 1) + 1) S for step j */
   int64_t gs_timed;           /* Gram-Schmidt pairs timed in gs_ms */
+  int32_t bellman_value_bytes; /* bytes per probability the sweeps read: 8, or 2 with lowp_sweep */
+  int64_t bellman_rows_fp64;  /* with lowp_sweep: rows the sweeps re-evaluated in binary64 (at least
+                                 one per state and sweep: the rows that can attain the minimum) */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */
@@ -170,6 +179,26 @@ mdp_status mdp_get_info(mdp_handle h, int64_t* S, int32_t* A, int64_t* nnz);
  */
 mdp_status mdp_bellman(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
                        double* residual_inf, void* stream);
+
+/*
+ * mdp_bellman_lowp -- mdp_bellman for an MDP whose probabilities are all exact in
+ * binary16 or bfloat16 (multiples of 2^-11 or 2^-8 summing to 1 per row, the
+ * exact-dyadic inputs of the mixed-precision path; checked at mdp_create), with
+ * the same outputs bit for bit and fewer bytes moved.  The sweep (Eq. 3-4,
+ * Algorithm 1 steps 2-3) reads the stacked matrix as 16-bit values, screens every
+ * row in binary32 against a rigorous rounding bound, and re-evaluates in binary64,
+ * exactly as mdp_bellman does, every row that can attain the minimum (all rows of
+ * a state whose screen is not finite); the min / lowest argmin / residual is then
+ * mdp_bellman's own.  The first call on a handle builds the 16-bit copy of the
+ * values (2 B per stored entry) and binary32 copies of g and V, which the handle
+ * keeps.  The paper computes the greedy step in binary64 only (PETSc); this is the
+ * same result computed with less memory traffic.
+ *
+ *  Arguments as for mdp_bellman.  MDP_ERR_INVALID_ARG when the probabilities are
+ *  not exact in 16 bits.  Stream-ordered: returns without waiting for the kernel.
+ */
+mdp_status mdp_bellman_lowp(mdp_handle h, double gamma, const double* V, double* TV, int32_t* pi,
+                            double* residual_inf, void* stream);
 
 /*
  * mdp_policy_apply -- y = J_pi x = x - gamma * P_pi x, the matrix-free policy

@@ -182,7 +182,7 @@ struct GraphKey {
   const void* basis;
   const void* basis32;
   double gamma, atol, alpha;
-  int max_pi, max_ksp, m, refine, precision, tile, blocks, pstore;
+  int max_pi, max_ksp, m, refine, precision, tile, blocks, pstore, lowp, lp_ts, lp_blocks;
 };
 
 struct GraphCache {
@@ -292,7 +292,7 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
   // outer body: the sweep and the stop tests, then IF (go) the evaluation
   cudaGraphNode_t n_sweep, n_if;
   MDP_TRY(capture(h, cs, &seg, &nk[kSegSweep], [&]() -> mdp_status {
-    MDP_TRY(launch_bellman(h, gamma, V, h->TV, pi, cs));
+    MDP_TRY(launch_sweep(h, o->lowp_sweep != 0, gamma, V, h->TV, pi, cs));
     gs_outer_check_kernel<<<1, 256, 0, cs>>>(h->resmax, D, kSegSweep, K, o->atol_pi, o->alpha, o->max_iter_pi,
                                             o->max_iter_ksp, m, h->partial_stride, c_outer, c_go);
     return control_done();
@@ -403,6 +403,9 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   key.tile = h->bell_tile_states;
   key.blocks = h->bell_blocks;
   key.pstore = h->pstore;
+  key.lowp = (o->lowp_sweep && lowp_available(h)) ? 1 : 0;
+  key.lp_ts = h->lp_ts;
+  key.lp_blocks = h->lp_blocks;
   if (!c->valid || !same_key(c->key, key)) {
     drop_graph(c);
     const mdp_status s = build_graph(h, c, o, V, pi, mixed, st);

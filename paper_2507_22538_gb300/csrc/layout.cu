@@ -299,6 +299,10 @@ static void destroy_handle(mdp_s* h) {
   dfree(st, h->partials);
   dfree(st, h->sc);
   dfree(st, h->resmax);
+  dfree(st, h->P16);
+  dfree(st, h->g32);
+  dfree(st, h->vf32);
+  dfree(st, h->lp_rows);
   char* ks = (char*)h->kstate;
   dfree(st, ks);
   if (h->ev0) cudaEventDestroy(h->ev0);

@@ -124,6 +124,15 @@ struct mdp_s {
   double* sc = nullptr;      // device scalars [kScalarSlots]
   unsigned long long* resmax = nullptr;  // device max of |TV - V| bits
   cudaStream_t stream = nullptr;         // stream of mdp_create: device memory is allocated on it
+  // certified low-precision sweep (bellman_lowp.cu), set up on first use when the
+  // probabilities are exact in binary16 / bfloat16
+  uint16_t* P16 = nullptr;               // [P.nstored] 16-bit copy of P.val (same sliced layout)
+  float* g32 = nullptr;                  // [R] binary32 costs
+  float* vf32 = nullptr;                 // [S] binary32 copy of the sweep's V
+  unsigned long long* lp_rows = nullptr; // rows re-evaluated in binary64 (running count)
+  int lp_blocks = 0;                     // grid of the low-precision sweep
+  int lp_tile = 0;                       // states per tile it was shaped for (0: not yet)
+  int lp_ts = 0;                         // its own tile size (the Bellman tile, halved until it fits)
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   cudaEvent_t done = nullptr;  // recorded after the work of every call; mdp_destroy waits on it
@@ -158,6 +167,14 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
 // bellman.cu
 mdp_status configure_bellman(mdp_s* h);  // threads and grid of the Bellman sweep
 mdp_status launch_bellman(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi, cudaStream_t st);
+
+// bellman_lowp.cu: the certified low-precision sweep (bit for bit the results of launch_bellman)
+bool lowp_available(const mdp_s* h);          // probabilities exact in binary16 / bfloat16
+mdp_status prepare_lowp(mdp_s* h, cudaStream_t st);
+mdp_status launch_bellman_lowp(mdp_s* h, double gamma, const double* V, double* TV, int32_t* pi, cudaStream_t st);
+// the low-precision sweep when asked for and available, else the binary64 one
+mdp_status launch_sweep(mdp_s* h, bool lowp, double gamma, const double* V, double* TV, int32_t* pi,
+                        cudaStream_t st);
 
 // krylov.cu
 mdp_status launch_policy_apply(mdp_s* h, double gamma, const double* x, double* y, cudaStream_t st);

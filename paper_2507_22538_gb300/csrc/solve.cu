@@ -141,6 +141,11 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     mdp_status s0 = ensure_mixed(h, o->gmres_restart + 1);
     if (s0 != MDP_OK) return s0;
   }
+  const bool lowp = o->lowp_sweep && lowp_available(h);
+  if (lowp) {
+    MDP_TRY(prepare_lowp(h, st));
+    MDP_CUDA(cudaMemsetAsync(h->lp_rows, 0, sizeof(unsigned long long), st));
+  }
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
   const double ibytes0 = h->inner_bytes;
@@ -166,7 +171,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
     nvtxRangePushA("Bellman sweep and stop test");
     struct PopSweep { bool on = true; void pop() { if (on) nvtxRangePop(); on = false; } ~PopSweep() { pop(); } } sweep_range;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev0, st));
-    mdp_status s = launch_bellman(h, o->gamma, V, h->TV, pi, st);
+    mdp_status s = launch_sweep(h, lowp, o->gamma, V, h->TV, pi, st);
     if (s != MDP_OK) return s;
     if (o->record_timing) MDP_CUDA(cudaEventRecord(h->ev1, st));
     local.bellman_sweeps++;
@@ -224,6 +229,15 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   MDP_CUDA(cudaStreamSynchronize(st));
   }
   local.outer_iters = k;
+  local.bellman_value_bytes = lowp ? 2 : 8;
+  if (lowp) {
+    double* pin = tls_pinned();
+    MDP_CUDA(cudaMemcpyAsync(pin, h->lp_rows, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    MDP_CUDA(cudaStreamSynchronize(st));
+    unsigned long long rows = 0;
+    std::memcpy(&rows, pin, sizeof(rows));
+    local.bellman_rows_fp64 = (int64_t)rows;
+  }
   local.kernel_launches = h->launches - launches0;
   local.policy_matvecs = h->matvecs - matvecs0;
   local.vector_reads = h->vreads - vreads0;

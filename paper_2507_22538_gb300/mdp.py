@@ -43,7 +43,7 @@ class mdp_solve_opts(ctypes.Structure):
                 ("richardson_scale", ctypes.c_double), ("max_iter_pi", ctypes.c_int32),
                 ("max_iter_ksp", ctypes.c_int32), ("gmres_restart", ctypes.c_int32), ("inner", ctypes.c_int32),
                 ("record_timing", ctypes.c_int32), ("gmres_refine", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("graph", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("lowp_sweep", ctypes.c_int32)]
 
 
 class mdp_solve_stats(ctypes.Structure):
@@ -55,7 +55,8 @@ class mdp_solve_stats(ctypes.Structure):
                 ("vector_reads", ctypes.c_int64), ("vector_writes", ctypes.c_int64), ("inner_bytes", ctypes.c_double),
                 ("policy_value_bytes", ctypes.c_int32), ("matvec_ms", ctypes.c_double),
                 ("matvecs_timed", ctypes.c_int64), ("gs_ms", ctypes.c_double), ("gs_flops", ctypes.c_double),
-                ("gs_timed", ctypes.c_int64)]
+                ("gs_timed", ctypes.c_int64), ("bellman_value_bytes", ctypes.c_int32),
+                ("bellman_rows_fp64", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -72,6 +73,7 @@ _SIGNATURES = {
     "mdp_get_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int64)]),
     "mdp_bellman": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P, _P]),
+    "mdp_bellman_lowp": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P, _P]),
     "mdp_policy_apply": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, _P]),
     "mdp_policy_eval": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P, ctypes.c_int, ctypes.c_int32,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_int32,
@@ -180,6 +182,11 @@ def mdp_bellman(h, gamma, V, TV, pi, residual_inf=None, stream=None) -> int:
     return load().mdp_bellman(h, float(gamma), _ptr(V), _ptr(TV), _ptr(pi), _ptr(residual_inf), _stream(stream))
 
 
+def mdp_bellman_lowp(h, gamma, V, TV, pi, residual_inf=None, stream=None) -> int:
+    return load().mdp_bellman_lowp(h, float(gamma), _ptr(V), _ptr(TV), _ptr(pi), _ptr(residual_inf),
+                                   _stream(stream))
+
+
 def mdp_policy_apply(h, gamma, pi, x, y, stream=None) -> int:
     return load().mdp_policy_apply(h, float(gamma), _ptr(pi), _ptr(x), _ptr(y), _stream(stream))
 
@@ -274,6 +281,14 @@ class MDP:
         check(mdp_bellman(self.h, gamma, V, TV, pi, res, stream), "mdp_bellman")
         return TV, pi, res
 
+    def bellman_lowp(self, gamma, V, stream=None):
+        import torch
+        TV = torch.empty_like(V)
+        pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
+        res = torch.empty(1, dtype=torch.float64, device=V.device)
+        check(mdp_bellman_lowp(self.h, gamma, V, TV, pi, res, stream), "mdp_bellman_lowp")
+        return TV, pi, res
+
     def policy_apply(self, gamma, pi, x, stream=None):
         import torch
         y = torch.empty_like(x)
@@ -290,7 +305,7 @@ class MDP:
 
     def solve(self, gamma, V0=None, tol=1e-8, alpha=1e-4, inner=MDP_GMRES, restart=30, omega=1.0,
               max_outer=1000, max_inner=1000, record_timing=False, refine=MDP_REFINE_NEVER, precision=MDP_PREC_F64,
-              stream=None, device="cuda", graph=False):
+              stream=None, device="cuda", graph=False, lowp_sweep=False):
         import torch
         o = mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.richardson_scale = gamma, tol, alpha, omega
@@ -299,6 +314,7 @@ class MDP:
         o.gmres_refine = refine
         o.precision = precision
         o.graph = 1 if graph else 0
+        o.lowp_sweep = 1 if lowp_sweep else 0
         V = torch.zeros(self.S, dtype=torch.float64, device=device) if V0 is None else V0.clone()
         pi = torch.empty(self.S, dtype=torch.int32, device=V.device)
         st, stats = mdp_solve(self.h, o, V, pi, stream)

@@ -89,3 +89,19 @@ def test_stress_solve(stress, precision):
     qt = _tolerance(vals, gs, Vg)
     assert float(np.max(np.abs(tv - Vg[states]))) <= tol + qt
     check_policy(pg[states], Q, qt)
+
+
+def test_stress_lowp_sweep_bit_identical(stress):
+    """The full-size workload through the certified low-precision sweep (binary16 values,
+    binary32 screen, binary64 re-evaluation of the candidate rows): TV, policy and
+    residual bit for bit those of the binary64 sweep, at a random V and at zero."""
+    import torch
+    M, col, val, g = stress
+    for V in (torch.from_numpy(random_value_vector(S, 17, 10.0)).cuda(),
+              torch.zeros(S, dtype=torch.float64, device="cuda")):
+        a = M.bellman(GAMMA, V)
+        b = M.bellman_lowp(GAMMA, V)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            assert torch.equal(x.view(torch.int32) if x.dtype == torch.int32 else x.view(torch.int64),
+                               y.view(torch.int32) if y.dtype == torch.int32 else y.view(torch.int64))
