@@ -490,6 +490,55 @@ def run_small(steps=20):
                          "outer": stats.outer_iters, "inner": stats.inner_iters_total,
                          "launches": stats.kernel_launches, "final_residual": stats.final_residual}
     out["speedup_graph"] = out["stream"]["ms"] / out["graph"]["ms"]
+    # the same problem solved inside one thread-block cluster (mdp_solve_small_batch, n = 1),
+    # and a batch of 256 such problems (seeds 1..256) in one call
+    with mdp.MDP.from_data(m, stream) as M:
+        V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+        pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+        o = mdp.mdp_default_opts()
+        o.gamma, o.atol_pi, o.alpha, o.gmres_restart = m.gamma, 1e-10, 1e-3, 30
+        times = []
+        for i in range(steps + 3):
+            V.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, status, stats = mdp.mdp_solve_small_batch([M.h], [o], [V], [pi], stream)
+            times.append(time.perf_counter() - t0)
+            mdp.check(st, "mdp_solve_small_batch")
+            mdp.check(status[0], "small batch member")
+        out["cluster"] = {"ms": statistics.median(times[3:]) * 1e3, "outer": stats[0].outer_iters,
+                          "inner": stats[0].inner_iters_total, "launches": stats[0].kernel_launches,
+                          "final_residual": stats[0].final_residual}
+    out["speedup_cluster_vs_graph"] = out["graph"]["ms"] / out["cluster"]["ms"]
+    nb = 256
+    ms_b = [random_sparse(1000, 4, 8, 0.9, seed=i + 1) for i in range(nb)]
+    Ms = [mdp.MDP.from_data(x, stream) for x in ms_b]
+    try:
+        Vs = [torch.zeros(x.S, dtype=torch.float64, device="cuda") for x in ms_b]
+        ps = [torch.empty(x.S, dtype=torch.int32, device="cuda") for x in ms_b]
+        opts = []
+        for x in ms_b:
+            o = mdp.mdp_default_opts()
+            o.gamma, o.atol_pi, o.alpha, o.gmres_restart = x.gamma, 1e-10, 1e-3, 30
+            opts.append(o)
+        times = []
+        for i in range(4):
+            for v in Vs:
+                v.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, status, stats = mdp.mdp_solve_small_batch([M.h for M in Ms], opts, Vs, ps, stream)
+            times.append(time.perf_counter() - t0)
+            mdp.check(st, "mdp_solve_small_batch")
+            assert all(x == mdp.MDP_OK for x in status), status
+        tb = statistics.median(times[1:])
+        out["cluster_batch"] = {"problems": nb, "s": tb, "solves_per_s": nb / tb,
+                                "one_at_a_time_graph_solves_per_s": 1e3 / out["graph"]["ms"],
+                                "what": "256 random MDPs of the same shape (seeds 1..256) in one "
+                                        "mdp_solve_small_batch call, each on one 2-block cluster"}
+    finally:
+        for M in Ms:
+            M.close()
     return out
 
 

@@ -290,6 +290,38 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
                            int32_t* const* pi, mdp_solve_stats* stats, mdp_status* status, void* stream);
 
 /*
+ * mdp_solve_small_batch -- Algorithm 1 on n small MDPs, each solved from start to
+ * finish by one thread-block cluster (1 to 8 blocks, about 512 states per block),
+ * the whole batch in one kernel launch per cluster size, with no host round trip
+ * until every problem has stopped.  The sweep (Eq. 3-4), the stop tests, the
+ * policy's rows and GMRES(m) with classical Gram-Schmidt and Givens rotations (the
+ * method of mdp_solve) run inside the cluster; every reduction is a fixed-order
+ * block sum followed by a fixed-order sum over the cluster's blocks.  The paper
+ * solves one MDP per call with distributed PETSc kernels; this is the same method
+ * for many small problems, where one grid-wide kernel per Arnoldi pass would be
+ * bound by launch latency.
+ *
+ *  n        number of problems, >= 1.
+ *  handles  [n] distinct handles on the current device, each with S <= 65536.
+ *  opts     [n] options as for mdp_solve; inner MDP_GMRES, gmres_refine
+ *           MDP_REFINE_NEVER and precision MDP_PREC_F64 (graph, record_timing and
+ *           lowp_sweep are ignored).
+ *  V, pi    [n] device pointers: V[i] double[S_i] (in V_0, out V), pi[i] int32[S_i].
+ *  stats    [n] host structs (may be NULL): outer_iters, inner_iters_total,
+ *           final_residual, converged, bellman_sweeps; seconds and kernel_launches
+ *           are those of the whole batch.
+ *  status   [n] host: each problem's outcome (MDP_OK, MDP_NOT_CONVERGED, MDP_ERR_NUMERIC).
+ * Each problem's arithmetic depends on its own size only, so its V, pi and counts
+ * are the same bit for bit alone and in any batch.  They are certified like
+ * mdp_solve's results, but not bit-identical to them: the reductions add in a
+ * different order.  Blocks until every problem has stopped.  Returns MDP_OK when
+ * the batch ran, MDP_ERR_INVALID_ARG for a bad argument (nothing runs).
+ */
+mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles, const mdp_solve_opts* opts,
+                                 double* const* V, int32_t* const* pi, mdp_solve_stats* stats,
+                                 mdp_status* status, void* stream);
+
+/*
  * mdp_bellman_csr_noalloc -- the Bellman application of mdp_bellman (TV, greedy pi,
  * ||TV - V||_inf) computed straight from the caller's row-stacked CSR arrays,
  * with no handle and no device allocation.  The paper has no counterpart: it is

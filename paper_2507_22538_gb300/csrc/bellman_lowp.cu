@@ -240,7 +240,7 @@ static int vec_grid(const mdp_s* h, int64_t n) {
 bool lowp_available(const mdp_s* h) { return h->pstore == kStoreF16 || h->pstore == kStoreBF16; }
 
 // The 16-bit values, binary32 costs and V, the counter, and the launch shape for the
-// current tile size (set up on first use, reshaped when mdp_tune changes the tile).
+// current tile size (set up on first use, reshaped when mdp_tune changes a tile).
 static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
   if (!lowp_available(h))
     return fail(MDP_ERR_INVALID_ARG,
@@ -269,9 +269,11 @@ static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
     MDP_CUDA(cudaGetLastError());
     MDP_CUDA(cudaMemsetAsync(h->lp_rows, 0, sizeof(unsigned long long), st));
   }
-  if (h->lp_tile != h->bell_tile_states) {
-    int ts = h->bell_tile_states;  // the Bellman tile, halved until its 18 B per row fit
-    while (ts > 1 && lowp_smem_for(ts, h->A) > 227 * 1024) ts /= 2;
+  // the tile mdp_tune chose for this sweep, else the binary64 sweep's, halved until
+  // its 18 B per row fit in shared memory
+  int ts = h->lp_ts_tuned > 0 ? h->lp_ts_tuned : h->bell_tile_states;
+  while (ts > 1 && lowp_smem_for(ts, h->A) > 227 * 1024) ts /= 2;
+  if (h->lp_ts != ts) {
     h->lp_ts = ts;
     const size_t smem = lowp_smem(h);
     if (smem > 227 * 1024) return fail(MDP_ERR_INVALID_ARG, "low-precision sweep tile does not fit on an SM");
@@ -285,7 +287,6 @@ static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
     if (per_sm < 1) return fail(MDP_ERR_INVALID_ARG, "low-precision sweep tile does not fit on an SM");
     const int64_t ntiles = (h->S + ts - 1) / ts;
     h->lp_blocks = (int)std::min<int64_t>(ntiles, (int64_t)h->sm_count * per_sm);
-    h->lp_tile = h->bell_tile_states;
   }
   return MDP_OK;
 }

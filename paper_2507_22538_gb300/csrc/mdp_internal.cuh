@@ -131,8 +131,8 @@ struct mdp_s {
   float* vf32 = nullptr;                 // [S] binary32 copy of the sweep's V
   unsigned long long* lp_rows = nullptr; // rows re-evaluated in binary64 (running count)
   int lp_blocks = 0;                     // grid of the low-precision sweep
-  int lp_tile = 0;                       // states per tile it was shaped for (0: not yet)
-  int lp_ts = 0;                         // its own tile size (the Bellman tile, halved until it fits)
+  int lp_ts = 0;                         // its states per tile (0: not shaped yet)
+  int lp_ts_tuned = 0;                   // the tile mdp_tune chose for it (0: follow the Bellman tile)
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   cudaEvent_t done = nullptr;  // recorded after the work of every call; mdp_destroy waits on it

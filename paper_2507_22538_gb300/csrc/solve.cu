@@ -110,6 +110,39 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   }
   h->bell_tile_states = best;
   MDP_TRY(configure_bellman(h));
+  // the low-precision sweep has its own tile (18 B of shared memory per row, and a
+  // binary64 re-evaluation phase whose latency larger tiles amortise)
+  if (lowp_available(h)) {
+    auto time_lp = [&](float* ms) -> mdp_status {
+      MDP_TRY(launch_bellman_lowp(h, gamma, h->w, h->TV, h->piw, st));  // warm-up (and set-up)
+      MDP_CUDA(cudaEventRecord(h->ev0, st));
+      for (int r = 0; r < 3; ++r) MDP_TRY(launch_bellman_lowp(h, gamma, h->w, h->TV, h->piw, st));
+      MDP_CUDA(cudaEventRecord(h->ev1, st));
+      MDP_CUDA(cudaEventSynchronize(h->ev1));
+      MDP_CUDA(cudaEventElapsedTime(ms, h->ev0, h->ev1));
+      *ms /= 3.f;
+      return MDP_OK;
+    };
+    int best_lp = 0;
+    float best_lp_ms = 0.f;
+    for (int ts : kCandidates) {
+      if (ts > h->S || (size_t)ts * h->A * 18 + 16 > 227 * 1024) continue;
+      h->lp_ts_tuned = ts;
+      float ms = 0.f;
+      const mdp_status s = time_lp(&ms);
+      if (s != MDP_OK) {
+        if (s == MDP_ERR_INVALID_ARG) continue;  // the tile does not fit: skip it
+        h->lp_ts_tuned = best_lp;
+        return s;
+      }
+      if (best_lp == 0 || ms < 0.98f * best_lp_ms) {
+        best_lp = ts;
+        best_lp_ms = ms;
+      }
+    }
+    h->lp_ts_tuned = best_lp;
+    MDP_TRY(prepare_lowp(h, st));
+  }
   MDP_CUDA(cudaEventRecord(h->done, st));
   if (tile_states) *tile_states = best;
   if (ms_per_sweep) *ms_per_sweep = best_ms;

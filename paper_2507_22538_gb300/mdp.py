@@ -82,6 +82,9 @@ _SIGNATURES = {
     "mdp_solve_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_opts),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_stats),
                                        ctypes.POINTER(ctypes.c_int), _P]),
+    "mdp_solve_small_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_opts),
+                                             ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(mdp_solve_stats),
+                                             ctypes.POINTER(ctypes.c_int), _P]),
     "mdp_tune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
                                 _P]),
     "mdp_last_error": (ctypes.c_char_p, []),
@@ -230,6 +233,22 @@ def mdp_solve_batch(handles, opts, V, pi, stream=None):
     stats = (mdp_solve_stats * n)()
     status = (ctypes.c_int * n)()
     st = load().mdp_solve_batch(n, hs, os_, vs, ps, stats, status, _stream(stream))
+    return st, list(status), list(stats)
+
+
+def mdp_solve_small_batch(handles, opts, V, pi, stream=None):
+    """Solve len(handles) small MDPs, one thread-block cluster each, in one launch per
+    cluster size.  Same arguments and returns as mdp_solve_batch."""
+    n = len(handles)
+    if not (len(opts) == len(V) == len(pi) == n):
+        raise ValueError("handles, opts, V and pi must have the same length")
+    hs = (_P * n)(*handles)
+    os_ = (mdp_solve_opts * n)(*opts)
+    vs = (_P * n)(*[_ptr(v) for v in V])
+    ps = (_P * n)(*[_ptr(p) for p in pi])
+    stats = (mdp_solve_stats * n)()
+    status = (ctypes.c_int * n)()
+    st = load().mdp_solve_small_batch(n, hs, os_, vs, ps, stats, status, _stream(stream))
     return st, list(status), list(stats)
 
 
