@@ -582,10 +582,27 @@ def run_stress(sweeps=10):
         peak, _ = load_peaks()
         out["bellman"] = {"ms_per_sweep": ms, "bytes": nbytes, "GB/s": nbytes / ms / 1e6,
                           "frac": nbytes / ms / 1e6 / peak, "fp64_fma_per_s": R * Kx / (ms * 1e-3)}
+        # the certified low-precision sweep at the workload's stated precision (binary16 values,
+        # int32 columns): same outputs bit for bit
+        for _ in range(3):
+            mdp.check(mdp.mdp_bellman_lowp(M.h, gx, V, TV, pi, None, stream), "mdp_bellman_lowp")
+        e0.record(stream)
+        for _ in range(sweeps):
+            mdp.check(mdp.mdp_bellman_lowp(M.h, gx, V, TV, pi, None, stream), "mdp_bellman_lowp")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_l = e0.elapsed_time(e1) / sweeps
+        lb = lowp_bytes(Sx, Ax, Kx)
+        out["bellman_lowp"] = {"ms_per_sweep": ms_l, "bytes": lb, "GB/s": lb / ms_l / 1e6, "frac": lb / ms_l / 1e6 / peak,
+                               "l2_sectors_per_sweep": R * Kx, "gather_sector_GBps": R * Kx * 32 / ms_l / 1e6,
+                               "what": "binary16 values + int32 columns (the workload's stated storage); each "
+                                       "random V gather is its own 32-byte L2 sector"}
         ref = None
-        for name, prec in (("solve_f64", mdp.MDP_PREC_F64), ("solve_mixed", mdp.MDP_PREC_MIXED)):
+        for name, prec, lp in (("solve_f64", mdp.MDP_PREC_F64, 0), ("solve_mixed", mdp.MDP_PREC_MIXED, 0),
+                               ("solve_mixed_lowp_sweep", mdp.MDP_PREC_MIXED, 1)):
             o = mdp.mdp_default_opts()
             o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.precision = gx, 1e-8, 1e-4, 30, prec
+            o.lowp_sweep = lp
             for rep in range(2):  # the first call allocates the Krylov workspace
                 V.zero_()
                 torch.cuda.synchronize()
@@ -595,7 +612,8 @@ def run_stress(sweeps=10):
                 dt = time.perf_counter() - t0
             mdp.check(st, "mdp_solve")
             out[name] = {"s": dt, "outer": stats.outer_iters, "inner": stats.inner_iters_total,
-                         "final_residual": stats.final_residual, "policy_value_bytes": stats.policy_value_bytes}
+                         "final_residual": stats.final_residual, "policy_value_bytes": stats.policy_value_bytes,
+                         "sweep_value_bytes": stats.bellman_value_bytes}
             Vh, pih = V.cpu().numpy(), pi.cpu().numpy()
             # costs lie in [0, 1): |g| < 1
             out[name]["error"] = error_statement(Vh, pih, stats.final_residual, gx, Kx, 1.0, ref)
@@ -1020,25 +1038,44 @@ def main():
 
         quant = {}
         qref = None
-        for name, o in (("f64", opts), ("mixed", mopts)):
+        lopts, lmopts = mdp.mdp_default_opts(), mdp.mdp_default_opts()
+        for f, _ in mdp.mdp_solve_opts._fields_:
+            setattr(lopts, f, getattr(opts, f))
+            setattr(lmopts, f, getattr(mopts, f))
+        lopts.lowp_sweep = lmopts.lowp_sweep = 1  # the certified binary16 sweep (same results bit for bit)
+        for name, o in (("f64", opts), ("mixed", mopts), ("f64_lowp_sweep", lopts), ("mixed_lowp_sweep", lmopts)):
             for _ in range(args.warmup):
                 qstep(o)
             torch.cuda.synchronize()
             e0.record(stream)
             its = []
+            sw_ms, sw_n, rows64 = 0.0, 0, 0
             for _ in range(args.steps):
                 s = qstep(o)
                 its.append((s["outer_iters"], s["inner_iters_total"], s["policy_value_bytes"], s["final_residual"]))
+                sw_ms += s["bellman_ms"]
+                sw_n += s["bellman_sweeps"]
+                rows64 += s["bellman_rows_fp64"]
             e1.record(stream)
             torch.cuda.synchronize()
             quant[name] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "outer": its[-1][0],
                            "inner": its[-1][1], "policy_value_bytes": its[-1][2],
+                           "sweep_value_bytes": s["bellman_value_bytes"], "sweep_ms": sw_ms / max(1, sw_n),
                            "max_final_residual": max(i[3] for i in its)}
+            if o.lowp_sweep:
+                lb = lowp_bytes(S, A, K_ROW)
+                quant[name]["sweep_GBps"] = lb / (quant[name]["sweep_ms"] * 1e-3) / 1e9
+                quant[name]["sweep_frac"] = quant[name]["sweep_GBps"] / load_peaks()[0]
+                quant[name]["rows_fp64_per_state_and_sweep"] = rows64 / max(1, sw_n) / S
             Vq, piq = V.cpu().numpy().copy(), pi.cpu().numpy().copy()
             quant[name]["error"] = error_statement(Vq, piq, its[-1][3], GAMMA, K_ROW, float(np.max(np.abs(mq.g))),
                                                    qref)
             qref = qref or (Vq, piq)
         quant["speedup_mixed_vs_f64"] = quant["f64"]["ms_per_step"] / quant["mixed"]["ms_per_step"]
+        quant["speedup_mixed_lowp_sweep_vs_f64"] = (quant["f64"]["ms_per_step"] /
+                                                    quant["mixed_lowp_sweep"]["ms_per_step"])
+        quant["lowp_sweep_bit_identical"] = all(
+            quant[a]["error"].get("max_abs_diff_vs_fp64_gpu", 0.0) == 0.0 for a in ("f64_lowp_sweep",))
         Mq.close()
         # end to end from pinned host buffers with the values in binary16 (exact for this MDP)
         # against the same values in binary64: create + mixed solve + read back
@@ -1054,7 +1091,7 @@ def main():
                 st, hq = mdp.mdp_create(S, A, *host, False, stream)
                 mdp.check(st, "mdp_create")
                 V.zero_()
-                st, _ = mdp.mdp_solve(hq, mopts, V, pi, stream)
+                st, _ = mdp.mdp_solve(hq, lmopts, V, pi, stream)
                 mdp.check(st, "mdp_solve")
                 Vh_q = V.to("cpu", non_blocking=True)
                 pih_q = pi.to("cpu", non_blocking=True)

@@ -40,6 +40,7 @@ constexpr int kBsWarps = kBsThreads / 32;
 constexpr int kBsMaxCluster = 8;          // portable cluster size
 constexpr int kBsStatesPerBlock = 512;    // cluster size: enough blocks for about this many states each
 constexpr int64_t kBsMaxStates = 65536;
+constexpr int kBsSmemCap = 200 * 1024;    // dynamic shared memory for a block's share of the basis and w
 
 struct BsProblem {
   const double* val;
@@ -183,9 +184,10 @@ namespace {
 
 // Algorithm 1 on problem blockIdx.x / cluster size, by the blocks of one cluster.
 __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem* __restrict__ probs,
-                                                                 BsResult* __restrict__ results) {
+                                                                 BsResult* __restrict__ results, int smem_bytes) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ BsShared sh;
+  extern __shared__ double bs_dyn[];
   const int c = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const BsProblem P = probs[blockIdx.x / c];
   const int64_t S = P.S;
@@ -197,8 +199,14 @@ __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double* __restrict__ V = P.V;
   int32_t* __restrict__ pi = P.pi;
-  double* __restrict__ w = P.w;
-  double* __restrict__ U = P.basis;
+  double* __restrict__ U = P.basis;  // global basis: the mat-vec gathers u_j from it
+  // The block's own states of the basis and of w: in shared memory when (m + 2) vectors
+  // of its share fit (every access of the dots, projection and update is local), else
+  // the global arrays.  Same values and order either way, so the same results.
+  const bool local = (int64_t)(m + 2) * per * (int64_t)sizeof(double) <= (int64_t)smem_bytes;
+  double* const Ul = local ? bs_dyn : U;                  // u_i of state s at Ul[i * ust + s - uoff]
+  const int64_t ust = local ? per : S, uoff = local ? s_lo : 0;
+  double* const w = local ? bs_dyn + (int64_t)(m + 1) * per - s_lo : P.w;  // w[s] for s in [s_lo, s_hi)
   int buf = 0;
   int k = 0, sweeps = 0, status = MDP_OK;
   long long inner = 0;
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem
         const int64_t r = s * A + pi[s];
         const double x = P.g[r] - (V[s] - gamma * bs_row_dot(P, r, V));
         U[s] = x;
+        if (local) Ul[s - uoff] = x;
         nr = fma(x, x, nr);
       }
       __threadfence();
@@ -275,12 +284,13 @@ __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem
         // w = J v_j = sigma_j (u_j - gamma P_pi u_j)
         const double sj = sh.sigma[j];
         const double* uj = U + (int64_t)j * S;
+        const double* ujl = Ul + (int64_t)j * ust - uoff;
         for (int64_t s = s_lo + threadIdx.x; s < s_hi; s += kBsThreads)
-          w[s] = sj * (uj[s] - gamma * bs_row_dot(P, s * A + pi[s], uj));
+          w[s] = sj * (ujl[s] - gamma * bs_row_dot(P, s * A + pi[s], uj));
         __syncthreads();
         // h_i = v_i . w = sigma_i (u_i . w), i <= j: warp per vector, lanes over states
         for (int i = warp; i <= j; i += kBsWarps) {
-          const double* ui = U + (int64_t)i * S;
+          const double* ui = Ul + (int64_t)i * ust - uoff;
           double d = 0.0;
           for (int64_t s = s_lo + lane; s < s_hi; s += 32) d = fma(ui[s], w[s], d);
           for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
@@ -296,20 +306,23 @@ __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem
         __syncthreads();
         // u_{j+1} = w - sum_i coef_i u_i, and ||u_{j+1}||^2
         double* un = U + (int64_t)(j + 1) * S;
+        double* unl = Ul + (int64_t)(j + 1) * ust - uoff;
         double nn = 0.0;
         for (int64_t s = s_lo + threadIdx.x; s < s_hi; s += kBsThreads) {
           double x = w[s];
+          const double* b = Ul + (s - uoff);
           int i = 0;
           for (; i + 4 <= j + 1; i += 4) {
-            const double b0 = U[(int64_t)i * S + s], b1 = U[(int64_t)(i + 1) * S + s];
-            const double b2 = U[(int64_t)(i + 2) * S + s], b3 = U[(int64_t)(i + 3) * S + s];
+            const double b0 = b[(int64_t)i * ust], b1 = b[(int64_t)(i + 1) * ust];
+            const double b2 = b[(int64_t)(i + 2) * ust], b3 = b[(int64_t)(i + 3) * ust];
             x = fma(-sh.coef[i], b0, x);
             x = fma(-sh.coef[i + 1], b1, x);
             x = fma(-sh.coef[i + 2], b2, x);
             x = fma(-sh.coef[i + 3], b3, x);
           }
-          for (; i <= j; ++i) x = fma(-sh.coef[i], U[(int64_t)i * S + s], x);
+          for (; i <= j; ++i) x = fma(-sh.coef[i], b[(int64_t)i * ust], x);
           un[s] = x;
+          if (local) unl[s] = x;
           nn = fma(x, x, nn);
         }
         __threadfence();
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem
       __syncthreads();
       for (int64_t s = s_lo + threadIdx.x; s < s_hi; s += kBsThreads) {
         double t = 0.0;
-        for (int i = 0; i < n; ++i) t = fma(sh.coef[i], U[(int64_t)i * S + s], t);
+        for (int i = 0; i < n; ++i) t = fma(sh.coef[i], Ul[(int64_t)i * ust + (s - uoff)], t);
         V[s] += t;
       }
       __threadfence();
@@ -461,12 +474,27 @@ extern "C" mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles
   } release{st, dprobs, dres};
   MDP_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BsProblem) * n, cudaMemcpyHostToDevice, st));
   int launches = 0;
+  int sms = 0;
+  MDP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   for (int g = 0, c = 1, at = 0; g < 4; ++g, c *= 2) {
     if (!counts[g]) continue;
+    // A batch that leaves SMs free is latency-bound: each block then keeps its share of
+    // the basis and w in shared memory (one block per SM).  A larger batch keeps them
+    // in global memory, L2-resident, with several blocks per SM.  The results are the
+    // same either way.
+    int smem = 0;
+    if ((int64_t)counts[g] * c <= 2 * (int64_t)sms) {
+      for (int t = at; t < at + counts[g]; ++t) {
+        const int64_t per = (probs[t].S + c - 1) / c;
+        const int64_t need = (int64_t)(probs[t].m + 2) * per * (int64_t)sizeof(double);
+        if (need <= kBsSmemCap) smem = std::max(smem, (int)need);
+      }
+      if (smem > 0) MDP_TRY(raise_dyn_smem((const void*)block_solve_kernel, (size_t)smem));
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(counts[g] * c));
     cfg.blockDim = dim3(kBsThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -477,7 +505,7 @@ extern "C" mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles
     cfg.numAttrs = 1;
     const BsProblem* pp = dprobs + at;
     BsResult* rr = dres + at;
-    MDP_CUDA(cudaLaunchKernelEx(&cfg, block_solve_kernel, pp, rr));
+    MDP_CUDA(cudaLaunchKernelEx(&cfg, block_solve_kernel, pp, rr, smem));
     ++launches;
     at += counts[g];
   }
