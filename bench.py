@@ -395,6 +395,7 @@ def run_serving(n, slots=4, seed=5):
                              "max_dV": float(np.max(np.abs(a.V - b.V))) if a.V.shape == b.V.shape and a.V.size else None})
     same = not mism
     nnz = np.array([r.data.nnz for r in reqs], dtype=np.float64)
+    small = run_small_burst(slots=slots, seed=seed)
     return {"requests": n, "slots": slots, "hbm_budget_GB": 120, "arrival_rate_per_s": rate,
             "mix": "S log-uniform 1e3..1e6, A 2..32, k 4..64, gamma in {0.9,0.99,0.999,0.9999}, Dirichlet(1), "
                    "GMRES(30), alpha 1e-3, tol 1e-8; drawn on the device at admission (counted in the latency)",
@@ -404,17 +405,53 @@ def run_serving(n, slots=4, seed=5):
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same),
             "statuses_alone": {int(k): int(v) for k, v in zip(*np.unique([a.status for a in alone], return_counts=True))},
-            "mismatches": mism[:8], "n_mismatches": len(mism)}
+            "mismatches": mism[:8], "n_mismatches": len(mism), "small_burst": small}
 
 
-def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01):
+SMALL_MIX = dict(SERVE_MIX, s_range=(1_000, 4_096))
+
+
+def run_small_burst(n=512, slots=4, seed=5, small_states=4096):
+    """A burst of n small requests (the serving mix with S log-uniform in [1e3, 4096])
+    arriving at once: one request per solve on the grid path, against the service
+    gathering the pending small requests into mdp_solve_small_batch calls (one
+    thread-block cluster per request).  A seeded sample is compared with the same
+    request solved alone with the same routing."""
+    import numpy as np
+
+    from paper_2507_22538_gb300.serve import Request, SolveService, latency_summary, solve_alone
+    reqs = [Request(i, DeviceRequest(i, seed + 1000, **SMALL_MIX), tol=1e-8, alpha=1e-3) for i in range(n)]
+    out = {"requests": n, "mix": "the serving mix with S log-uniform in [1e3, 4096], all arriving at once"}
+    for tag, ss in (("grid_one_per_solve", 0), ("cluster_batched", small_states)):
+        for r in reqs[:3]:
+            solve_alone(r, small_states=ss)  # warm-up
+        svc = SolveService(slots=slots, hbm_budget=120 << 30, small_states=ss).start()
+        for r in reqs:
+            svc.submit(r)
+        res = svc.wait(n)
+        svc.close()
+        summ = latency_summary(res)
+        summ["mean_batch"] = float(np.mean(svc.batches))
+        sample = np.random.default_rng(seed).choice(n, size=16, replace=False)
+        summ["equal_alone"] = all(
+            np.array_equal(solve_alone(reqs[i], small_states=ss).V, res[int(i)].V) for i in sample)
+        summ["statuses"] = {int(k): int(v) for k, v in zip(*np.unique([x.status for x in res.values()],
+                                                                       return_counts=True))}
+        out[tag] = summ
+    out["speedup_solves_per_s"] = out["cluster_batched"]["solves_per_s"] / out["grid_one_per_solve"]["solves_per_s"]
+    return out
+
+
+def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01, small_states=4096):
     """The full serving stream: n requests of the counter-based mix (S log-uniform in
     [1e3, 1e6], A in [2, 32], k in [4, 64], gamma in {0.9, 0.99, 0.999, 0.9999}, drawn
     on the device at admission) under Poisson arrivals at 0.8 of the one-at-a-time
-    rate measured on the first `calib` requests, admitted by a 120 GB budget into
-    `slots` concurrent solves.  Results of the calibration requests and of a seeded
-    sample of verify_frac of the rest are compared bit for bit with the same
-    request solved alone."""
+    rate of plain FP64 solves measured on the first `calib` requests, admitted by a
+    120 GB budget into `slots` concurrent solves; pending requests of at most
+    small_states states are gathered into cluster-solver launches
+    (mdp_solve_small_batch).  Results of the calibration requests and of a seeded
+    sample of verify_frac of the rest are compared bit for bit with the same request
+    solved alone with the same routing."""
     import numpy as np
 
     from mdpgen.cuda_gen import load as load_gen
@@ -432,7 +469,8 @@ def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01):
     sample = [int(i) for i in rng.choice(np.arange(calib, n), size=max(1, int(verify_frac * (n - calib))),
                                          replace=False)] if n > calib else []
     checked = set(alone) | set(sample)
-    svc = SolveService(slots=slots, hbm_budget=120 << 30, keep=lambda rid: rid in checked).start()
+    svc = SolveService(slots=slots, hbm_budget=120 << 30, keep=lambda rid: rid in checked,
+                       small_states=small_states).start()
     t0 = svc.now()
     for r, a in zip(reqs, arrivals):
         wait = t0 + a - svc.now()
@@ -442,8 +480,14 @@ def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01):
     out = svc.wait(n, timeout=4 * 3600)
     svc.close()
     summ = latency_summary(out)
+    from paper_2507_22538_gb300.serve import is_small
+    n_small = sum(is_small(r, small_states) for r in reqs)
+    small_lat = [out[r.rid].latency for r in reqs if is_small(r, small_states)]
     for i in sample:
-        alone[i] = solve_alone(reqs[i])
+        alone[i] = solve_alone(reqs[i], small_states=small_states)
+    for i in list(alone):
+        if is_small(reqs[i], small_states):  # the calibration ran them on the grid path
+            alone[i] = solve_alone(reqs[i], small_states=small_states)
     mism = [rid for rid, a in alone.items()
             if not (a.status == out[rid].status and np.array_equal(a.V, out[rid].V) and np.array_equal(a.pi, out[rid].pi))]
     statuses = {int(k): int(v) for k, v in zip(*np.unique([r.status for r in out.values()], return_counts=True))}
@@ -454,6 +498,11 @@ def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01):
             "entries_per_request": {"mean": float(nnz.mean()), "max": float(nnz.max())},
             "calibration": {"requests": calib, "mean_solve_alone_s": float(service.mean())},
             "continuous": summ, "oom_retries": svc.oom_retries, "peak_in_flight": svc.peak_in_flight,
+            "small_route": {"small_states": small_states, "requests": n_small,
+                            "p50_s": float(np.percentile(small_lat, 50)) if small_lat else None,
+                            "p99_s": float(np.percentile(small_lat, 99)) if small_lat else None,
+                            "mean_batch_of_cluster_launches": float(np.mean([b for b in svc.batches if b > 1]))
+                            if any(b > 1 for b in svc.batches) else 1.0},
             "statuses": statuses, "verified_alone": len(alone), "mismatches": mism[:8], "n_mismatches": len(mism)}
 
 

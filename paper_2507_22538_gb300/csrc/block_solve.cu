@@ -183,8 +183,11 @@ namespace mdp {
 namespace {
 
 // Algorithm 1 on problem blockIdx.x / cluster size, by the blocks of one cluster.
-__global__ void __launch_bounds__(kBsThreads) block_solve_kernel(const BsProblem* __restrict__ probs,
-                                                                 BsResult* __restrict__ results, int smem_bytes) {
+// MINB: blocks per SM the register budget is sized for (1 with the basis in shared
+// memory, one block per SM anyway; 2 for the global-memory variant of large batches).
+template <int MINB>
+__global__ void __launch_bounds__(kBsThreads, MINB) block_solve_kernel(const BsProblem* __restrict__ probs,
+                                                                       BsResult* __restrict__ results, int smem_bytes) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ BsShared sh;
   extern __shared__ double bs_dyn[];
@@ -489,7 +492,7 @@ extern "C" mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles
         const int64_t need = (int64_t)(probs[t].m + 2) * per * (int64_t)sizeof(double);
         if (need <= kBsSmemCap) smem = std::max(smem, (int)need);
       }
-      if (smem > 0) MDP_TRY(raise_dyn_smem((const void*)block_solve_kernel, (size_t)smem));
+      if (smem > 0) MDP_TRY(raise_dyn_smem((const void*)block_solve_kernel<1>, (size_t)smem));
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(counts[g] * c));
@@ -505,7 +508,10 @@ extern "C" mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles
     cfg.numAttrs = 1;
     const BsProblem* pp = dprobs + at;
     BsResult* rr = dres + at;
-    MDP_CUDA(cudaLaunchKernelEx(&cfg, block_solve_kernel, pp, rr, smem));
+    if (smem > 0)
+      MDP_CUDA(cudaLaunchKernelEx(&cfg, block_solve_kernel<1>, pp, rr, smem));
+    else
+      MDP_CUDA(cudaLaunchKernelEx(&cfg, block_solve_kernel<2>, pp, rr, smem));
     ++launches;
     at += counts[g];
   }

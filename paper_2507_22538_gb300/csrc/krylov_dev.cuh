@@ -303,10 +303,34 @@ __device__ __forceinline__ void gm_matvec_body(int bid, int nb, const TP* __rest
 // NB accumulators.
 __host__ __device__ constexpr int pow2_up(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
-// The dots of exactly NA basis vectors with w over this block's states.
+// Two consecutive elements of a vector (16 bytes of binary64, 8 of binary32).
+template <typename T> struct Pair2;
+template <> struct Pair2<double> { using type = double2; };
+template <> struct Pair2<float> { using type = float2; };
+
+// The dots of exactly NA basis vectors with w over this block's states.  With S even
+// (every basis vector then starts on a 16-byte boundary) a thread takes two
+// consecutive states per step with one 16-byte load per vector: half the load
+// instructions and requests of one state per thread, which the strided streams of
+// the basis need to overlap with the FP64 pipe (a microbenchmark at 25 vectors:
+// 55 against 72 us, S = 1e6).
 template <int NA, int NP, typename T>
 __device__ __forceinline__ void dots_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
                                           const T* __restrict__ w, T (&d)[NP]) {
+  if ((S & 1) == 0) {
+    using T2 = typename Pair2<T>::type;
+    const int64_t S2 = S >> 1;
+    const T2* w2 = reinterpret_cast<const T2*>(w);
+    for (int64_t p = bid * (int64_t)blockDim.x + threadIdx.x; p < S2; p += (int64_t)nb * blockDim.x) {
+      const T2 ws = w2[p];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const T2 b = reinterpret_cast<const T2*>(basis + (int64_t)i * S)[p];
+        d[i] = fma(b.y, ws.y, fma(b.x, ws.x, d[i]));
+      }
+    }
+    return;
+  }
   for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
     const T ws = w[s];
 #pragma unroll
@@ -383,14 +407,34 @@ enum { kPlain = 0, kDgks = 1, kAlways = 2, kSecond = 3 };
 // registers) and the compiler takes up to 128 registers, two blocks per SM; a cap
 // of 64 (four blocks) trades a few spills for twice the warps and measured 4%
 // faster on the whole FP64 solve.
-constexpr int kProjectMinBlocks = 4;
+constexpr int kProjectMinBlocks = 3;
 
 // u = src - sum of exactly NA coefficient-scaled basis vectors over this block's
-// states; returns this thread's share of ||u||^2.
+// states; returns this thread's share of ||u||^2.  With S even, two consecutive
+// states per step as in dots_rows: two independent chains of fused multiply-adds
+// (each state's chain is the same as with one state per thread) and 16-byte loads
+// (a microbenchmark at 25 vectors: 53 against 100 us, S = 1e6).
 template <int NA, typename T>
 __device__ __forceinline__ T project_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
                                           const T* __restrict__ src, T* __restrict__ u, const T* c) {
   T uu = T(0);
+  if ((S & 1) == 0) {
+    using T2 = typename Pair2<T>::type;
+    const int64_t S2 = S >> 1;
+    for (int64_t p = bid * (int64_t)blockDim.x + threadIdx.x; p < S2; p += (int64_t)nb * blockDim.x) {
+      T2 x = reinterpret_cast<const T2*>(src)[p];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const T2 b = reinterpret_cast<const T2*>(basis + (int64_t)i * S)[p];
+        x.x = fma(-c[i], b.x, x.x);
+        x.y = fma(-c[i], b.y, x.y);
+      }
+      reinterpret_cast<T2*>(u)[p] = x;
+      uu = fma(x.x, x.x, uu);
+      uu = fma(x.y, x.y, uu);
+    }
+    return uu;
+  }
   for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
     T x = src[s];
 #pragma unroll

@@ -8,7 +8,11 @@ V and the policy back, so admitted requests overlap on the GPU while later
 ones wait.  With batch_max > 1 a worker takes, besides the first request that
 fits, later pending requests that also fit (any S, A, k and gamma; GMRES in
 FP64 or mixed precision) and solves them together with mdp_solve_batch: one launch per pass for
-all of them, each result bit for bit its stand-alone one.  The solver calls release the Python interpreter lock, so the
+all of them, each result bit for bit its stand-alone one.  With small_states > 0, requests of at most that
+many states (GMRES in FP64) are instead gathered with the other pending small ones, up to small_batch_max,
+and solved by mdp_solve_small_batch: one thread-block cluster per request, the whole batch in one launch
+(solve_alone routes such a request the same way, so each result is still bit for bit its stand-alone
+one).  The solver calls release the Python interpreter lock, so the
 workers' host threads run concurrently.  All computation happens in libmdp's
 kernels; this module only schedules.
 """
@@ -93,13 +97,15 @@ class SolveService:
     """A fixed pool of worker slots with an HBM admission budget."""
 
     def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0, batch_max: int = 1,
-                 keep=None):
+                 keep=None, small_states: int = 0, small_batch_max: int = 256):
         """keep: optional predicate on a request id; results of other requests drop V and
         the policy (status, iteration counts and latency stay), to bound host memory on
         long streams."""
         import torch
         self.slots = slots
         self.batch_max = max(1, int(batch_max))
+        self.small_states = int(small_states)
+        self.small_batch_max = max(1, int(small_batch_max))
         self.keep = keep
         self.budget = int(hbm_budget)
         self.device = device
@@ -163,6 +169,9 @@ class SolveService:
     def _batchable(r: Request) -> bool:
         return r.inner == mdp.MDP_GMRES and r.precision in (mdp.MDP_PREC_F64, mdp.MDP_PREC_MIXED)
 
+    def _small(self, r: Request) -> bool:
+        return is_small(r, self.small_states)
+
     def _admit(self):
         """First pending request (arrival order) that fits the free budget, plus (with
         batch_max > 1) later pending requests that still fit, when all of them run
@@ -172,7 +181,15 @@ class SolveService:
             if need <= self._free:
                 batch = [r]
                 total = need
-                if self.batch_max > 1 and self._batchable(r):
+                if self._small(r):  # small requests go together to the cluster solver
+                    for r2 in self._pending[i + 1:]:
+                        if len(batch) == self.small_batch_max:
+                            break
+                        n2 = device_bytes(r2.data, r2.restart, r2.precision)
+                        if self._small(r2) and total + n2 <= self._free:
+                            batch.append(r2)
+                            total += n2
+                elif self.batch_max > 1 and self._batchable(r):
                     for r2 in self._pending[i + 1:]:
                         if len(batch) == self.batch_max:
                             break
@@ -204,7 +221,12 @@ class SolveService:
             admitted = self.now()
             retry = False
             try:
-                outs = [self._solve(batch[0], stream)] if len(batch) == 1 else self._solve_batch(batch, stream)
+                if self._small(batch[0]):
+                    outs = self._solve_small(batch, stream)
+                elif len(batch) == 1:
+                    outs = [self._solve(batch[0], stream)]
+                else:
+                    outs = self._solve_batch(batch, stream)
             except Exception as exc:  # failed requests still complete, with their status
                 status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
                 oom = isinstance(exc, torch.cuda.OutOfMemoryError) or status == mdp.MDP_ERR_OOM
@@ -293,11 +315,52 @@ class SolveService:
                 for i, r in enumerate(batch)]
 
 
-def solve_alone(req: Request) -> Result:
-    """The same request on the current stream with nothing else running."""
+    @staticmethod
+    def _solve_small(batch, stream) -> list:
+        import torch
+        handles = []
+        with torch.cuda.stream(stream):
+            try:
+                for r in batch:
+                    st, h = _create(r.data, stream)
+                    mdp.check(st, f"mdp_create (request {r.rid})")
+                    handles.append(h)
+                opts = []
+                for r in batch:
+                    o = mdp.mdp_default_opts()
+                    o.gamma, o.atol_pi, o.alpha, o.inner = r.data.gamma, r.tol, r.alpha, r.inner
+                    o.gmres_restart, o.precision = r.restart, r.precision
+                    opts.append(o)
+                V = [torch.zeros(r.data.S, dtype=torch.float64, device="cuda") for r in batch]
+                pi = [torch.empty(r.data.S, dtype=torch.int32, device="cuda") for r in batch]
+                st, status, stats = mdp.mdp_solve_small_batch(handles, opts, V, pi, stream)
+                mdp.check(st, "mdp_solve_small_batch")
+                Vh = [v.cpu() for v in V]  # on this stream: ordered after the solve
+                pih = [p.cpu() for p in pi]
+            finally:
+                for h in handles:
+                    mdp.mdp_destroy(h)
+        return [Result(r.rid, status[i], Vh[i].numpy(), pih[i].numpy(), stats[i].outer_iters,
+                       int(stats[i].inner_iters_total), stats[i].final_residual, r.arrival, 0.0, 0.0)
+                for i, r in enumerate(batch)]
+
+
+def is_small(r: Request, small_states: int) -> bool:
+    """Whether the cluster solver takes the request: at most small_states (and 65,536) states,
+    GMRES in FP64."""
+    return (0 < int(r.data.S) <= min(small_states, 65536) and r.inner == mdp.MDP_GMRES
+            and r.precision == mdp.MDP_PREC_F64)
+
+
+def solve_alone(req: Request, small_states: int = 0) -> Result:
+    """The same request on the current stream with nothing else running (routed to the
+    cluster solver, as a service with the same small_states would, when it is small)."""
     import torch
     t0 = time.perf_counter()
-    res = SolveService._solve(req, torch.cuda.current_stream())
+    if is_small(req, small_states):
+        res = SolveService._solve_small([req], torch.cuda.current_stream())[0]
+    else:
+        res = SolveService._solve(req, torch.cuda.current_stream())
     res.finished = time.perf_counter() - t0
     return res
 

@@ -189,3 +189,35 @@ def test_out_of_memory_is_retried_while_others_run():
     out = lone.wait(1)
     lone.close()
     assert out[2].status == mdp.MDP_ERR_OOM and lone.oom_retries == 0
+
+
+def test_small_requests_go_to_the_cluster_solver():
+    """With small_states set, pending requests of at most that many states are solved
+    together by mdp_solve_small_batch (one cluster each); larger ones take the grid
+    path.  Every result equals the request solved alone with the same routing, bit for
+    bit, and every small one is certified by the oracle."""
+    from paper_2507_22538_gb300 import mdp
+    from paper_2507_22538_gb300.serve import Request, SolveService, is_small, solve_alone
+    from tests._util import check_policy, q_tolerance
+    reqs = [Request(i, serving_request(i, seed=31, **MIX), tol=1e-8, alpha=1e-3) for i in range(24)]
+    small = 4096
+    assert 0 < sum(is_small(r, small) for r in reqs) < len(reqs)
+    alone = {r.rid: solve_alone(r, small_states=small) for r in reqs}
+    svc = SolveService(slots=2, small_states=small).start()
+    for r in reqs:
+        svc.submit(r)
+    res = svc.wait(len(reqs))
+    svc.close()
+    assert max(svc.batches) > 1  # small requests shared a launch
+    for r in reqs:
+        a, b = alone[r.rid], res[r.rid]
+        assert a.status == mdp.MDP_OK and b.status == mdp.MDP_OK
+        assert np.array_equal(a.V, b.V) and np.array_equal(a.pi, b.pi)
+        assert a.outer_iters == b.outer_iters and a.inner_iters == b.inner_iters
+        if is_small(r, small):
+            m = r.data
+            P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+            Q = O.q_values(P, m.g, m.gamma, b.V, m.S, m.A)
+            qt = q_tolerance(m, b.V)
+            assert float(np.max(np.abs(Q.min(axis=1) - b.V))) <= 1e-8 + qt
+            check_policy(b.pi, Q, qt)
