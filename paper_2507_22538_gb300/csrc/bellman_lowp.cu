@@ -36,9 +36,10 @@
 namespace mdp {
 
 constexpr int kLowpMaxRowLen = 16382;
-// Shared memory per row of a tile: bounds lo, hi (binary32), the binary64 Q of the
-// candidate rows, and the candidate list (row index within the tile, < 2^16).
-constexpr int kLowpSmemPerRow = 4 + 4 + 8 + 2;
+// Shared memory per row of a tile: 8 bytes that hold the row's bounds (lo, hi in
+// binary32) until its state's candidates are chosen and its binary64 Q after that,
+// and the candidate list (row index within the tile, < 2^16).
+constexpr int kLowpSmemPerRow = 8 + 2;
 
 __device__ __forceinline__ float lp_to_float(__half v) { return __half2float(v); }
 __device__ __forceinline__ float lp_to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
@@ -115,10 +116,9 @@ __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_ker
   __shared__ double red[32];
   __shared__ int ncand;
   const int nr = TS * A;
-  double* qd = lp_smem;                                           // [nr] binary64 Q of candidate rows
-  float* lo = reinterpret_cast<float*>(qd + nr);                  // [nr]
-  float* hi = lo + nr;                                            // [nr]
-  uint16_t* list = reinterpret_cast<uint16_t*>(hi + nr);          // [nr]
+  double* qd = lp_smem;                                           // [nr] binary64 Q (phases 2-4)
+  float2* lohi = reinterpret_cast<float2*>(lp_smem);              // [nr] the same bytes: bounds (phases 1-2)
+  uint16_t* list = reinterpret_cast<uint16_t*>(qd + nr);          // [nr]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   double dmax = 0.0;
   unsigned long long cand_total = 0;
@@ -142,8 +142,8 @@ __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_ker
         const float qt = fmaf(gammaf, acc, gq);
         const float e = gammaf * ((float)(n + 4) * 0x1p-23f) * mag + 0x1p-22f * (fabsf(qt) + fabsf(gq)) + 0x1p-120f;
         const bool ok = n <= kLowpMaxRowLen && isfinite(qt) && isfinite(e);
-        lo[r - r0] = ok ? qt - e : __int_as_float(0x7fc00000);
-        hi[r - r0] = ok ? qt + e : __int_as_float(0x7fc00000);
+        const float nan = __int_as_float(0x7fc00000);
+        lohi[r - r0] = ok ? make_float2(qt - e, qt + e) : make_float2(nan, nan);
       }
     }
     __syncthreads();
@@ -153,13 +153,14 @@ __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_ker
       bool all = false;
       float U = __int_as_float(0x7f800000);
       for (int a = 0; a < A; ++a) {
-        const float l = lo[b + a];
-        all |= (l != l);
-        U = fminf(U, hi[b + a]);
+        const float2 bnd = lohi[b + a];
+        all |= (bnd.x != bnd.x);
+        U = fminf(U, bnd.y);
       }
       for (int a = 0; a < A; ++a) {
+        const bool cand = all || lohi[b + a].x <= U;  // read this row's bounds before its Q overwrites them
         qd[b + a] = __longlong_as_double(0x7ff0000000000000LL);  // +inf: never the minimum
-        if (all || lo[b + a] <= U) list[atomicAdd(&ncand, 1)] = (uint16_t)(b + a);
+        if (cand) list[atomicAdd(&ncand, 1)] = (uint16_t)(b + a);
       }
     }
     __syncthreads();
@@ -270,7 +271,7 @@ static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
     MDP_CUDA(cudaMemsetAsync(h->lp_rows, 0, sizeof(unsigned long long), st));
   }
   // the tile mdp_tune chose for this sweep, else the binary64 sweep's, halved until
-  // its 18 B per row fit in shared memory
+  // its 10 B per row fit in shared memory
   int ts = h->lp_ts_tuned > 0 ? h->lp_ts_tuned : h->bell_tile_states;
   while (ts > 1 && lowp_smem_for(ts, h->A) > 227 * 1024) ts /= 2;
   if (h->lp_ts != ts) {

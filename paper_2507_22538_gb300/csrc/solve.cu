@@ -110,7 +110,7 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   }
   h->bell_tile_states = best;
   MDP_TRY(configure_bellman(h));
-  // the low-precision sweep has its own tile (18 B of shared memory per row, and a
+  // the low-precision sweep has its own tile (10 B of shared memory per row, and a
   // binary64 re-evaluation phase whose latency larger tiles amortise)
   if (lowp_available(h)) {
     auto time_lp = [&](float* ms) -> mdp_status {
@@ -126,7 +126,7 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
     int best_lp = 0;
     float best_lp_ms = 0.f;
     for (int ts : kCandidates) {
-      if (ts > h->S || (size_t)ts * h->A * 18 + 16 > 227 * 1024) continue;
+      if (ts > h->S || (size_t)ts * h->A * 10 + 16 > 227 * 1024) continue;
       h->lp_ts_tuned = ts;
       float ms = 0.f;
       const mdp_status s = time_lp(&ms);

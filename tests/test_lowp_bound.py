@@ -1,0 +1,66 @@
+"""The rounding bound of the certified low-precision sweep (mdp_bellman_lowp) against
+exact rational arithmetic, on the CPU.
+
+The sweep screens each row in binary32, q~ = fl32(gamma_f * sum_j p_j Vf_j + g_f) with
+Vf = fl32(V), and claims |q~ - Q| <= e with
+    e = gamma_f (n + 4) 2^-23 M + 2^-22 (|q~| + |g_f|) + 2^-120,  M = fl32(sum_j p_j |Vf_j|),
+where Q is the row's exact value g + gamma sum_j p_j V_j (the binary64 sweep's value is
+within 2^-50 |Q| of it).  Here the screen is emulated in numpy binary32 without fused
+multiply-adds (two roundings per step, a larger error than the kernel's one), and the
+exact value comes from fractions.Fraction; the bound must hold for every row, and with
+the 1.9x margin its derivation keeps for the kernel's own rounding.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from mdpgen import quantize_rows
+
+
+def _screen(p, V, g, gamma):
+    f32 = np.float32
+    gf, Vf, g32 = f32(gamma), V.astype(np.float32), f32(g)
+    acc, mag = f32(0.0), f32(0.0)
+    for pj, vj in zip(p.astype(np.float32), Vf):
+        acc = f32(acc + f32(pj * vj))
+        mag = f32(mag + f32(pj * abs(vj)))
+    q = f32(f32(gf * acc) + g32)
+    n = len(p)
+    e = float(gf) * (n + 4) * 2.0 ** -23 * float(mag) + 2.0 ** -22 * (abs(float(q)) + abs(float(g32))) + 2.0 ** -120
+    return float(q), e
+
+
+@pytest.mark.parametrize("scale", [1e-40, 1e-3, 1.0, 1e3, 1e8, 1e30])
+def test_lowp_bound_covers_the_exact_row_value(scale):
+    rng = np.random.default_rng(int(abs(np.log10(scale))) + 7)
+    worst = 0.0
+    for _ in range(150):
+        n = int(rng.integers(1, 100))
+        w = rng.random(n) + 1e-3
+        p = quantize_rows(w[None, :], 11)[0]  # exact in binary16 (reading C8)
+        V = (rng.random(n) * 2 - 1) * scale * (1 + rng.random(n) * 1e3)
+        g = float(rng.random() * 3 - 1) * max(scale, 1.0)
+        gamma = float(rng.choice([0.5, 0.9, 0.99, 0.999999]))
+        q, e = _screen(p, V, g, gamma)
+        exact = Fraction(g) + Fraction(gamma) * sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(p, V))
+        err = abs(Fraction(q) - exact)
+        assert err <= Fraction(e), (n, scale, float(err), e)
+        worst = max(worst, float(err) / e)
+    assert worst < 1.0
+
+
+def test_lowp_bound_fails_when_planted_too_tight():
+    """A bound without the magnitude term (a plausible mistake) is violated on these
+    rows: the test above would catch it."""
+    rng = np.random.default_rng(3)
+    violated = 0
+    for _ in range(200):
+        n = int(rng.integers(8, 64))
+        p = quantize_rows((rng.random(n) + 1e-3)[None, :], 11)[0]
+        V = (rng.random(n) * 2 - 1) * 1e3
+        q, e = _screen(p, V, 0.25, 0.99)
+        tight = 2.0 ** -22 * (abs(q) + 0.25)
+        exact = Fraction(0.25) + Fraction(0.99) * sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(p, V))
+        violated += abs(Fraction(q) - exact) > Fraction(tight)
+    assert violated > 0
