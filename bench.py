@@ -825,7 +825,7 @@ def run_solve_only(args):
     from paper_2507_22538_gb300 import mdp
     from paper_2507_22538_gb300.build import build
     build()
-    m = banded_birth_death(args.states, A, H, GAMMA)
+    m = banded_birth_death(args.states, A, H, GAMMA, quant_bits=args.quant_bits or None)
     stream = torch.cuda.current_stream()
     prec = mdp.MDP_PREC_MIXED if args.solve_only == "mixed" else mdp.MDP_PREC_F64
     with mdp.MDP.from_data(m, stream) as M:
@@ -834,6 +834,7 @@ def run_solve_only(args):
         pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
         o = mdp.mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.inner, o.precision = GAMMA, TOL, ALPHA, RESTART, mdp.MDP_GMRES, prec
+        o.lowp_sweep = 1 if args.quant_bits else 0  # the binary16-exact variant runs the certified binary16 sweep
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         for i in range(args.warmup + args.steps):
@@ -913,8 +914,9 @@ def main():
                     help="with --bellman-only: the banded workload, or the random bandwidth-stress generator "
                          "(A = 32, k = 32) at --states states")
     ap.add_argument("--quant-bits", type=int, default=0,
-                    help="with --bellman-only on the banded workload: round the band to multiples of 2^-this "
-                         "(11: exact in binary16) and also time the certified low-precision sweep")
+                    help="with --bellman-only or --solve-only on the banded workload: round the band to multiples of "
+                         "2^-this (11: exact in binary16) and also time (bellman-only) or use (solve-only) the "
+                         "certified low-precision sweep")
     ap.add_argument("--states", type=int, default=S, help="with --bellman-only/--inner-only/--solve-only: number of states")
     ap.add_argument("--inner-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: ITERS GMRES(30) iterations of mdp_policy_eval on the rows of action 0 "
