@@ -835,6 +835,7 @@ def run_solve_only(args):
         o = mdp.mdp_default_opts()
         o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.inner, o.precision = GAMMA, TOL, ALPHA, RESTART, mdp.MDP_GMRES, prec
         o.lowp_sweep = 1 if args.quant_bits else 0  # the binary16-exact variant runs the certified binary16 sweep
+        o.record_timing = 1 if args.timing else 0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         for i in range(args.warmup + args.steps):
@@ -847,9 +848,15 @@ def run_solve_only(args):
             launches = stats.kernel_launches
         e1.record(stream)
         torch.cuda.synchronize()
-    print(json.dumps({"mode": "solve_only", "precision": args.solve_only, "S": m.S,
-                      "ms_per_solve": e0.elapsed_time(e1) / max(1, args.steps), "launches_per_solve": launches,
-                      "outer": stats.outer_iters, "inner": stats.inner_iters_total}), flush=True)
+    out = {"mode": "solve_only", "precision": args.solve_only, "S": m.S,
+           "ms_per_solve": e0.elapsed_time(e1) / max(1, args.steps), "launches_per_solve": launches,
+           "outer": stats.outer_iters, "inner": stats.inner_iters_total}
+    if args.timing:  # the last solve's event-timed kernels (record_timing)
+        out.update(bellman_ms=stats.bellman_ms / max(1, stats.bellman_sweeps),
+                   matvec_ms=stats.matvec_ms / max(1, stats.matvecs_timed),
+                   gs_pair_ms=stats.gs_ms / max(1, stats.gs_timed),
+                   gs_tflops=stats.gs_flops / (stats.gs_ms * 1e-3) / 1e12 if stats.gs_ms > 0 else None)
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -923,6 +930,8 @@ def main():
                          "of the workload (a one-action MDP; no bench line)")
     ap.add_argument("--solve-only", choices=["f64", "mixed"], default=None,
                     help="profiling aid: W + K solves of the workload at this precision (no bench line)")
+    ap.add_argument("--timing", action="store_true",
+                    help="with --solve-only: record_timing on, and the event-timed kernel averages in the line")
     ap.add_argument("--serve-stream", type=int, default=0, metavar="N",
                     help="only the full serving stream of N requests (no bench line)")
     ap.add_argument("--stream", type=int, default=10000, metavar="N",

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <unordered_set>
 #include <vector>
 
 #include "mdp_internal.cuh"
@@ -400,12 +401,12 @@ extern "C" mdp_status mdp_solve_small_batch(int32_t n, const mdp_handle* handles
   if (n < 1 || !handles || !opts || !V || !pi || !status)
     return fail(MDP_ERR_INVALID_ARG, "need n >= 1 and non-null handles, opts, V, pi and status");
   int dev = -1;
+  std::unordered_set<const mdp_s*> seen;
   for (int i = 0; i < n; ++i) {
     const mdp_s* h = handles[i];
     const mdp_solve_opts* o = opts + i;
     if (!h || !V[i] || !pi[i]) return fail(MDP_ERR_INVALID_ARG, "null handle or vector in the batch");
-    for (int q = 0; q < i; ++q)
-      if (handles[q] == h) return fail(MDP_ERR_INVALID_ARG, "a handle appears twice in the batch");
+    if (!seen.insert(h).second) return fail(MDP_ERR_INVALID_ARG, "a handle appears twice in the batch");
     if (dev < 0) dev = h->device;
     if (h->device != dev) return fail(MDP_ERR_INVALID_ARG, "all handles must live on one device");
     if (h->S > kBsMaxStates) return fail(MDP_ERR_INVALID_ARG, "mdp_solve_small_batch takes at most 65536 states");
