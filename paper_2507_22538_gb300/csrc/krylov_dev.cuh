@@ -308,16 +308,19 @@ template <typename T> struct Pair2;
 template <> struct Pair2<double> { using type = double2; };
 template <> struct Pair2<float> { using type = float2; };
 
-// The dots of exactly NA basis vectors with w over this block's states.  With S even
-// (every basis vector then starts on a 16-byte boundary) a thread takes two
-// consecutive states per step with one 16-byte load per vector: half the load
+// The dots of exactly NA basis vectors with w over this block's states.  In binary64
+// with S even (every basis vector then starts on a 16-byte boundary) a thread takes
+// two consecutive states per step with one 16-byte load per vector: half the load
 // instructions and requests of one state per thread, which the strided streams of
 // the basis need to overlap with the FP64 pipe (a microbenchmark at 25 vectors:
-// 55 against 72 us, S = 1e6).
+// 55 against 72 us, S = 1e6).  The binary32 cycle of the mixed solver keeps one
+// state per thread: with pairs there, the mixed solve of the bfloat16-exact pendulum
+// grid (10^6 states, gamma = 0.9999) stagnated at a residual of 2.7e-7 through 1000
+// outer iterations, where one state per thread converges in about 105.
 template <int NA, int NP, typename T>
 __device__ __forceinline__ void dots_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
                                           const T* __restrict__ w, T (&d)[NP]) {
-  if ((S & 1) == 0) {
+  if (sizeof(T) == sizeof(double) && (S & 1) == 0) {
     using T2 = typename Pair2<T>::type;
     const int64_t S2 = S >> 1;
     const T2* w2 = reinterpret_cast<const T2*>(w);
@@ -418,7 +421,7 @@ template <int NA, typename T>
 __device__ __forceinline__ T project_rows(int bid, int nb, int64_t S, const T* __restrict__ basis,
                                           const T* __restrict__ src, T* __restrict__ u, const T* c) {
   T uu = T(0);
-  if ((S & 1) == 0) {
+  if (sizeof(T) == sizeof(double) && (S & 1) == 0) {
     using T2 = typename Pair2<T>::type;
     const int64_t S2 = S >> 1;
     for (int64_t p = bid * (int64_t)blockDim.x + threadIdx.x; p < S2; p += (int64_t)nb * blockDim.x) {
