@@ -73,15 +73,15 @@ def bellman_source_sha():
 
 
 def krylov_source_sha():
-    """sha256 (first 16 hex digits) of the code that makes the GMRES mat-vec kernel:
-    sell.cuh and krylov_dev.cuh (the row layout and the kernel body) and the
+    """sha256 (first 16 hex digits) of the code that makes the fused GMRES mat-vec + dots
+    kernel: sell.cuh and krylov_dev.cuh (the row layout and the kernel body) and the
     kernel's own definition in krylov.cu (host code there does not change it)."""
     csrc = os.path.join(ROOT, "paper_2507_22538_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("sell.cuh", "krylov_dev.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     src = open(os.path.join(csrc, "krylov.cu"), "rb").read()
-    start = src.index(b"__global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(")
+    start = src.index(b"gm_matvec_dots_kernel(const double* __restrict__ pval,")
     start = src.rindex(b"template", 0, start)
     h.update(src[start:src.index(b"\n}\n", start) + 3])
     return h.hexdigest()[:16]
@@ -113,12 +113,6 @@ def lowp_bytes(S_, A_, k_):
     while they are still in L2 and is not counted."""
     R = S_ * A_
     return R * k_ * 6 + R * 16 + S_ * 20
-
-
-def matvec_bytes():
-    """Algorithmic bytes of one FP64 Arnoldi mat-vec w = sigma (u - gamma P_pi u): the
-    policy's rows (8 B value + 4 B column per entry), u read once, w written."""
-    return S * K_ROW * 12 + S * 16
 
 
 def sweep_traffic():
@@ -1031,7 +1025,8 @@ def main():
             ev.record(stream)
             marks.append(ev)
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
-                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed", "gs_ms", "gs_flops", "gs_timed"):
+                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed", "matvec_bytes", "gs_ms", "gs_flops",
+                        "gs_timed"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
@@ -1219,27 +1214,32 @@ def main():
                 "bytes_per_launch": bellman_bytes(), "avg_launch_ms": bell_ms,
                 "share_of_step": share_bell, "tile_states": tile_states}
     mv_ms = totals["matvec_ms"] / max(1, totals["matvecs_timed"])
-    mv_gbs = matvec_bytes() / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else None
-    roof_mv = {"bound": "hbm", "kernel": "gm_matvec_kernel (policy mat-vec of every FP64 Arnoldi step; the largest "
-                                         "share of the step among single kernels)",
+    mv_bytes = totals["matvec_bytes"] / max(1, totals["matvecs_timed"])
+    mv_gbs = mv_bytes / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else None
+    roof_mv = {"bound": "hbm", "kernel": "gm_matvec_dots_kernel (policy mat-vec of every FP64 Arnoldi step fused with "
+                                         "the classical Gram-Schmidt dots; the largest share of the step among single "
+                                         "kernels)",
                "achieved": mv_gbs, "peak": peak, "unit": "GB/s", "frac": mv_gbs / peak if mv_gbs else None,
                "peak_kind": roofline["peak_kind"],
-               "traffic": summary_value("gm_matvec_banded_s4e5.txt", "dram_bytes_per_launch", "krylov_src_sha256_16",
-                                        krylov_source_sha()),
-               "bytes_per_launch": matvec_bytes(), "avg_launch_ms": mv_ms,
+               "traffic": summary_value("gm_matvec_dots_banded_s4e5.txt", "dram_bytes_per_launch",
+                                        "krylov_src_sha256_16", krylov_source_sha()),
+               # the capture is of step j = 24 (rows + u_j + w + 24 basis vectors)
+               "traffic_step": 24, "traffic_step_algorithmic_bytes": S * K_ROW * 12 + S * 16 + 24 * S * 8,
+               # bytes of the sampled launches (steps j = 0, 8, 16, 24): rows + u_j + w + j basis vectors
+               "bytes_per_launch": mv_bytes, "avg_launch_ms": mv_ms,
                "launches_timed": int(totals["matvecs_timed"]),
-               # every Arnoldi step launches one mat-vec; the timed ones are a sample of them
+               # every Arnoldi step launches one of them; the timed ones are a sample
                "share_of_step": mv_ms * totals["inner_iters_total"] / (ms * args.steps)}
-    # FP64 single-pass classical Gram-Schmidt of the sampled steps: bound by the FP64 pipe
+    # the FP64 projection of the sampled steps (u_{j+1} = w - sum c_i u_i and ||u||^2): FP64-pipe bound
     gs_tflops = totals["gs_flops"] / (totals["gs_ms"] * 1e-3) / 1e12 if totals["gs_ms"] > 0 else None
     fp64_peak = FP64_PEAK_TFLOPS
-    roof_gs = {"bound": "alu", "kernel": "gm_dots_kernel + gm_project_kernel (FP64 single-pass classical "
-                                        "Gram-Schmidt of an Arnoldi step: 2 (j+1) + 1 FMA per state)",
+    roof_gs = {"bound": "alu", "kernel": "gm_project_kernel (FP64 classical Gram-Schmidt projection of an Arnoldi "
+                                        "step: j + 2 FMA per state; its dots run in the mat-vec kernel)",
                "achieved": gs_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                "frac": gs_tflops / fp64_peak if gs_tflops else None,
                "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-               "traffic": None, "pairs_timed": int(totals["gs_timed"]),
-               "avg_pair_ms": totals["gs_ms"] / max(1, totals["gs_timed"])}
+               "traffic": None, "launches_timed": int(totals["gs_timed"]),
+               "avg_launch_ms": totals["gs_ms"] / max(1, totals["gs_timed"])}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}

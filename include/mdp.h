@@ -117,15 +117,19 @@ typedef struct {
                                  probability of the MDP is exactly representable there) */
   double matvec_ms;           /* summed device time of the policy mat-vec kernels of GMRES steps
                                  j = 0, 8, 16, ... of every restart cycle, each between its own pair
-                                 of CUDA events (record_timing only; all mat-vecs do the same work) */
+                                 of CUDA events (record_timing only); in the FP64 single-pass solver the
+                                 mat-vec kernel also forms the Gram-Schmidt dots */
   int64_t matvecs_timed;      /* mat-vec kernels timed in matvec_ms */
-  double gs_ms;               /* summed device time of the FP64 single-pass Gram-Schmidt (dots and
-                                 projection) of the same steps (record_timing only) */
-  double gs_flops;            /* their FP64 flops: 2 (2 (j + 1) + 1) S for step j */
-  int64_t gs_timed;           /* Gram-Schmidt pairs timed in gs_ms */
+  double gs_ms;               /* summed device time of the FP64 single-pass Gram-Schmidt projection of
+                                 the same steps (record_timing only) */
+  double gs_flops;            /* its FP64 flops: 2 (j + 2) S for step j (j + 1 products and the norm) */
+  int64_t gs_timed;           /* projections timed in gs_ms */
   int32_t bellman_value_bytes; /* bytes per probability the sweeps read: 8, or 2 with lowp_sweep */
   int64_t bellman_rows_fp64;  /* with lowp_sweep: rows the sweeps re-evaluated in binary64 (at least
                                  one per state and sweep: the rows that can attain the minimum) */
+  double matvec_bytes;        /* algorithmic bytes of the kernels timed in matvec_ms: the policy's rows,
+                                 u_j read, w written, and with the fused FP64 dots the j other basis
+                                 vectors of step j (record_timing only) */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

@@ -68,7 +68,7 @@ struct BatchReport {
 
 // The pass kinds with their own block ranges.  FP64 passes give mixed problems no
 // blocks and the binary32 passes (suffix F) give FP64 problems none.
-enum : int { kRangeBellman = 0, kRangeExtract, kRangeResidual, kRangeMatvec, kRangeUpdate, kRangeDots0,
+enum : int { kRangeBellman = 0, kRangeExtract, kRangeResidual, kRangeUpdate, kRangeDots0,
              kRangeProject0 = kRangeDots0 + 8, kRangeResidualF = kRangeProject0 + 8, kRangeMatvecF, kRangeUpdateF,
              kRangeDotsF0, kRangeProjectF0 = kRangeDotsF0 + 8, kRanges = kRangeProjectF0 + 8 };
 
@@ -121,22 +121,18 @@ __global__ void __launch_bounds__(kVecThreads) bb_residual_kernel(const BatchPro
                                     p.partials, p.K);
 }
 
-__global__ void __launch_bounds__(kVecThreads) bb_matvec_kernel(const BatchProblem* __restrict__ P,
-                                                                 const int32_t* __restrict__ start, int n, int j) {
+// The binary64 mat-vec fused with the Gram-Schmidt dots, as the single-problem solver runs it.
+template <int NB>
+__global__ void __launch_bounds__(kVecThreads, mvd_min_blocks(NB)) bb_matvec_dots_kernel(const BatchProblem* __restrict__ P,
+                                                                       const int32_t* __restrict__ start, int n,
+                                                                       int j) {
   BATCH_PROLOGUE
   if (p.puniform)
-    gm_matvec_body<true, double, double>(bid, nb, p.pval, p.pcol, p.poff, p.plen, p.pkmax, p.S, p.gamma, p.basis, j,
-                                         p.w, p.K);
+    gm_matvec_dots_body<true, NB>(bid, nb, p.pval, p.pcol, p.poff, p.plen, p.pkmax, p.S, p.gamma, p.basis, j, p.w,
+                                  p.partials, p.K);
   else
-    gm_matvec_body<false, double, double>(bid, nb, p.pval, p.pcol, p.poff, p.plen, 0, p.S, p.gamma, p.basis, j, p.w,
-                                          p.K);
-}
-
-template <int NB>
-__global__ void __launch_bounds__(kVecThreads) bb_dots_kernel(const BatchProblem* __restrict__ P,
-                                                               const int32_t* __restrict__ start, int n, int j) {
-  BATCH_PROLOGUE
-  gm_dots_body<NB, double, true>(bid, nb, p.S, p.basis, j, p.w, p.partials, p.K);
+    gm_matvec_dots_body<false, NB>(bid, nb, p.pval, p.pcol, p.poff, p.plen, 0, p.S, p.gamma, p.basis, j, p.w,
+                                   p.partials, p.K);
 }
 
 template <int NB>
@@ -367,7 +363,7 @@ int blocks_for(const Item& it, int kind) {
   if (f != it.mixed) return 0;
   switch (kind) {
     case kRangeResidual: case kRangeResidualF: return gmres_grid(h, kPassResidual, 0, f);
-    case kRangeMatvec: case kRangeMatvecF: return gmres_grid(h, kPassMatvec, 0, f);
+    case kRangeMatvecF: return gmres_grid(h, kPassMatvec, 0, f);
     case kRangeUpdate: case kRangeUpdateF: return gmres_grid(h, kPassUpdate, 0, f);
     default: break;
   }
@@ -426,16 +422,15 @@ mdp_status report(BatchBuffers& B, int na, int krylov, int64_t* launches) {
   } while (0)
 
 mdp_status arnoldi_batch(BatchBuffers& B, int na, int j, int64_t& launches) {
-  BB_LAUNCH(bb_matvec_kernel, kRangeMatvec, j);
-  switch ((j + 4) / 4) {
-    case 1: BB_LAUNCH(bb_dots_kernel<4>, kRangeDots0 + 0, j); BB_LAUNCH(bb_project_kernel<4>, kRangeProject0 + 0, j); break;
-    case 2: BB_LAUNCH(bb_dots_kernel<8>, kRangeDots0 + 1, j); BB_LAUNCH(bb_project_kernel<8>, kRangeProject0 + 1, j); break;
-    case 3: BB_LAUNCH(bb_dots_kernel<12>, kRangeDots0 + 2, j); BB_LAUNCH(bb_project_kernel<12>, kRangeProject0 + 2, j); break;
-    case 4: BB_LAUNCH(bb_dots_kernel<16>, kRangeDots0 + 3, j); BB_LAUNCH(bb_project_kernel<16>, kRangeProject0 + 3, j); break;
-    case 5: BB_LAUNCH(bb_dots_kernel<20>, kRangeDots0 + 4, j); BB_LAUNCH(bb_project_kernel<20>, kRangeProject0 + 4, j); break;
-    case 6: BB_LAUNCH(bb_dots_kernel<24>, kRangeDots0 + 5, j); BB_LAUNCH(bb_project_kernel<24>, kRangeProject0 + 5, j); break;
-    case 7: BB_LAUNCH(bb_dots_kernel<28>, kRangeDots0 + 6, j); BB_LAUNCH(bb_project_kernel<28>, kRangeProject0 + 6, j); break;
-    default: BB_LAUNCH(bb_dots_kernel<32>, kRangeDots0 + 7, j); BB_LAUNCH(bb_project_kernel<32>, kRangeProject0 + 7, j); break;
+  switch ((j + 4) / 4) {  // the binary64 problems: mat-vec with the dots, then the projection
+    case 1: BB_LAUNCH(bb_matvec_dots_kernel<4>, kRangeDots0 + 0, j); BB_LAUNCH(bb_project_kernel<4>, kRangeProject0 + 0, j); break;
+    case 2: BB_LAUNCH(bb_matvec_dots_kernel<8>, kRangeDots0 + 1, j); BB_LAUNCH(bb_project_kernel<8>, kRangeProject0 + 1, j); break;
+    case 3: BB_LAUNCH(bb_matvec_dots_kernel<12>, kRangeDots0 + 2, j); BB_LAUNCH(bb_project_kernel<12>, kRangeProject0 + 2, j); break;
+    case 4: BB_LAUNCH(bb_matvec_dots_kernel<16>, kRangeDots0 + 3, j); BB_LAUNCH(bb_project_kernel<16>, kRangeProject0 + 3, j); break;
+    case 5: BB_LAUNCH(bb_matvec_dots_kernel<20>, kRangeDots0 + 4, j); BB_LAUNCH(bb_project_kernel<20>, kRangeProject0 + 4, j); break;
+    case 6: BB_LAUNCH(bb_matvec_dots_kernel<24>, kRangeDots0 + 5, j); BB_LAUNCH(bb_project_kernel<24>, kRangeProject0 + 5, j); break;
+    case 7: BB_LAUNCH(bb_matvec_dots_kernel<28>, kRangeDots0 + 6, j); BB_LAUNCH(bb_project_kernel<28>, kRangeProject0 + 6, j); break;
+    default: BB_LAUNCH(bb_matvec_dots_kernel<32>, kRangeDots0 + 7, j); BB_LAUNCH(bb_project_kernel<32>, kRangeProject0 + 7, j); break;
   }
   // the mixed problems' binary32 step at the widths of the single-problem mixed solver
   BB_LAUNCH(bb_matvec_f_kernel, kRangeMatvecF, j);

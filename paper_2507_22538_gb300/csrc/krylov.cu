@@ -79,6 +79,23 @@ __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T
   gm_dots_body<NB, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
+// The binary64 mat-vec fused with the dots (single-pass classical Gram-Schmidt): one
+// launch per step instead of two, and w not read back.  A microbenchmark of the two
+// against the fused kernel at S = 1e6 (13 and 25 basis vectors): 120 -> 101 us and
+// 144 -> 121 us.
+template <bool U, int NB>
+__global__ void __launch_bounds__(kVecThreads, mvd_min_blocks(NB)) gm_matvec_dots_kernel(const double* __restrict__ pval,
+                                                                       const int32_t* __restrict__ pcol,
+                                                                       const int64_t* __restrict__ poff,
+                                                                       const int32_t* __restrict__ plen, int k,
+                                                                       int64_t S, double gamma,
+                                                                       const double* __restrict__ basis, int j,
+                                                                       double* __restrict__ w, double* partials,
+                                                                       KrylovState* K) {
+  gm_matvec_dots_body<U, NB>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w,
+                             partials, K);
+}
+
 // The binary32 dots pass (mixed solver) at 4 blocks per SM (64 registers): measured
 // 110.9 -> 107.1 ms per mixed solve.  The FP64 pass keeps the compiler's choice
 // (80 registers, 3 blocks), faster there (147.8 against 150.3 ms at 4 blocks).
@@ -494,6 +511,19 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   KrylovState* K = kstate(h);
   const bool timed = h->timing && (j % kMatvecTimingStride) == 0;
   if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j], st));
+  if constexpr (FINE && sizeof(T) == sizeof(double)) {
+    // binary64, single pass: the mat-vec fused with the dots, then the projection
+    const Sell& Q = h->Ppi;
+    gm_matvec_dots_kernel<U, NB><<<MDP_WAVE((gm_matvec_dots_kernel<U, NB>)), kVecThreads, 0, st>>>(
+        Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, S, gamma, B.basis, j, B.w, h->partials, K);
+    MDP_LAUNCH_CHECK(h);
+    if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
+    gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
+        S, B.basis, j, B.w, h->partials, K);
+    MDP_LAUNCH_CHECK(h);
+    if (timed && h->gs_on) MDP_CUDA(cudaEventRecord(h->gs_ev[j], st));
+    return MDP_OK;
+  }
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
   if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
@@ -550,6 +580,20 @@ static int pass_grid(mdp_s* h, GmresPass pass, int NB) {
     case kPassUpdate:
       return MDP_WAVE(gm_update_kernel<T>);
     case kPassDots:
+      if (sizeof(T) == sizeof(double)) {  // binary64: the mat-vec fused with the dots
+        switch (NB) {
+#define MDP_MVD(nb) return U ? MDP_WAVE((gm_matvec_dots_kernel<true, nb>)) : MDP_WAVE((gm_matvec_dots_kernel<false, nb>))
+          case 4: MDP_MVD(4);
+          case 8: MDP_MVD(8);
+          case 12: MDP_MVD(12);
+          case 16: MDP_MVD(16);
+          case 20: MDP_MVD(20);
+          case 24: MDP_MVD(24);
+          case 28: MDP_MVD(28);
+          default: MDP_MVD(32);
+#undef MDP_MVD
+        }
+      }
       switch (NB) {
         case 4: return MDP_WAVE((dots_kernel<4, T, FINE_T>()));
         case 8: return MDP_WAVE((dots_kernel<8, T, FINE_T>()));
@@ -655,6 +699,12 @@ static void count_cycle(mdp_s* h, int steps) {
   add_vector_bytes(h, 1, sizeof(T));
 }
 
+// Bytes per probability the mat-vec of value type T reads.
+template <typename T>
+static size_t vbytes_of(const mdp_s* h) {
+  return sizeof(T) == sizeof(double) ? 8 : (h->pstore == kStoreF32 ? 4 : 2);
+}
+
 // record_timing: add the device time of the timed mat-vecs among the first n
 // steps of the cycle that just finished (their events completed before the host
 // read the solver state).  Every kMatvecTimingStride-th step of a cycle is timed:
@@ -664,16 +714,21 @@ static void count_cycle(mdp_s* h, int steps) {
 // The FP64 single-pass Gram-Schmidt of the same steps (dots, then projection) is
 // timed from the mat-vec's end event to one after the projection; it does
 // 2 (j + 1) + 1 FP64 FMAs per state (j + 1 dots, j + 1 projection terms, ||u||^2).
-static mdp_status add_matvec_times(mdp_s* h, int n) {
+static mdp_status add_matvec_times(mdp_s* h, int n, size_t value_bytes, size_t vec_bytes) {
+  const double S = (double)h->S, entries = S * (double)h->Ppi.kmax;
   for (int j = 0; j < n; j += kMatvecTimingStride) {
     float ms = 0.f;
     MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j], h->mv_ev[2 * j + 1]));
     h->mv_ms += ms;
     h->mv_timed += 1;
+    // algorithmic bytes of the timed launch: the policy's rows, u_j read and w written,
+    // and with the fused binary64 dots the j other basis vectors
+    h->mv_bytes += entries * (double)(value_bytes + 4) + 2.0 * S * (double)vec_bytes;
     if (h->gs_on) {
+      h->mv_bytes += (double)j * S * (double)vec_bytes;
       MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j + 1], h->gs_ev[j]));
       h->gs_ms += ms;
-      h->gs_flops += 2.0 * (double)(2 * (j + 1) + 1) * (double)h->S;
+      h->gs_flops += 2.0 * (double)(j + 2) * S;  // the projection: j + 1 products and ||u||^2
       h->gs_timed += 1;
     }
   }
@@ -710,7 +765,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
     if (r != MDP_OK) return r;
     if (hd.flags & kSolveDone) break;
     if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
-    if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before));
+    if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before, vbytes_of<T>(h), sizeof(T)));
     it_before = hd.it;
     const int steps = std::min(m, maxit - hd.it);
     for (int j = 0; j < steps; ++j) {
@@ -723,7 +778,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
     if (r != MDP_OK) return r;
   }
   if (hd.it > it_before) count_cycle<T>(h, hd.it - it_before);
-  if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before));
+  if (h->timing) MDP_TRY(add_matvec_times(h, hd.it - it_before, vbytes_of<T>(h), sizeof(T)));
   if (hd.flags & kNumeric) return fail(MDP_ERR_NUMERIC, "non-finite residual in GMRES");
   *iters = hd.it;
   *res2 = rn;

@@ -398,6 +398,69 @@ __device__ __forceinline__ void gm_dots_body(int bid, int nb, int64_t S, const T
   }
 }
 
+// Arnoldi step of the binary64 solver with single-pass classical Gram-Schmidt, parts 1
+// and 2 in one pass: w = J v_j = sigma_j (u_j - gamma P_pi u_j), written for the
+// projection, and the raw dots u_i . w (i <= j) while w is still in a register, so w is
+// not read back and one launch and its gap are saved per step.  w equals the
+// separate mat-vec's bit for bit; the dots are sums of the same products grouped by
+// this kernel's grid.  Exactly j + 1 products per state (NB as in gm_dots_body's FINE
+// widths).  The last block turns the sums into the Hessenberg column and the
+// projection coefficients.
+template <int NA, bool U, int NP>
+__device__ __forceinline__ void matvec_dots_rows(int bid, int nb, const double* __restrict__ pval,
+                                                 const int32_t* __restrict__ pcol, const int64_t* __restrict__ poff,
+                                                 const int32_t* __restrict__ plen, int k, int64_t S, double g,
+                                                 double sj, const double* __restrict__ basis,
+                                                 const double* __restrict__ uj, double* __restrict__ w,
+                                                 double (&d)[NP]) {
+  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
+    const double ws = sj * (uj[s] - g * px);
+    w[s] = ws;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) d[i] = fma(basis[(int64_t)i * S + s], ws, d[i]);
+  }
+}
+
+// Blocks per SM the fused kernel's register budget is sized for: its row gathers want
+// many resident warps, its NB accumulators want registers.  A microbenchmark at
+// S = 1e6 put 13 products per state about level at 2 and 4 blocks per SM and 25
+// products best at 2; the narrowest widths are mostly the mat-vec, which runs best
+// with many warps.
+__host__ __device__ constexpr int mvd_min_blocks(int NB) { return NB <= 8 ? 4 : NB <= 16 ? 3 : 2; }
+
+template <bool U, int NB>
+__device__ __forceinline__ void gm_matvec_dots_body(int bid, int nb, const double* __restrict__ pval,
+                                                    const int32_t* __restrict__ pcol,
+                                                    const int64_t* __restrict__ poff,
+                                                    const int32_t* __restrict__ plen, int k, int64_t S,
+                                                    double gamma, const double* __restrict__ basis, int j,
+                                                    double* __restrict__ w, double* partials, KrylovState* K) {
+  static_assert(NB % 4 == 0, "fine widths are multiples of 4");
+  constexpr int NP = pow2_up(NB);
+  if (K->flags & (kCycleStop | kSolveDone)) return;
+  const double sj = K->sigma[j];
+  const double* uj = basis + (int64_t)j * S;
+  double d[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) d[i] = 0.0;
+  switch (j + 1 - (NB - 4)) {  // 1..4: the caller picks NB from j
+    case 1: matvec_dots_rows<NB - 3, U>(bid, nb, pval, pcol, poff, plen, k, S, gamma, sj, basis, uj, w, d); break;
+    case 2: matvec_dots_rows<NB - 2, U>(bid, nb, pval, pcol, poff, plen, k, S, gamma, sj, basis, uj, w, d); break;
+    case 3: matvec_dots_rows<NB - 1, U>(bid, nb, pval, pcol, poff, plen, k, S, gamma, sj, basis, uj, w, d); break;
+    default: matvec_dots_rows<NB, U>(bid, nb, pval, pcol, poff, plen, k, S, gamma, sj, basis, uj, w, d); break;
+  }
+  __shared__ double fout[NP];
+  if (grid_sum_at<NP, false>(d, 0.0, partials, K->pstride, K->gcount, fout, bid, nb) && threadIdx.x == 0) {
+    for (int i = 0; i <= j; ++i) {
+      const double h = K->sigma[i] * fout[i];
+      K->hc[i] = h;
+      K->coef[i] = h * K->sigma[i];
+    }
+    K->wnorm = 0.0;
+  }
+}
+
 // Arnoldi projection passes.  First pass (MODE = kPlain, kDgks or kAlways):
 // u_{j+1} = w - sum_i coef_i u_i and ||u_{j+1}||^2; kDgks and kAlways also form
 // the raw dots u_i . u_{j+1} that a second classical Gram-Schmidt pass needs.
