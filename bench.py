@@ -971,6 +971,7 @@ def main():
                                          oracle_npz], stdin=subprocess.PIPE, stdout=subprocess.PIPE,
                                         stderr=subprocess.PIPE, text=True)
 
+    t_main = time.perf_counter()
     import numpy as np
     import torch
 
@@ -1267,20 +1268,32 @@ def main():
             "graph_solve": graph_cmp,
             "gpu_launches": int(totals["kernel_launches"]), "clocks": clocks,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)}}
+    wall = {"main_s": time.perf_counter() - t_main}
+    t_sec = time.perf_counter()
     line["small"] = run_small()
+    wall["small_s"] = time.perf_counter() - t_sec
     if args.serve > 0:
+        t_sec = time.perf_counter()
         line["serving"] = run_serving(args.serve)
+        wall["serving_s"] = time.perf_counter() - t_sec
     if args.stress:
+        t_sec = time.perf_counter()
         line["bandwidth_stress"] = run_stress()
+        wall["bandwidth_stress_s"] = time.perf_counter() - t_sec
     if oracle_child is not None:
         # start the CPU oracle now: the sections below time whole multi-second solves and the
         # arrival-bound serving stream, which one busy host core does not perturb
         oracle_child.stdin.write("go\n")
         oracle_child.stdin.flush()
     if args.pendulum:
+        t_sec = time.perf_counter()
         line["pendulum"] = run_pendulum()
+        wall["pendulum_s"] = time.perf_counter() - t_sec
     if args.stream > 0 and world == 1:
+        t_sec = time.perf_counter()
         line["serving_stream"] = run_serving_stream(args.stream)
+        wall["serving_stream_s"] = time.perf_counter() - t_sec
+    line["section_wall_s"] = wall
     line["iterations"]["error"] = error_statement(V64, pi64, s64_res, GAMMA, K_ROW, gnorm)
     if oracle_child is not None:
         out, err = oracle_child.communicate()

@@ -252,15 +252,19 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_
 /*
  * mdp_tune -- autotune the launch shape of the Bellman sweep (Eq. 3-4) on this
  * handle's matrix: times the fused sweep at V = 0 for each tile size (states per
- * block: 8 .. 512 that fit in shared memory) and keeps the fastest, which every
- * later mdp_bellman, mdp_solve and mdp_solve_batch call on the handle uses.  The
- * paper has no counterpart (its sparse kernels are PETSc's).  Results do not
- * depend on the tile size: every state's Q values, minimum and the residual are
- * computed the same way in any tile.
+ * block: 8 .. 512 that fit in shared memory) and keeps the fastest, then for that
+ * tile the number of resident blocks per SM of its grid (from the occupancy limit
+ * down to 1), which every later mdp_bellman, mdp_solve and mdp_solve_batch call on
+ * the handle uses; when the probabilities are exact in 16 bits it also picks the
+ * tile of the low-precision sweep (mdp_bellman_lowp).  The paper has no
+ * counterpart (its sparse kernels are PETSc's).  Results do not depend on the
+ * launch shape: every state's Q values, minimum and the residual are computed the
+ * same way in any tile and grid.
  *
  *  gamma         discount factor of the timed sweeps, in (0, 1).
  *  tile_states   host out (may be NULL): the chosen tile size.
- *  ms_per_sweep  host out (may be NULL): its time per sweep.
+ *  ms_per_sweep  host out (may be NULL): the binary64 sweep's time per sweep with the
+ *                chosen tile and grid.
  * Blocks until done.  Overwrites the handle's scratch vectors only.
  */
 mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_per_sweep, void* stream);

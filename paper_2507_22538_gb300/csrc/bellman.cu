@@ -26,6 +26,8 @@ mdp_status configure_bellman(mdp_s* h) {
   else
     MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bellman_kernel<false>, kBellThreads, smem));
   if (per_sm < 1) return fail(MDP_ERR_INVALID_ARG, "Bellman tile does not fit on an SM (too many actions)");
+  h->bell_max_per_sm = per_sm;
+  if (h->bell_per_sm_cap > 0) per_sm = std::min(per_sm, h->bell_per_sm_cap);  // chosen by mdp_tune
   const int64_t ntiles = (h->S + h->bell_tile_states - 1) / h->bell_tile_states;
   h->bell_threads = kBellThreads;
   h->bell_blocks = (int)std::min<int64_t>(ntiles, (int64_t)h->sm_count * per_sm);

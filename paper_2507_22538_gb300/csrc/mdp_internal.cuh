@@ -94,6 +94,8 @@ struct mdp_s {
   int bell_tile_states = 32;
   int bell_threads = 256;
   int bell_blocks = 0;
+  int bell_max_per_sm = 0;   // resident blocks per SM the tile allows (occupancy calculator)
+  int bell_per_sm_cap = 0;   // blocks per SM the grid uses, chosen by mdp_tune (0: bell_max_per_sm)
 
   // vector-kernel launch shape (thread per state)
   int vec_threads = 256;

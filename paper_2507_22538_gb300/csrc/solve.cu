@@ -90,11 +90,14 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   const int start = h->bell_tile_states;
   int best = start;
   float best_ms = 0.f;
+  h->bell_per_sm_cap = 0;  // tiles are compared at full occupancy
+  MDP_TRY(configure_bellman(h));
   MDP_TRY(time_one(&best_ms));
   static const int kCandidates[] = {8, 16, 32, 64, 128, 256, 512};
   for (int ts : kCandidates) {
     if (ts == start || ts > h->S || (size_t)ts * h->A * sizeof(double) > 227 * 1024) continue;
     h->bell_tile_states = ts;
+    h->bell_per_sm_cap = 0;
     if (configure_bellman(h) != MDP_OK) continue;  // the tile does not fit: skip it
     float ms = 0.f;
     mdp_status s = time_one(&ms);
@@ -110,6 +113,24 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   }
   h->bell_tile_states = best;
   MDP_TRY(configure_bellman(h));
+  // then the grid: resident blocks per SM from the occupancy limit down (fewer blocks
+  // leave each SM's L1 and request queues to fewer tiles at a time)
+  {
+    const int top = h->bell_max_per_sm;
+    int best_cap = 0;
+    for (int cap = top - 1; cap >= 1; --cap) {
+      h->bell_per_sm_cap = cap;
+      MDP_TRY(configure_bellman(h));
+      float ms = 0.f;
+      MDP_TRY(time_one(&ms));
+      if (ms < 0.98f * best_ms) {
+        best_cap = cap;
+        best_ms = ms;
+      }
+    }
+    h->bell_per_sm_cap = best_cap;
+    MDP_TRY(configure_bellman(h));
+  }
   // the low-precision sweep has its own tile (10 B of shared memory per row, and a
   // binary64 re-evaluation phase whose latency larger tiles amortise)
   if (lowp_available(h)) {
