@@ -358,6 +358,8 @@ def run_serving(n, slots=4, seed=5):
         solve_alone(r)  # warm-up
     alone = [solve_alone(r) for r in reqs]
     service = np.array([a.finished for a in alone])
+    # the same solves stream-driven (the service and solve_alone run graph-driven solves)
+    service_stream = np.array([solve_alone(r, graph=False).finished for r in reqs])
     rate = 0.8 / float(service.mean())
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -402,7 +404,9 @@ def run_serving(n, slots=4, seed=5):
                    "GMRES(30), alpha 1e-3, tol 1e-8; drawn on the device at admission (counted in the latency)",
             "entries_per_request": {"mean": float(nnz.mean()), "max": float(nnz.max())},
             "one_at_a_time_mean_s": float(service.mean()),
+            "one_at_a_time_stream_driven_mean_s": float(service_stream.mean()),
             "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
+            "one_at_a_time_stream_driven": fifo_one_at_a_time(arrivals, service_stream),
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same),
             "statuses_alone": {int(k): int(v) for k, v in zip(*np.unique([a.status for a in alone], return_counts=True))},
@@ -505,6 +509,89 @@ def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01, small_st
                             "mean_batch_of_cluster_launches": float(np.mean([b for b in svc.batches if b > 1]))
                             if any(b > 1 for b in svc.batches) else 1.0},
             "statuses": statuses, "verified_alone": len(alone), "mismatches": mism[:8], "n_mismatches": len(mism)}
+
+
+MID_MIX = dict(SERVE_MIX, s_range=(65_537, 200_000))
+
+
+def run_mid_batch(n=16, seed=7, reps=3):
+    """n requests of the serving mix with S log-uniform in [65,537, 2e5] (above the
+    cluster solver's limit), drawn on the device once: the solve calls alone (stream-
+    and graph-driven, one request at a time) against mdp_solve_batch on all n (stream-
+    driven: one host read per outer iteration and per GMRES cycle for the batch;
+    graph-driven: the whole batch as one CUDA graph launch, built inside the call).
+    Every mode gives every request the same V, policy and counts bit for bit."""
+    import numpy as np
+    import torch
+
+    from mdpgen.cuda_gen import load as load_gen
+    from paper_2507_22538_gb300 import mdp
+    load_gen()
+    stream = torch.cuda.current_stream()
+    reqs = [DeviceRequest(i, seed, **MID_MIX) for i in range(n)]
+    handles = []
+    try:
+        for r in reqs:
+            rp, col, val, g = r.device_arrays()
+            st, h = mdp.mdp_create(r.S, r.A, rp, col, val, g, True, stream)
+            del rp, col, val, g
+            mdp.check(st, "mdp_create")
+            handles.append(h)
+        V = [torch.zeros(r.S, dtype=torch.float64, device="cuda") for r in reqs]
+        pi = [torch.empty(r.S, dtype=torch.int32, device="cuda") for r in reqs]
+
+        def opts(graph):
+            out = []
+            for r in reqs:
+                o = mdp.mdp_default_opts()
+                o.gamma, o.atol_pi, o.alpha, o.gmres_restart, o.graph = r.gamma, 1e-8, 1e-3, 30, graph
+                out.append(o)
+            return out
+
+        results, times = {}, {}
+        for mode in ("alone_stream", "alone_graph", "batch_stream", "batch_graph"):
+            graph = 1 if mode.endswith("graph") else 0
+            ts = []
+            for rep in range(reps + 1):  # rep 0 warms up (and builds the alone graphs)
+                for v in V:
+                    v.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if mode.startswith("alone"):
+                    stats, status = [], []
+                    for i, o in enumerate(opts(graph)):
+                        st, s1 = mdp.mdp_solve(handles[i], o, V[i], pi[i], stream)
+                        status.append(st)
+                        stats.append(s1)
+                else:
+                    st, status, stats = mdp.mdp_solve_batch(handles, opts(graph), V, pi, stream)
+                    mdp.check(st, "mdp_solve_batch")
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            times[mode] = ts
+            results[mode] = ([v.cpu().numpy() for v in V], [p.cpu().numpy() for p in pi], list(status),
+                             [(x.outer_iters, int(x.inner_iters_total), x.final_residual) for x in stats])
+        ref = results["alone_stream"]
+        same = all(all(np.array_equal(a, b) for a, b in zip(results[m][0], ref[0])) and
+                   all(np.array_equal(a, b) for a, b in zip(results[m][1], ref[1])) and
+                   results[m][2] == ref[2] and results[m][3] == ref[3] for m in results)
+        out = {"requests": n, "mix": "the serving mix with S log-uniform in [65537, 2e5], A 2..32, k 4..64, "
+                                     "gamma in {0.9,0.99,0.999,0.9999}, GMRES(30), alpha 1e-3, tol 1e-8",
+               "states": [r.S for r in reqs], "entries_total": int(sum(r.nnz for r in reqs)),
+               "outer_inner": [list(x[:2]) for x in ref[3]], "statuses": [int(x) for x in ref[2]],
+               "equal_bitwise_all_modes": bool(same),
+               "timing": "host wall time of all n solves, median of %d after a warm-up" % reps}
+        for m, ts in times.items():
+            med = statistics.median(ts[1:])
+            out[m] = {"s": med, "solves_per_s": n / med}
+        out["alone_graph"]["first_call_s"] = times["alone_graph"][0]  # includes building every handle's graph
+        out["batch_graph"]["first_call_s"] = times["batch_graph"][0]
+        out["speedup_batch_graph_vs_alone_stream"] = out["alone_stream"]["s"] / out["batch_graph"]["s"]
+        out["speedup_batch_graph_vs_batch_stream"] = out["batch_stream"]["s"] / out["batch_graph"]["s"]
+        return out
+    finally:
+        for h in handles:
+            mdp.mdp_destroy(h)
 
 
 def run_small(steps=20):
@@ -939,6 +1026,8 @@ def main():
                     help="requests of the full serving stream added to the line (0: skip)")
     ap.add_argument("--small-only", action="store_true",
                     help="only the small-workload stream vs graph measurement (no bench line)")
+    ap.add_argument("--mid-batch-only", action="store_true",
+                    help="only the mid-size batch measurement, alone vs batched, stream vs graph (no bench line)")
     args = ap.parse_args()
     if args.cpu_oracle_worker:
         return run_cpu_oracle_worker(args)
@@ -953,6 +1042,12 @@ def main():
         from paper_2507_22538_gb300.build import build
         build()
         print(json.dumps({"mode": "small_only", **run_small()}), flush=True)
+        return 0
+    if args.mid_batch_only:
+        import torch
+        from paper_2507_22538_gb300.build import build
+        build()
+        print(json.dumps({"mode": "mid_batch_only", **run_mid_batch()}), flush=True)
         return 0
     if args.solve_only:
         return run_solve_only(args)
@@ -1275,6 +1370,9 @@ def main():
     t_sec = time.perf_counter()
     line["small"] = run_small()
     wall["small_s"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
+    line["mid_batch"] = run_mid_batch()
+    wall["mid_batch_s"] = time.perf_counter() - t_sec
     if args.serve > 0:
         t_sec = time.perf_counter()
         line["serving"] = run_serving(args.serve)

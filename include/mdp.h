@@ -85,8 +85,9 @@ typedef struct {
                               on the device, with no host round trip until the solve ends.  Same
                               kernels and results, bit for bit, as the stream-driven solve.  The
                               instantiated graph stays in the handle and is rebuilt when V, pi,
-                              gamma, the options or the Bellman launch shape change.  Ignored by
-                              mdp_solve_batch.                                                    (0) */
+                              gamma, the options or the Bellman launch shape change.  A batch
+                              (mdp_solve_batch) runs as one graph launch when every member sets
+                              it.                                                                 (0) */
   int32_t lowp_sweep;      /* nonzero: when every probability of the MDP is exact in binary16 or
                               bfloat16, run the Bellman sweeps as mdp_bellman_lowp does (16-bit
                               values, binary32 screen, binary64 re-evaluation of the rows that can
@@ -278,7 +279,14 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
  * GMRES cycle for the whole batch.  The paper solves one MDP per call; this is
  * the same method applied to many, with the per-problem arithmetic unchanged:
  * each problem's V, pi, iteration counts and status equal those of mdp_solve on
- * that problem alone, bit for bit.
+ * that problem alone, bit for bit.  When every member's opts.graph is set, the
+ * whole batch runs as one CUDA graph launch instead, whose independent branches
+ * are the members' graph-driven solves (the nodes mdp_solve runs with opts.graph):
+ * each problem's loops are decided on the device at its own pace, its kernels may
+ * overlap with the other members', and nothing returns to the host until all have
+ * stopped.  The graph is built and destroyed by the call (a handle's own cached
+ * graph is dropped and rebuilt by its next graph-driven mdp_solve); the results
+ * are the same bit for bit.
  *
  *  n        number of problems, >= 1.
  *  handles  [n] distinct handles on the current device (each used by this call only).

@@ -15,6 +15,13 @@
 // one per problem.  Problems that stop (converged, capped, failed) leave the
 // tables at the next outer iteration; inside a cycle, problems whose cycle or
 // solve ended return at once from the passes queued after.
+//
+// With opts.graph set on every member the batch runs instead as one CUDA graph
+// whose independent branches are the members' graph-driven solves (graph.cu):
+// no host round trip until all have stopped, each problem at its own pace.  A
+// lockstep graph (all problems in every node, stopped ones returning at once)
+// measured slower on uneven mid-size batches: the longest solve then drags every
+// other problem's empty blocks through each of its launches.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -533,16 +540,20 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
     else
       MDP_TRY(ensure_basis(items[i].h, items[i].o->gmres_restart + 1));
   }
+  bool all_graph = true;
+  for (int i = 0; i < n; ++i) all_graph = all_graph && opts[i].graph != 0;
   BatchBuffers B;
   B.n = n;
   B.st = st;
-  B.pin = t_arena.get(BatchBuffers::pinned_bytes(n));
-  if (!B.pin) return fail(MDP_ERR_OOM, "pinned host allocation failed");
-  if (cudaMallocAsync((void**)&B.desc, sizeof(BatchProblem) * n, st) != cudaSuccess ||
-      cudaMallocAsync((void**)&B.ranges, sizeof(int32_t) * kRanges * (n + 1), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&B.rep, sizeof(BatchReport) * n, st) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(MDP_ERR_OOM, "device allocation failed: batch tables");
+  if (!all_graph) {  // the lockstep tables (the graph-driven batch needs none)
+    B.pin = t_arena.get(BatchBuffers::pinned_bytes(n));
+    if (!B.pin) return fail(MDP_ERR_OOM, "pinned host allocation failed");
+    if (cudaMallocAsync((void**)&B.desc, sizeof(BatchProblem) * n, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&B.ranges, sizeof(int32_t) * kRanges * (n + 1), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&B.rep, sizeof(BatchReport) * n, st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(MDP_ERR_OOM, "device allocation failed: batch tables");
+    }
   }
   int64_t launches = 0;
   auto run = [&]() -> mdp_status {
@@ -605,7 +616,30 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
     }
     return MDP_OK;
   };
-  const mdp_status ran = run();
+  // opts.graph on every member: one CUDA graph with each problem's graph-driven solve as
+  // an independent branch (graph.cu), instead of the lockstep launches
+  auto run_branches = [&]() -> mdp_status {
+    std::vector<mdp_s*> hs(n);
+    std::vector<const mdp_solve_opts*> os(n);
+    std::vector<mdp_solve_stats> local(n);
+    std::vector<mdp_status> sts(n, MDP_OK);
+    for (int i = 0; i < n; ++i) {
+      hs[i] = items[i].h;
+      os[i] = items[i].o;
+    }
+    const mdp_status s = graph_solve_batch(n, hs.data(), os.data(), V, pi, local.data(), sts.data(), &launches, st);
+    for (int i = 0; i < n; ++i) {
+      Item& it = items[i];
+      it.k = local[i].outer_iters;
+      it.stats.converged = local[i].converged;
+      it.stats.inner_iters_total = local[i].inner_iters_total;
+      it.stats.final_residual = local[i].final_residual;
+      it.stats.bellman_sweeps = local[i].bellman_sweeps;
+      it.status = sts[i];
+    }
+    return s;
+  };
+  const mdp_status ran = all_graph ? run_branches() : run();
   // every handle's later calls wait for this one, also after a failure part way
   for (int i = 0; i < n; ++i) MDP_CUDA(cudaEventRecord(items[i].h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));

@@ -28,6 +28,7 @@
 // the Bellman launch shape).
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "krylov_dev.cuh"
 
@@ -38,6 +39,33 @@ mdp_status gmres_residual_launch(mdp_s* h, bool mixed, double gamma, const doubl
 mdp_status gmres_steps_launch(mdp_s* h, bool mixed, double gamma, int j0, int j1, int refine, cudaStream_t st);
 mdp_status gmres_tail_launch(mdp_s* h, bool mixed, double gamma, double* theta, cudaStream_t st);
 void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int64_t steps, int64_t tri);
+
+// Add a captured segment to `parent` as a child-graph node after `deps` (the
+// segment graph is consumed).
+mdp_status graph_add_segment(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps, cudaGraph_t seg,
+                             cudaGraphNode_t* node) {
+  const cudaError_t e = cudaGraphAddChildGraphNode(node, parent, deps, ndeps, seg);
+  cudaGraphDestroy(seg);  // the node holds its own copy
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddChildGraphNode");
+  return MDP_OK;
+}
+
+// Add a conditional node (IF or WHILE on handle c) to `parent` after `deps`;
+// *body receives the graph of its body.
+mdp_status graph_add_conditional(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps,
+                                 cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type,
+                                 cudaGraphNode_t* node, cudaGraph_t* body) {
+  // zero-filled storage: the parameter union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = c;
+  p->conditional.type = type;
+  p->conditional.size = 1;
+  MDP_CUDA(cudaGraphAddNode(node, parent, deps, nullptr, ndeps, p));
+  *body = p->conditional.phGraph_out[0];
+  return MDP_OK;
+}
 
 namespace {
 
@@ -226,32 +254,12 @@ mdp_status capture(mdp_s* h, cudaStream_t cs, cudaGraph_t* out, int* kernels, F 
   return MDP_OK;
 }
 
-// Add a captured segment to `parent` as a child-graph node after `deps`.
-mdp_status add_segment(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps, cudaGraph_t seg,
-                       cudaGraphNode_t* node) {
-  const cudaError_t e = cudaGraphAddChildGraphNode(node, parent, deps, ndeps, seg);
-  cudaGraphDestroy(seg);  // the node holds its own copy
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddChildGraphNode");
-  return MDP_OK;
-}
-
-mdp_status add_conditional(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps,
-                           cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type, cudaGraphNode_t* node,
-                           cudaGraph_t* body) {
-  // zero-filled storage: the parameter union has no default constructor
-  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
-  cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(raw);
-  p->type = cudaGraphNodeTypeConditional;
-  p->conditional.handle = c;
-  p->conditional.type = type;
-  p->conditional.size = 1;
-  MDP_CUDA(cudaGraphAddNode(node, parent, deps, nullptr, ndeps, p));
-  *body = p->conditional.phGraph_out[0];
-  return MDP_OK;
-}
-
-mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double* V, int32_t* pi, bool mixed,
-                       cudaStream_t st) {
+// Add the nodes of one graph-driven solve on handle h to `graph`: an init node with
+// no dependencies, then the outer WHILE.  The conditional handles are made on `graph`;
+// c->seg_kernels receives the kernels per segment (for the device record, uploaded
+// by the caller before the launch).
+mdp_status add_solve_nodes(mdp_s* h, GraphCache* c, cudaGraph_t graph, const mdp_solve_opts* o, double* V,
+                           int32_t* pi, bool mixed, bool lowp) {
   cudaStream_t cs = c->cap;
   KrylovState* K = (KrylovState*)h->kstate;
   GraphDevice* D = c->D;
@@ -262,9 +270,6 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
   const int seg_tail = kSegChunk0 + nchunks, seg_end = seg_tail + 1;
   int* nk = c->seg_kernels;
   std::memset(nk, 0, sizeof(c->seg_kernels));
-  cudaGraph_t graph = nullptr;
-  MDP_CUDA(cudaGraphCreate(&graph, 0));
-  c->graph = graph;
   cudaGraphConditionalHandle c_outer, c_go, c_inner;
   MDP_CUDA(cudaGraphConditionalHandleCreate(&c_outer, graph, 1u, cudaGraphCondAssignDefault));
   MDP_CUDA(cudaGraphConditionalHandleCreate(&c_go, graph, 0u, cudaGraphCondAssignDefault));
@@ -285,21 +290,21 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
     gs_init_kernel<<<1, 32, 0, cs>>>(D, kSegInit);
     return control_done();
   }));
-  MDP_TRY(add_segment(graph, nullptr, 0, seg, &n_init));
+  MDP_TRY(graph_add_segment(graph, nullptr, 0, seg, &n_init));
   cudaGraph_t outer_body = nullptr;
-  MDP_TRY(add_conditional(graph, &n_init, 1, c_outer, cudaGraphCondTypeWhile, &n_outer, &outer_body));
+  MDP_TRY(graph_add_conditional(graph, &n_init, 1, c_outer, cudaGraphCondTypeWhile, &n_outer, &outer_body));
 
   // outer body: the sweep and the stop tests, then IF (go) the evaluation
   cudaGraphNode_t n_sweep, n_if;
   MDP_TRY(capture(h, cs, &seg, &nk[kSegSweep], [&]() -> mdp_status {
-    MDP_TRY(launch_sweep(h, o->lowp_sweep != 0, gamma, V, h->TV, pi, cs));
+    MDP_TRY(launch_sweep(h, lowp, gamma, V, h->TV, pi, cs));
     gs_outer_check_kernel<<<1, 256, 0, cs>>>(h->resmax, D, kSegSweep, K, o->atol_pi, o->alpha, o->max_iter_pi,
                                             o->max_iter_ksp, m, h->partial_stride, c_outer, c_go);
     return control_done();
   }));
-  MDP_TRY(add_segment(outer_body, nullptr, 0, seg, &n_sweep));
+  MDP_TRY(graph_add_segment(outer_body, nullptr, 0, seg, &n_sweep));
   cudaGraph_t go_body = nullptr;
-  MDP_TRY(add_conditional(outer_body, &n_sweep, 1, c_go, cudaGraphCondTypeIf, &n_if, &go_body));
+  MDP_TRY(graph_add_conditional(outer_body, &n_sweep, 1, c_go, cudaGraphCondTypeIf, &n_if, &go_body));
 
   // evaluation: policy rows, the first restart residual, WHILE (inner) cycles, the end
   cudaGraphNode_t n_go, n_inner, n_end;
@@ -309,9 +314,9 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
     gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, kSegGo, 0, (long long)o->max_iter_ksp + 1, c_inner);
     return control_done();
   }));
-  MDP_TRY(add_segment(go_body, nullptr, 0, seg, &n_go));
+  MDP_TRY(graph_add_segment(go_body, nullptr, 0, seg, &n_go));
   cudaGraph_t inner_body = nullptr;
-  MDP_TRY(add_conditional(go_body, &n_go, 1, c_inner, cudaGraphCondTypeWhile, &n_inner, &inner_body));
+  MDP_TRY(graph_add_conditional(go_body, &n_go, 1, c_inner, cudaGraphCondTypeWhile, &n_inner, &inner_body));
 
   // one restart cycle: chunk 0, then chunks 1.. each under its own IF, in sequence
   cudaGraphNode_t prev = nullptr;  // the last node of the cycle so far in inner_body
@@ -323,17 +328,17 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
       return control_done();
     }));
     if (q == 0) {
-      MDP_TRY(add_segment(inner_body, nullptr, 0, seg, &prev));
+      MDP_TRY(graph_add_segment(inner_body, nullptr, 0, seg, &prev));
     } else {
       cudaGraphNode_t n_if_chunk, n_chunk;
       cudaGraph_t chunk_body = nullptr;
-      const mdp_status s_if = add_conditional(inner_body, &prev, 1, hs.go[q], cudaGraphCondTypeIf, &n_if_chunk,
+      const mdp_status s_if = graph_add_conditional(inner_body, &prev, 1, hs.go[q], cudaGraphCondTypeIf, &n_if_chunk,
                                               &chunk_body);
       if (s_if != MDP_OK) {
         cudaGraphDestroy(seg);
         return s_if;
       }
-      MDP_TRY(add_segment(chunk_body, nullptr, 0, seg, &n_chunk));
+      MDP_TRY(graph_add_segment(chunk_body, nullptr, 0, seg, &n_chunk));
       prev = n_if_chunk;
     }
   }
@@ -343,21 +348,139 @@ mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double*
     gs_inner_cond_kernel<<<1, 32, 0, cs>>>(K, D, seg_tail, 1, (long long)o->max_iter_ksp + 1, c_inner);
     return control_done();
   }));
-  MDP_TRY(add_segment(inner_body, &prev, 1, seg, &n_tail));
+  MDP_TRY(graph_add_segment(inner_body, &prev, 1, seg, &n_tail));
   MDP_TRY(capture(h, cs, &seg, &nk[seg_end], [&]() -> mdp_status {
     gs_outer_end_kernel<<<1, 32, 0, cs>>>(K, D, seg_end, c_outer);
     return control_done();
   }));
-  MDP_TRY(add_segment(go_body, &n_inner, 1, seg, &n_end));
+  MDP_TRY(graph_add_segment(go_body, &n_inner, 1, seg, &n_end));
 
-  MDP_CUDA(cudaGraphInstantiate(&c->exec, graph, 0));
+  return MDP_OK;
+}
+
+mdp_status build_graph(mdp_s* h, GraphCache* c, const mdp_solve_opts* o, double* V, int32_t* pi, bool mixed,
+                       cudaStream_t st) {
+  MDP_CUDA(cudaGraphCreate(&c->graph, 0));
+  MDP_TRY(add_solve_nodes(h, c, c->graph, o, V, pi, mixed, o->lowp_sweep != 0));
+  MDP_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
   // the kernels per segment, read by the control kernels
-  MDP_CUDA(cudaMemcpyAsync(D->seg_kernels, nk, sizeof(c->seg_kernels), cudaMemcpyHostToDevice, st));
+  MDP_CUDA(cudaMemcpyAsync(c->D->seg_kernels, c->seg_kernels, sizeof(c->seg_kernels), cudaMemcpyHostToDevice, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   return MDP_OK;
 }
 
+// The handle's graph record: capture stream and device solve record, made on first use.
+mdp_status graph_cache(mdp_s* h, cudaStream_t st, GraphCache** out) {
+  GraphCache* c = (GraphCache*)h->gcache;
+  if (!c) {
+    c = new GraphCache();
+    h->gcache = c;
+    MDP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  }
+  if (!c->D) {
+    if (cudaMallocAsync((void**)&c->D, sizeof(GraphDevice), st) != cudaSuccess) {
+      cudaGetLastError();
+      c->D = nullptr;
+      return fail(MDP_ERR_OOM, "device allocation failed: graph solve state");
+    }
+  }
+  *out = c;
+  return MDP_OK;
+}
+
+// Fill the iteration fields of *local from a solve record; the status of the solve.
+mdp_status graph_outcome(mdp_s* h, bool mixed, const GraphSolveState& g, mdp_solve_stats* local) {
+  local->outer_iters = g.k;
+  local->converged = g.converged;
+  local->inner_iters_total = g.inner_total;
+  local->final_residual = g.res;
+  local->bellman_sweeps = g.sweeps;
+  h->launches += g.launches;
+  gmres_count_work(h, mixed, g.solves, g.cycles, g.steps, g.tri);
+  if (g.guard) return fail(MDP_ERR_CUDA, "internal: a loop guard of the graph-driven solve ended it");
+  if (g.status == MDP_ERR_NUMERIC)
+    return fail(MDP_ERR_NUMERIC, g.numeric_inner ? "non-finite residual in GMRES" : "non-finite Bellman residual");
+  if (g.status == MDP_NOT_CONVERGED)
+    return fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
+  return MDP_OK;
+}
+
+// Pinned host copies of the solve records of a batch; one per host thread, grown on demand.
+struct PinnedRecords {
+  GraphSolveState* p = nullptr;
+  int cap = 0;
+  ~PinnedRecords() {
+    if (p) cudaFreeHost(p);
+  }
+  GraphSolveState* get(int n) {
+    if (n <= cap) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const int want = std::max(n, 64);
+    if (cudaMallocHost((void**)&p, sizeof(GraphSolveState) * want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return nullptr;
+    }
+    cap = want;
+    return p;
+  }
+};
+thread_local PinnedRecords t_records;
+
 }  // namespace
+
+// mdp_solve_batch with every member's opts.graph set: one CUDA graph that holds each
+// problem's graph-driven solve (the nodes mdp_solve's graph has) as an independent
+// branch.  Every branch decides its own loops on the device, so the problems run at
+// their own pace and their kernels overlap on the GPU where the launch leaves room;
+// each one computes exactly what its stand-alone solve computes.  The graph is built,
+// launched once and destroyed by this call.  A handle's own cached graph reads the
+// device record the batch reuses, so it is dropped (and rebuilt by its next graph-
+// driven mdp_solve).  Buffers are ensured by the caller; fills local[] and status[].
+mdp_status graph_solve_batch(int n, mdp_s* const* hs, const mdp_solve_opts* const* os, double* const* V,
+                             int32_t* const* pi, mdp_solve_stats* local, mdp_status* status, int64_t* launches,
+                             cudaStream_t st) {
+  std::vector<GraphCache*> cs(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    MDP_TRY(graph_cache(hs[i], st, &cs[i]));
+    drop_graph(cs[i]);
+  }
+  GraphSolveState* rec = t_records.get(n);
+  if (!rec) return fail(MDP_ERR_OOM, "pinned host allocation failed");
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto body = [&]() -> mdp_status {
+    MDP_CUDA(cudaGraphCreate(&graph, 0));
+    for (int i = 0; i < n; ++i)
+      MDP_TRY(add_solve_nodes(hs[i], cs[i], graph, os[i], V[i], pi[i], os[i]->precision == MDP_PREC_MIXED, false));
+    MDP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    for (int i = 0; i < n; ++i)
+      MDP_CUDA(cudaMemcpyAsync(cs[i]->D->seg_kernels, cs[i]->seg_kernels, sizeof(cs[i]->seg_kernels),
+                               cudaMemcpyHostToDevice, st));
+    MDP_CUDA(cudaGraphLaunch(exec, st));
+    for (int i = 0; i < n; ++i)
+      MDP_CUDA(cudaMemcpyAsync(rec + i, &cs[i]->D->G, sizeof(GraphSolveState), cudaMemcpyDeviceToHost, st));
+    MDP_CUDA(cudaStreamSynchronize(st));
+    return MDP_OK;
+  };
+  const mdp_status s = body();
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (s != MDP_OK) return s;
+  int64_t total = 0;
+  bool guard = false;
+  for (int i = 0; i < n; ++i) {
+    const mdp_status si = graph_outcome(hs[i], os[i]->precision == MDP_PREC_MIXED, rec[i], local + i);
+    guard = guard || rec[i].guard;
+    status[i] = (si == MDP_OK || si == MDP_NOT_CONVERGED || si == MDP_ERR_NUMERIC) ? si : MDP_OK;
+    total += rec[i].launches;
+  }
+  *launches = total;
+  if (guard) return fail(MDP_ERR_CUDA, "internal: a loop guard of the graph-driven batch ended it");
+  return MDP_OK;
+}
 
 void graph_cache_free(mdp_s* h) {
   GraphCache* c = (GraphCache*)h->gcache;
@@ -375,17 +498,8 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
                        cudaStream_t st) {
   const bool mixed = (o->precision == MDP_PREC_MIXED);
   MDP_TRY(mixed ? ensure_mixed(h, o->gmres_restart + 1) : ensure_basis(h, o->gmres_restart + 1));
-  GraphCache* c = (GraphCache*)h->gcache;
-  if (!c) {
-    c = new GraphCache();
-    h->gcache = c;
-    MDP_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    if (cudaMallocAsync((void**)&c->D, sizeof(GraphDevice), st) != cudaSuccess) {
-      cudaGetLastError();
-      c->D = nullptr;
-      return fail(MDP_ERR_OOM, "device allocation failed: graph solve state");
-    }
-  }
+  GraphCache* c = nullptr;
+  MDP_TRY(graph_cache(h, st, &c));
   GraphKey key;
   std::memset(&key, 0, sizeof(key));
   key.V = V;
@@ -424,20 +538,7 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   MDP_CUDA(cudaMemcpyAsync(out, &c->D->G, sizeof(GraphSolveState), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaEventRecord(h->done, st));
   MDP_CUDA(cudaStreamSynchronize(st));
-  const GraphSolveState g = *out;
-  local->outer_iters = g.k;
-  local->converged = g.converged;
-  local->inner_iters_total = g.inner_total;
-  local->final_residual = g.res;
-  local->bellman_sweeps = g.sweeps;
-  h->launches += g.launches;
-  gmres_count_work(h, mixed, g.solves, g.cycles, g.steps, g.tri);
-  if (g.guard) return fail(MDP_ERR_CUDA, "internal: a loop guard of the graph-driven solve ended it");
-  if (g.status == MDP_ERR_NUMERIC)
-    return fail(MDP_ERR_NUMERIC, g.numeric_inner ? "non-finite residual in GMRES" : "non-finite Bellman residual");
-  if (g.status == MDP_NOT_CONVERGED)
-    return fail(MDP_NOT_CONVERGED, "max_iter_pi policy evaluations without reaching atol_pi");
-  return MDP_OK;
+  return graph_outcome(h, mixed, *out, local);
 }
 
 }  // namespace mdp

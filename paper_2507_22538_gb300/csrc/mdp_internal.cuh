@@ -201,5 +201,16 @@ size_t krylov_state_bytes();
 mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi, mdp_solve_stats* stats,
                        cudaStream_t st);
 void graph_cache_free(mdp_s* h);
+// mdp_solve_batch with opts.graph on every member: one graph, each problem's graph-driven
+// solve an independent branch (handles distinct, buffers ensured; fills local[], status[])
+mdp_status graph_solve_batch(int n, mdp_s* const* hs, const mdp_solve_opts* const* os, double* const* V,
+                             int32_t* const* pi, mdp_solve_stats* local, mdp_status* status, int64_t* launches,
+                             cudaStream_t st);
+// Building blocks of the captured graphs (graph.cu; also used by the batched graph solve).
+mdp_status graph_add_segment(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps, cudaGraph_t seg,
+                             cudaGraphNode_t* node);
+mdp_status graph_add_conditional(cudaGraph_t parent, const cudaGraphNode_t* deps, size_t ndeps,
+                                 cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type,
+                                 cudaGraphNode_t* node, cudaGraph_t* body);
 
 }  // namespace mdp

@@ -12,7 +12,10 @@ all of them, each result bit for bit its stand-alone one.  With small_states > 0
 many states (GMRES in FP64) are instead gathered with the other pending small ones, up to small_batch_max,
 and solved by mdp_solve_small_batch: one thread-block cluster per request, the whole batch in one launch
 (solve_alone routes such a request the same way, so each result is still bit for bit its stand-alone
-one).  The solver calls release the Python interpreter lock, so the
+one).  With graph set (the default), every grid solve runs graph-driven (opts.graph): a single
+request as one CUDA graph launch, a batch as one graph whose branches are its members' solves, with
+no host round trip until they stop; the results are the same bit for bit as stream-driven solves.
+The solver calls release the Python interpreter lock, so the
 workers' host threads run concurrently.  All computation happens in libmdp's
 kernels; this module only schedules.
 """
@@ -97,7 +100,7 @@ class SolveService:
     """A fixed pool of worker slots with an HBM admission budget."""
 
     def __init__(self, slots: int = 4, hbm_budget: int = 120 << 30, device: int = 0, batch_max: int = 1,
-                 keep=None, small_states: int = 0, small_batch_max: int = 256):
+                 keep=None, small_states: int = 0, small_batch_max: int = 256, graph: bool = True):
         """keep: optional predicate on a request id; results of other requests drop V and
         the policy (status, iteration counts and latency stay), to bound host memory on
         long streams."""
@@ -106,6 +109,7 @@ class SolveService:
         self.batch_max = max(1, int(batch_max))
         self.small_states = int(small_states)
         self.small_batch_max = max(1, int(small_batch_max))
+        self.graph = bool(graph)
         self.keep = keep
         self.budget = int(hbm_budget)
         self.device = device
@@ -224,9 +228,9 @@ class SolveService:
                 if self._small(batch[0]):
                     outs = self._solve_small(batch, stream)
                 elif len(batch) == 1:
-                    outs = [self._solve(batch[0], stream)]
+                    outs = [self._solve(batch[0], stream, self.graph)]
                 else:
-                    outs = self._solve_batch(batch, stream)
+                    outs = self._solve_batch(batch, stream, self.graph)
             except Exception as exc:  # failed requests still complete, with their status
                 status = exc.status if isinstance(exc, mdp.MDPError) else mdp.MDP_ERR_CUDA
                 oom = isinstance(exc, torch.cuda.OutOfMemoryError) or status == mdp.MDP_ERR_OOM
@@ -265,7 +269,7 @@ class SolveService:
                 self._cv.notify_all()
 
     @staticmethod
-    def _solve(req: Request, stream) -> Result:
+    def _solve(req: Request, stream, graph: bool = True) -> Result:
         import torch
         d = req.data
         with torch.cuda.stream(stream):
@@ -274,7 +278,7 @@ class SolveService:
             try:
                 o = mdp.mdp_default_opts()
                 o.gamma, o.atol_pi, o.alpha, o.inner = d.gamma, req.tol, req.alpha, req.inner
-                o.gmres_restart, o.precision = req.restart, req.precision
+                o.gmres_restart, o.precision, o.graph = req.restart, req.precision, int(graph)
                 V = torch.zeros(d.S, dtype=torch.float64, device="cuda")
                 pi = torch.empty(d.S, dtype=torch.int32, device="cuda")
                 st, stats = mdp.mdp_solve(h, o, V, pi, stream)
@@ -286,7 +290,7 @@ class SolveService:
                       stats.final_residual, req.arrival, 0.0, 0.0, err)
 
     @staticmethod
-    def _solve_batch(batch, stream) -> list:
+    def _solve_batch(batch, stream, graph: bool = True) -> list:
         import torch
         handles = []
         with torch.cuda.stream(stream):
@@ -299,7 +303,7 @@ class SolveService:
                 for r in batch:
                     o = mdp.mdp_default_opts()
                     o.gamma, o.atol_pi, o.alpha, o.inner = r.data.gamma, r.tol, r.alpha, r.inner
-                    o.gmres_restart, o.precision = r.restart, r.precision
+                    o.gmres_restart, o.precision, o.graph = r.restart, r.precision, int(graph)
                     opts.append(o)
                 V = [torch.zeros(r.data.S, dtype=torch.float64, device="cuda") for r in batch]
                 pi = [torch.empty(r.data.S, dtype=torch.int32, device="cuda") for r in batch]
@@ -352,15 +356,16 @@ def is_small(r: Request, small_states: int) -> bool:
             and r.precision == mdp.MDP_PREC_F64)
 
 
-def solve_alone(req: Request, small_states: int = 0) -> Result:
+def solve_alone(req: Request, small_states: int = 0, graph: bool = True) -> Result:
     """The same request on the current stream with nothing else running (routed to the
-    cluster solver, as a service with the same small_states would, when it is small)."""
+    cluster solver, as a service with the same small_states would, when it is small;
+    graph- or stream-driven otherwise)."""
     import torch
     t0 = time.perf_counter()
     if is_small(req, small_states):
         res = SolveService._solve_small([req], torch.cuda.current_stream())[0]
     else:
-        res = SolveService._solve(req, torch.cuda.current_stream())
+        res = SolveService._solve(req, torch.cuda.current_stream(), graph)
     res.finished = time.perf_counter() - t0
     return res
 

@@ -161,3 +161,89 @@ def test_batch_rejects_bad_arguments():
         # the handle still works afterwards
         st, status, stats = mdp.mdp_solve_batch([M.h], [o], [V], [pi])
         assert st == mdp.MDP_OK and status[0] == mdp.MDP_OK
+
+
+def _batch_v0(ms, opts, V0=None):
+    """The batch from given start vectors (zeros where V0[i] is None)."""
+    import torch
+
+    from paper_2507_22538_gb300 import mdp
+    Ms = [mdp.MDP.from_data(m) for m in ms]
+    try:
+        V = []
+        for i, m in enumerate(ms):
+            v = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+            if V0 is not None and V0[i] is not None:
+                v.copy_(torch.as_tensor(V0[i], dtype=torch.float64))
+            V.append(v)
+        pi = [torch.empty(m.S, dtype=torch.int32, device="cuda") for m in ms]
+        st, status, stats = mdp.mdp_solve_batch([M.h for M in Ms], opts, V, pi, None)
+        torch.cuda.synchronize()
+        return st, status, [v.cpu().numpy() for v in V], [p.cpu().numpy() for p in pi], stats
+    finally:
+        for M in Ms:
+            M.close()
+
+
+def _graph_opts(opts):
+    for o in opts:
+        o.graph = 1
+    return opts
+
+
+def _same_results(a, b, names):
+    st_a, status_a, V_a, pi_a, stats_a = a
+    st_b, status_b, V_b, pi_b, stats_b = b
+    assert st_a == st_b
+    for i, name in enumerate(names):
+        assert status_a[i] == status_b[i], (name, status_a[i], status_b[i])
+        assert np.array_equal(V_a[i], V_b[i], equal_nan=True), name
+        assert np.array_equal(pi_a[i], pi_b[i]), name
+        for f in ("outer_iters", "inner_iters_total", "bellman_sweeps", "converged", "policy_value_bytes"):
+            assert getattr(stats_a[i], f) == getattr(stats_b[i], f), (name, f)
+        ra, rb = stats_a[i].final_residual, stats_b[i].final_residual
+        assert ra == rb or (np.isnan(ra) and np.isnan(rb)), name
+
+
+def test_graph_batch_equals_stream_batch_bitwise(problems):
+    """opts.graph on every member: the whole batch as one CUDA graph launch, decided
+    on the device, gives every problem the stream-driven batch's results bit for bit
+    (and so its stand-alone solve's), in both orders."""
+    ms = [p[0] for p in problems]
+    names = [m.name for m in ms]
+    stream = _batch_v0(ms, [_opts(*p) for p in problems])
+    graph = _batch_v0(ms, _graph_opts([_opts(*p) for p in problems]))
+    _same_results(stream, graph, names)
+    rev = _batch_v0(ms[::-1], _graph_opts([_opts(*p) for p in problems])[::-1])
+    _same_results(graph, (rev[0], rev[1][::-1], rev[2][::-1], rev[3][::-1], rev[4][::-1]), names)
+
+
+@pytest.mark.parametrize("caps", [(0, 1000), (1, 1000), (3, 1000), (1000, 0), (1000, 1), (1000, 7), (2, 5)])
+def test_graph_batch_caps(caps):
+    """Outer and inner iteration caps, per problem, end the device-side loops where
+    the stream-driven batch ends them."""
+    max_pi, max_ksp = caps
+    ms = [random_sparse(1000, 4, 8, 0.9, seed=1), banded_birth_death(3000, 10, 16, 0.999),
+          _ragged(500, 3, 13, 0.99)]
+    def opts():
+        out = []
+        for m, restart, prec in zip(ms, (30, 7, 12), (F64, MIXED, F64)):
+            o = _opts(m, 1e-9, 1e-3, restart, max_pi, prec)
+            o.max_iter_ksp = max_ksp
+            out.append(o)
+        return out
+    stream = _batch_v0(ms, opts())
+    graph = _batch_v0(ms, _graph_opts(opts()))
+    _same_results(stream, graph, [m.name for m in ms])
+
+
+def test_graph_batch_nan_member():
+    """A member started from a NaN vector fails with MDP_ERR_NUMERIC after its first
+    sweep; the others finish as in the stream-driven batch."""
+    from paper_2507_22538_gb300 import mdp
+    ms = [random_sparse(1000, 4, 8, 0.9, seed=1), random_sparse(800, 5, 6, 0.99, seed=4)]
+    V0 = [None, np.full(800, np.nan)]
+    stream = _batch_v0(ms, [_opts(m, 1e-9, 1e-3, 30, 1000) for m in ms], V0)
+    graph = _batch_v0(ms, _graph_opts([_opts(m, 1e-9, 1e-3, 30, 1000) for m in ms]), V0)
+    _same_results(stream, graph, [m.name for m in ms])
+    assert graph[1][0] == mdp.MDP_OK and graph[1][1] == mdp.MDP_ERR_NUMERIC

@@ -14,15 +14,22 @@ pytestmark = pytest.mark.gpu
 MIX = dict(s_range=(200, 20_000), a_range=(2, 16), k_range=(4, 32), gammas=(0.9, 0.99, 0.999))
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("graph", [True, False], ids=["graph", "stream"])
+def test_results_alone_equal_results_in_the_mix(graph):
+    """Graph-driven service (the default) and stream-driven service: each result equals
+    the request solved alone, and the two drivers give the same bits."""
     from paper_2507_22538_gb300 import mdp
     from paper_2507_22538_gb300.serve import Request, SolveService, latency_summary, solve_alone
     reqs = [Request(i, serving_request(i, seed=17, **MIX), tol=1e-8, alpha=1e-3) for i in range(24)]
-    alone = {r.rid: solve_alone(r) for r in reqs}
+    alone = {r.rid: solve_alone(r, graph=graph) for r in reqs}
+    other = {r.rid: solve_alone(r, graph=not graph) for r in reqs[:6]}
+    for rid, b in other.items():
+        assert np.array_equal(alone[rid].V, b.V) and np.array_equal(alone[rid].pi, b.pi)
+        assert alone[rid].inner_iters == b.inner_iters
     # a budget that holds only part of the mix at once: admission must wait for memory
     from paper_2507_22538_gb300.serve import device_bytes
     budget = int(3 * max(device_bytes(r.data) for r in reqs))
-    svc = SolveService(slots=4, hbm_budget=budget).start()
+    svc = SolveService(slots=4, hbm_budget=budget, graph=graph).start()
     rng = np.random.default_rng(0)
     for r in reqs:
         svc.submit(r)
@@ -66,13 +73,14 @@ def test_request_above_budget_is_refused():
         svc.submit(Request(0, serving_request(0, seed=1, **MIX)))
 
 
-def test_batched_service_equals_alone():
+@pytest.mark.parametrize("graph", [True, False], ids=["graph", "stream"])
+def test_batched_service_equals_alone(graph):
     """With batch_max > 1 the service solves pending requests of different S, A, k and
-    gamma together (mdp_solve_batch); each result still equals the request solved
-    alone, bit for bit."""
+    gamma together (mdp_solve_batch: one graph with a branch per request, or lockstep
+    launches); each result still equals the request solved alone, bit for bit."""
     from paper_2507_22538_gb300.serve import Request, SolveService, solve_alone
     reqs = [Request(i, serving_request(i, seed=29, **MIX), tol=1e-8, alpha=1e-3) for i in range(16)]
-    svc = SolveService(slots=2, batch_max=8).start()
+    svc = SolveService(slots=2, batch_max=8, graph=graph).start()
     for r in reqs:
         svc.submit(r)
     res = svc.wait(len(reqs))
