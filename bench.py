@@ -511,10 +511,36 @@ def run_serving_stream(n, slots=4, seed=5, calib=200, verify_frac=0.01, small_st
             "statuses": statuses, "verified_alone": len(alone), "mismatches": mism[:8], "n_mismatches": len(mism)}
 
 
+def sweep_variants(M, gamma, V, TV, pi, stream, sweeps=10):
+    """The tuned launch shape of a handle's Bellman sweep, and the time per sweep of
+    each rows-per-warp / value-load-width variant at the tuned tile (occupancy-limited
+    grid); the tuned shape is restored afterwards."""
+    import torch
+
+    from paper_2507_22538_gb300 import mdp
+    st, shape = mdp.mdp_get_sweep_shape(M.h)
+    mdp.check(st, "mdp_get_sweep_shape")
+    out = {"tuned": shape, "ms_per_sweep": {}}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rpw, vb in ((32, 16), (32, 32), (64, 16), (64, 32)):
+        mdp.check(mdp.mdp_set_sweep_shape(M.h, shape["tile_states"], rpw, vb, 0), "mdp_set_sweep_shape")
+        for _ in range(2):
+            mdp.check(mdp.mdp_bellman(M.h, gamma, V, TV, pi, None, stream), "mdp_bellman")
+        e0.record(stream)
+        for _ in range(sweeps):
+            mdp.check(mdp.mdp_bellman(M.h, gamma, V, TV, pi, None, stream), "mdp_bellman")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["ms_per_sweep"][f"rows_per_warp={rpw},load_bytes={vb}"] = e0.elapsed_time(e1) / sweeps
+    mdp.check(mdp.mdp_set_sweep_shape(M.h, shape["tile_states"], shape["rows_per_warp"], shape["value_load_bytes"],
+                                      shape["blocks_per_sm"]), "mdp_set_sweep_shape")
+    return out
+
+
 MID_MIX = dict(SERVE_MIX, s_range=(65_537, 200_000))
 
 
-def run_mid_batch(n=16, seed=7, reps=3):
+def run_mid_batch(n=16, seed=7, reps=5):
     """n requests of the serving mix with S log-uniform in [65,537, 2e5] (above the
     cluster solver's limit), drawn on the device once: the solve calls alone (stream-
     and graph-driven, one request at a time) against mdp_solve_batch on all n (stream-
@@ -583,7 +609,7 @@ def run_mid_batch(n=16, seed=7, reps=3):
                "timing": "host wall time of all n solves, median of %d after a warm-up" % reps}
         for m, ts in times.items():
             med = statistics.median(ts[1:])
-            out[m] = {"s": med, "solves_per_s": n / med}
+            out[m] = {"s": med, "solves_per_s": n / med, "all_s": [round(t, 4) for t in ts]}
         out["alone_graph"]["first_call_s"] = times["alone_graph"][0]  # includes building every handle's graph
         out["batch_graph"]["first_call_s"] = times["batch_graph"][0]
         out["speedup_batch_graph_vs_alone_stream"] = out["alone_stream"]["s"] / out["batch_graph"]["s"]
@@ -705,6 +731,7 @@ def run_stress(sweeps=10):
         V = torch.zeros(Sx, dtype=torch.float64, device="cuda")
         TV = torch.empty_like(V)
         pi = torch.empty(Sx, dtype=torch.int32, device="cuda")
+        out["sweep_shape"] = sweep_variants(M, gx, V, TV, pi, stream, sweeps=4)
         for _ in range(3):
             mdp.check(mdp.mdp_bellman(M.h, gx, V, TV, pi, None, stream), "mdp_bellman")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1097,6 +1124,7 @@ def main():
     mdp.check(st_t, "mdp_tune")
     V = torch.zeros(S, dtype=torch.float64, device="cuda")
     pi = torch.empty(S, dtype=torch.int32, device="cuda")
+    shape_info = sweep_variants(M, GAMMA, V, torch.empty_like(V), pi, stream)
     opts = mdp.mdp_default_opts()
     opts.gamma, opts.atol_pi, opts.alpha, opts.gmres_restart = GAMMA, TOL, ALPHA, RESTART
     opts.inner, opts.record_timing = mdp.MDP_GMRES, 1
@@ -1311,7 +1339,7 @@ def main():
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "traffic": sweep_traffic(),
                 "bytes_per_launch": bellman_bytes(), "avg_launch_ms": bell_ms,
-                "share_of_step": share_bell, "tile_states": tile_states}
+                "share_of_step": share_bell, "tile_states": tile_states, "sweep_shape": shape_info}
     mv_ms = totals["matvec_ms"] / max(1, totals["matvecs_timed"])
     mv_bytes = totals["matvec_bytes"] / max(1, totals["matvecs_timed"])
     mv_gbs = mv_bytes / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else None

@@ -258,9 +258,12 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_
  * down to 1), which every later mdp_bellman, mdp_solve and mdp_solve_batch call on
  * the handle uses; when the probabilities are exact in 16 bits it also picks the
  * tile of the low-precision sweep (mdp_bellman_lowp).  The paper has no
- * counterpart (its sparse kernels are PETSc's).  Results do not depend on the
- * launch shape: every state's Q values, minimum and the residual are computed the
- * same way in any tile and grid.
+ * counterpart (its sparse kernels are PETSc's).  Between the tile and the grid it
+ * also picks, at full occupancy, the rows of the stacked matrix a warp takes per
+ * step (32: one row per lane; 64: two rows per lane, their loads side by side) and
+ * the width of the binary64 value loads (16 or 32 bytes per chunk of 4 entries).
+ * Results do not depend on the launch shape: every state's Q values, minimum and
+ * the residual are computed the same way in any tile, grid and variant.
  *
  *  gamma         discount factor of the timed sweeps, in (0, 1).
  *  tile_states   host out (may be NULL): the chosen tile size.
@@ -269,6 +272,30 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* opts, double* V, int32_
  * Blocks until done.  Overwrites the handle's scratch vectors only.
  */
 mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_per_sweep, void* stream);
+
+/*
+ * mdp_get_sweep_shape -- the launch shape the Bellman sweep of this handle uses
+ * (the creation defaults, or what mdp_tune or mdp_set_sweep_shape set).  Host
+ * outputs, each may be NULL: states per block (tile), blocks of the grid, the cap on
+ * resident blocks per SM (0: the occupancy limit), rows of the stacked matrix per
+ * warp step (32 or 64) and bytes per binary64 value load (16 or 32); passing these
+ * to mdp_set_sweep_shape restores the shape.  No device work.  The paper has no
+ * counterpart.
+ */
+mdp_status mdp_get_sweep_shape(mdp_handle h, int32_t* tile_states, int32_t* blocks, int32_t* blocks_per_sm,
+                               int32_t* rows_per_warp, int32_t* value_load_bytes);
+
+/*
+ * mdp_set_sweep_shape -- set the Bellman sweep's launch shape by hand, e.g. to reuse
+ * what mdp_tune chose for the same matrix in an earlier run: states per block
+ * (tile_states, whose Q values must fit in shared memory: tile_states * A * 8 bytes
+ * <= 227 KB), rows per warp step (32 or 64), bytes per binary64 value load (16 or
+ * 32) and resident blocks per SM of the grid (0: the occupancy limit).  Results do
+ * not depend on the shape.  MDP_ERR_INVALID_ARG for an unsupported shape (the
+ * handle keeps its previous one).  No device work.  The paper has no counterpart.
+ */
+mdp_status mdp_set_sweep_shape(mdp_handle h, int32_t tile_states, int32_t rows_per_warp, int32_t value_load_bytes,
+                               int32_t blocks_per_sm);
 
 /*
  * mdp_solve_batch -- Algorithm 1 on n independent MDPs at once (problems of

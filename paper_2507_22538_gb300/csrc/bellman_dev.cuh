@@ -25,7 +25,12 @@ constexpr int kBellMinBlocks = 6;
 __device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
 
 
-template <bool UNIFORM>
+// Launch-shape variants the tuner picks from (mdp_tune): RPL rows per lane (1: one
+// 32-row slice per warp step; 2: two slices, their loads side by side) and V256
+// (the binary64 values of a chunk in one 32-byte load instead of two 16-byte ones).
+// Every variant computes each row's sum as the same chain of fused multiply-adds,
+// so the outputs do not depend on the variant.
+template <bool UNIFORM, int RPL = 1, bool V256 = false>
 __device__ __forceinline__ void bellman_body(int bid, int nb, 
     const double* __restrict__ sval, const int32_t* __restrict__ scol, const int64_t* __restrict__ off,
     const int32_t* __restrict__ len, int k, const double* __restrict__ g, const double* __restrict__ V, int64_t S,
@@ -41,15 +46,39 @@ __device__ __forceinline__ void bellman_body(int bid, int nb,
     const int64_t s1 = min(S, s0 + TS);
     const int64_t r0 = s0 * A, r1 = s1 * A;
     const int64_t q0 = r0 / kSlice, q1 = (r1 - 1) / kSlice;
-    // phase 1: one row per lane, one 32-row slice per warp
-    for (int64_t q = q0 + warp; q <= q1; q += nwarps) {
-      const int64_t r = q * kSlice + lane;
-      if (r >= r0 && r < r1) {
-        const int n = UNIFORM ? k : len[r];
-        const int w = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
-        const int64_t base = UNIFORM ? q * kSlice * (int64_t)k : off[q];
-        const double acc = sell_row_dot(sval, scol, base, w, lane, n, V);
-        q_s[r - r0] = fma(gamma, acc, g[r]);
+    // phase 1: one row per lane, RPL 32-row slices per warp step
+    if constexpr (RPL == 1) {
+      for (int64_t q = q0 + warp; q <= q1; q += nwarps) {
+        const int64_t r = q * kSlice + lane;
+        if (r >= r0 && r < r1) {
+          const int n = UNIFORM ? k : len[r];
+          const int w = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
+          const int64_t base = UNIFORM ? q * kSlice * (int64_t)k : off[q];
+          const double acc = sell_row_dot<double, double, V256>(sval, scol, base, w, lane, n, V);
+          q_s[r - r0] = fma(gamma, acc, g[r]);
+        }
+      }
+    } else {
+      static_assert(RPL == 2, "one or two rows per lane");
+      for (int64_t q = q0 + 2 * warp; q <= q1; q += 2 * nwarps) {
+        const int64_t ra = q * kSlice + lane, rb = ra + kSlice;
+        const bool in_a = ra >= r0 && ra < r1, in_b = q + 1 <= q1 && rb >= r0 && rb < r1;
+        int na = 0, nb_ = 0, wa = 0, wb = 0;
+        int64_t ba = 0, bb = 0;
+        if (in_a) {
+          na = UNIFORM ? k : len[ra];
+          wa = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
+          ba = UNIFORM ? q * kSlice * (int64_t)k : off[q];
+        }
+        if (in_b) {
+          nb_ = UNIFORM ? k : len[rb];
+          wb = UNIFORM ? k : (int)((off[q + 2] - off[q + 1]) / kSlice);
+          bb = UNIFORM ? (q + 1) * kSlice * (int64_t)k : off[q + 1];
+        }
+        double acc_a, acc_b;
+        sell_row_dot2<double, double, V256>(sval, scol, ba, wa, na, bb, wb, nb_, lane, V, acc_a, acc_b);
+        if (in_a) q_s[ra - r0] = fma(gamma, acc_a, g[ra]);
+        if (in_b) q_s[rb - r0] = fma(gamma, acc_b, g[rb]);
       }
     }
     __syncthreads();

@@ -210,7 +210,7 @@ struct GraphKey {
   const void* basis;
   const void* basis32;
   double gamma, atol, alpha;
-  int max_pi, max_ksp, m, refine, precision, tile, blocks, pstore, lowp, lp_ts, lp_blocks;
+  int max_pi, max_ksp, m, refine, precision, tile, blocks, rpl, v256, pstore, lowp, lp_ts, lp_blocks;
 };
 
 struct GraphCache {
@@ -516,6 +516,8 @@ mdp_status graph_solve(mdp_s* h, const mdp_solve_opts* o, double* V, int32_t* pi
   key.precision = o->precision;
   key.tile = h->bell_tile_states;
   key.blocks = h->bell_blocks;
+  key.rpl = h->bell_rpl;
+  key.v256 = h->bell_v256;
   key.pstore = h->pstore;
   key.lowp = (o->lowp_sweep && lowp_available(h)) ? 1 : 0;
   key.lp_ts = h->lp_ts;

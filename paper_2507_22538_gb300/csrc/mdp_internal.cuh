@@ -96,6 +96,8 @@ struct mdp_s {
   int bell_blocks = 0;
   int bell_max_per_sm = 0;   // resident blocks per SM the tile allows (occupancy calculator)
   int bell_per_sm_cap = 0;   // blocks per SM the grid uses, chosen by mdp_tune (0: bell_max_per_sm)
+  int bell_rpl = 1;          // rows of the stacked matrix per lane and warp step (1 or 2), chosen by mdp_tune
+  int bell_v256 = 0;         // 1: binary64 values of a chunk in one 32-byte load (chosen by mdp_tune)
 
   // vector-kernel launch shape (thread per state)
   int vec_threads = 256;

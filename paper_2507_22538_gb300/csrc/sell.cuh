@@ -44,10 +44,27 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int (&v)[kChunk]) {
   v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
 }
 
+// One chunk of binary64 values with a single 32-byte load (256-bit vector load of the
+// read-only path); the chunk starts on a 32-byte boundary (a multiple of 4 elements
+// from a 256-byte aligned slice).
+__device__ __forceinline__ void load_chunk_v256(const double* p, double (&v)[kChunk]) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+}
+
+// The value load of one chunk: two 16-byte loads (load_chunk), or with V256 (binary64
+// only) one 32-byte load.  The launch-shape tuner picks the width per matrix.
+template <bool V256, typename TP>
+__device__ __forceinline__ void load_vals(const TP* p, TP (&v)[kChunk]) {
+  if constexpr (V256 && sizeof(TP) == sizeof(double))
+    load_chunk_v256(reinterpret_cast<const double*>(p), reinterpret_cast<double(&)[kChunk]>(v));
+  else
+    load_chunk(p, v);
+}
+
 // sum_j val[j] * x[col[j]] over the n entries of lane `lane`'s row in a slice
 // (start `base`, width w; n <= w), in ascending j, accumulated in TX.  Full
 // chunks go two at a time (8 independent loads in flight), the rest one by one.
-template <typename TP, typename TX>
+template <typename TP, typename TX, bool V256 = false>
 __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const int32_t* __restrict__ col, int64_t base,
                                            int w, int lane, int n, const TX* __restrict__ x) {
   const TP* vp = val + base + lane * kChunk;
@@ -59,8 +76,8 @@ __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const int
   for (; c + 2 <= nc; c += 2) {
     TP v0[kChunk], v1[kChunk];
     int c0[kChunk], c1[kChunk];
-    load_chunk(vp + c * kStride, v0);
-    load_chunk(vp + (c + 1) * kStride, v1);
+    load_vals<V256>(vp + c * kStride, v0);
+    load_vals<V256>(vp + (c + 1) * kStride, v1);
     load_chunk(cp + c * kStride, c0);
     load_chunk(cp + (c + 1) * kStride, c1);
 #pragma unroll
@@ -71,7 +88,7 @@ __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const int
   if (c < nc) {
     TP v0[kChunk];
     int c0[kChunk];
-    load_chunk(vp + c * kStride, v0);
+    load_vals<V256>(vp + c * kStride, v0);
     load_chunk(cp + c * kStride, c0);
 #pragma unroll
     for (int u = 0; u < kChunk; ++u) acc = fma(static_cast<TX>(v0[u]), __ldg(x + c0[u]), acc);
@@ -81,6 +98,55 @@ __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const int
     acc = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc);
   }
   return acc;
+}
+
+// Two rows per lane (lane `lane` of two slices, starts base0/base1, widths w0/w1,
+// n0/n1 entries; n = 0 for a row the lane does not own): the chunks of both rows are
+// loaded side by side, so a warp keeps twice the loads in flight with the same
+// registers per row, while each row's sum is the same chain of fused multiply-adds,
+// in the same order, as sell_row_dot's: the results are equal bit for bit.
+template <typename TP, typename TX, bool V256 = false>
+__device__ __forceinline__ void sell_row_dot2(const TP* __restrict__ val, const int32_t* __restrict__ col,
+                                              int64_t base0, int w0, int n0, int64_t base1, int w1, int n1,
+                                              int lane, const TX* __restrict__ x, TX& acc0, TX& acc1) {
+  constexpr int64_t kStride = kSlice * kChunk;
+  const TP* vp0 = val + base0 + lane * kChunk;
+  const int32_t* cp0 = col + base0 + lane * kChunk;
+  const TP* vp1 = val + base1 + lane * kChunk;
+  const int32_t* cp1 = col + base1 + lane * kChunk;
+  const int nc0 = n0 / kChunk, nc1 = n1 / kChunk;
+  const int nc = nc0 > nc1 ? nc0 : nc1;
+  acc0 = TX(0);
+  acc1 = TX(0);
+  for (int c = 0; c < nc; ++c) {
+    TP v0[kChunk], v1[kChunk];
+    int c0[kChunk], c1[kChunk];
+    const bool has0 = c < nc0, has1 = c < nc1;
+    if (has0) {
+      load_vals<V256>(vp0 + c * kStride, v0);
+      load_chunk(cp0 + c * kStride, c0);
+    }
+    if (has1) {
+      load_vals<V256>(vp1 + c * kStride, v1);
+      load_chunk(cp1 + c * kStride, c1);
+    }
+    if (has0) {
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) acc0 = fma(static_cast<TX>(v0[u]), __ldg(x + c0[u]), acc0);
+    }
+    if (has1) {
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) acc1 = fma(static_cast<TX>(v1[u]), __ldg(x + c1[u]), acc1);
+    }
+  }
+  for (int j = nc0 * kChunk; j < n0; ++j) {
+    const int64_t i = sell_at(base0, w0, lane, j);
+    acc0 = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc0);
+  }
+  for (int j = nc1 * kChunk; j < n1; ++j) {
+    const int64_t i = sell_at(base1, w1, lane, j);
+    acc1 = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc1);
+  }
 }
 
 }  // namespace mdp

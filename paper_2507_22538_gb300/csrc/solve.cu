@@ -90,7 +90,9 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   const int start = h->bell_tile_states;
   int best = start;
   float best_ms = 0.f;
-  h->bell_per_sm_cap = 0;  // tiles are compared at full occupancy
+  h->bell_per_sm_cap = 0;  // tiles are compared at full occupancy, one row per lane, 16-byte loads
+  h->bell_rpl = 1;
+  h->bell_v256 = 0;
   MDP_TRY(configure_bellman(h));
   MDP_TRY(time_one(&best_ms));
   static const int kCandidates[] = {8, 16, 32, 64, 128, 256, 512};
@@ -113,6 +115,27 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   }
   h->bell_tile_states = best;
   MDP_TRY(configure_bellman(h));
+  // then, for that tile, rows per lane (32 or 64 rows per warp step) and the width of
+  // the value loads (16 or 32 bytes), each at full occupancy
+  {
+    int best_rpl = 1, best_v = 0;
+    static const int kVariants[3][2] = {{1, 1}, {2, 0}, {2, 1}};
+    for (const auto& var : kVariants) {
+      h->bell_rpl = var[0];
+      h->bell_v256 = var[1];
+      MDP_TRY(configure_bellman(h));
+      float ms = 0.f;
+      MDP_TRY(time_one(&ms));
+      if (ms < 0.98f * best_ms) {
+        best_rpl = var[0];
+        best_v = var[1];
+        best_ms = ms;
+      }
+    }
+    h->bell_rpl = best_rpl;
+    h->bell_v256 = best_v;
+    MDP_TRY(configure_bellman(h));
+  }
   // then the grid: resident blocks per SM from the occupancy limit down (fewer blocks
   // leave each SM's L1 and request queues to fewer tiles at a time)
   {
@@ -167,6 +190,42 @@ mdp_status mdp_tune(mdp_handle h, double gamma, int32_t* tile_states, float* ms_
   MDP_CUDA(cudaEventRecord(h->done, st));
   if (tile_states) *tile_states = best;
   if (ms_per_sweep) *ms_per_sweep = best_ms;
+  return MDP_OK;
+}
+
+mdp_status mdp_set_sweep_shape(mdp_handle h, int32_t tile_states, int32_t rows_per_warp, int32_t value_load_bytes,
+                               int32_t blocks_per_sm) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (tile_states < 1 || tile_states > 4096 || (rows_per_warp != 32 && rows_per_warp != 64) ||
+      (value_load_bytes != 16 && value_load_bytes != 32) || blocks_per_sm < 0)
+    return fail(MDP_ERR_INVALID_ARG,
+                "need 1 <= tile_states <= 4096, rows_per_warp 32 or 64, value_load_bytes 16 or 32, blocks_per_sm >= 0");
+  if ((size_t)tile_states * h->A * sizeof(double) > 227 * 1024)
+    return fail(MDP_ERR_INVALID_ARG, "the tile's Q values do not fit in shared memory");
+  const int old_ts = h->bell_tile_states, old_rpl = h->bell_rpl, old_v = h->bell_v256, old_cap = h->bell_per_sm_cap;
+  h->bell_tile_states = tile_states;
+  h->bell_rpl = rows_per_warp / kSlice;
+  h->bell_v256 = value_load_bytes == 32 ? 1 : 0;
+  h->bell_per_sm_cap = blocks_per_sm;
+  const mdp_status s = configure_bellman(h);
+  if (s != MDP_OK) {  // keep the previous shape
+    h->bell_tile_states = old_ts;
+    h->bell_rpl = old_rpl;
+    h->bell_v256 = old_v;
+    h->bell_per_sm_cap = old_cap;
+    configure_bellman(h);
+  }
+  return s;
+}
+
+mdp_status mdp_get_sweep_shape(mdp_handle h, int32_t* tile_states, int32_t* blocks, int32_t* blocks_per_sm,
+                               int32_t* rows_per_warp, int32_t* value_load_bytes) {
+  if (!h) return fail(MDP_ERR_INVALID_ARG, "null handle");
+  if (tile_states) *tile_states = h->bell_tile_states;
+  if (blocks) *blocks = h->bell_blocks;
+  if (blocks_per_sm) *blocks_per_sm = h->bell_per_sm_cap;
+  if (rows_per_warp) *rows_per_warp = kSlice * h->bell_rpl;
+  if (value_load_bytes) *value_load_bytes = h->bell_v256 ? 32 : 16;
   return MDP_OK;
 }
 

@@ -87,6 +87,8 @@ _SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_int), _P]),
     "mdp_tune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
                                 _P]),
+    "mdp_get_sweep_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 5),
+    "mdp_set_sweep_shape": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mdp_last_error": (ctypes.c_char_p, []),
     "mdp_bellman_csr_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_double,
                                                _P, _P, _P, _P, _P]),
@@ -217,6 +219,20 @@ def mdp_tune(h, gamma, stream=None):
     ms = ctypes.c_float(0.0)
     st = load().mdp_tune(h, float(gamma), ctypes.byref(ts), ctypes.byref(ms), _stream(stream))
     return st, ts.value, ms.value
+
+
+def mdp_set_sweep_shape(h, tile_states, rows_per_warp=32, value_load_bytes=16, blocks_per_sm=0):
+    return load().mdp_set_sweep_shape(h, int(tile_states), int(rows_per_warp), int(value_load_bytes),
+                                      int(blocks_per_sm))
+
+
+def mdp_get_sweep_shape(h):
+    """(status, {tile_states, blocks, blocks_per_sm, rows_per_warp, value_load_bytes}) of the
+    handle's Bellman sweep."""
+    v = [ctypes.c_int32() for _ in range(5)]
+    st = load().mdp_get_sweep_shape(h, *[ctypes.byref(x) for x in v])
+    return st, dict(zip(("tile_states", "blocks", "blocks_per_sm", "rows_per_warp", "value_load_bytes"),
+                        (x.value for x in v)))
 
 
 def mdp_solve_batch(handles, opts, V, pi, stream=None):

@@ -163,6 +163,73 @@ def test_tune_keeps_results(S, A, k):
     assert torch.equal(TV0, TV1) and torch.equal(pi0, pi1) and torch.equal(r0, r1)
 
 
+SHAPES = [(tile, rpw, vb, bps) for tile in (8, 37, 64, 256) for rpw in (32, 64) for vb in (16, 32)
+          for bps in (0, 1)]
+
+
+@pytest.mark.parametrize("name", ["c1_shape", "ragged_tail_states", "many_actions", "long_rows", "k1_deterministic",
+                                  "tiny", "banded", "ragged_rows", "ragged_rows_big_A"])
+def test_every_sweep_shape_gives_the_same_bits(name):
+    """The launch shapes the tuner chooses among (states per tile, 32 or 64 rows per
+    warp step, 16- or 32-byte value loads, blocks per SM): every one gives the oracle-
+    checked default sweep's TV, policy and residual bit for bit."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = dict(CASES)[name]()
+    V = torch.from_numpy(random_value_vector(m.S, 3, scale=1.0 / (1 - m.gamma))).cuda()
+    with mdp.MDP.from_data(m) as M:
+        TV0, pi0, r0 = M.bellman(m.gamma, V)
+        seen = 0
+        for tile, rpw, vb, bps in SHAPES:
+            st = mdp.mdp_set_sweep_shape(M.h, tile, rpw, vb, bps)
+            if tile * m.A * 8 > 227 * 1024:
+                assert st == mdp.MDP_ERR_INVALID_ARG
+                continue
+            assert st == mdp.MDP_OK, mdp.mdp_last_error()
+            st, shape = mdp.mdp_get_sweep_shape(M.h)
+            assert shape["tile_states"] == tile and shape["rows_per_warp"] == rpw
+            assert shape["value_load_bytes"] == vb and shape["blocks"] >= 1
+            TV1, pi1, r1 = M.bellman(m.gamma, V)
+            torch.cuda.synchronize()
+            assert torch.equal(TV0, TV1) and torch.equal(pi0, pi1) and torch.equal(r0, r1), (tile, rpw, vb, bps)
+            seen += 1
+        assert seen >= 8
+        assert mdp.mdp_set_sweep_shape(M.h, 64, 48, 16, 0) == mdp.MDP_ERR_INVALID_ARG
+        assert mdp.mdp_set_sweep_shape(M.h, 64, 32, 8, 0) == mdp.MDP_ERR_INVALID_ARG
+        assert mdp.mdp_set_sweep_shape(M.h, 0, 32, 16, 0) == mdp.MDP_ERR_INVALID_ARG
+
+
+def test_tuned_shape_solves_the_same():
+    """After mdp_tune (tile, rows per warp step, load width, grid) a stream- and a
+    graph-driven solve give the untuned solve's V, policy and counts bit for bit."""
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m = banded_birth_death(20000, 20, 33, 0.999)
+    with mdp.MDP.from_data(m) as M:
+        def solve(graph):
+            V = torch.zeros(m.S, dtype=torch.float64, device="cuda")
+            pi = torch.empty(m.S, dtype=torch.int32, device="cuda")
+            o = mdp.mdp_default_opts()
+            o.gamma, o.atol_pi, o.alpha, o.graph = m.gamma, 1e-8, 0.01, graph
+            st, stats = mdp.mdp_solve(M.h, o, V, pi, None)
+            torch.cuda.synchronize()
+            assert st == mdp.MDP_OK
+            return V.cpu(), pi.cpu(), stats.outer_iters, stats.inner_iters_total, stats.final_residual
+        ref = solve(0)
+        st, ts, ms = mdp.mdp_tune(M.h, m.gamma)
+        assert st == mdp.MDP_OK
+        st, shape = mdp.mdp_get_sweep_shape(M.h)
+        assert shape["rows_per_warp"] in (32, 64) and shape["value_load_bytes"] in (16, 32)
+        for graph in (0, 1):
+            out = solve(graph)
+            assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]) and out[2:] == ref[2:]
+        # a hand-set shape of each variant
+        for rpw, vb in ((64, 32), (32, 32), (64, 16)):
+            assert mdp.mdp_set_sweep_shape(M.h, 32, rpw, vb, 0) == mdp.MDP_OK
+            out = solve(1)
+            assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]) and out[2:] == ref[2:]
+
+
 def test_live_handle_survives_a_handle_with_a_smaller_tile():
     """The sweep's dynamic shared memory cap is one setting per kernel and device,
     shared by all handles: creating a handle whose Q tile needs less (A = 29: 256
