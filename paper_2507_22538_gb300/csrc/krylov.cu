@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
                                                                    const double* __restrict__ b,
                                                                    T* __restrict__ u0, double* partials,
                                                                    KrylovState* K) {
+  pdl_begin();
   gm_residual_body<U, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, theta, b, u0, partials, K);
 }
 
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const TP* __rest
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
                                                                  double gamma, const T* __restrict__ basis, int j,
                                                                  T* __restrict__ w, const KrylovState* K) {
+  pdl_begin();
   gm_matvec_body<U, TP, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w, K);
 }
 
@@ -76,6 +78,7 @@ template <int NB, typename T, bool FINE>
 __global__ void __launch_bounds__(kVecThreads) gm_dots_kernel(int64_t S, const T* __restrict__ basis, int j,
                                                                const T* __restrict__ w, double* partials,
                                                                KrylovState* K) {
+  pdl_begin();
   gm_dots_body<NB, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
@@ -92,6 +95,7 @@ __global__ void __launch_bounds__(kVecThreads, mvd_min_blocks(NB)) gm_matvec_dot
                                                                        const double* __restrict__ basis, int j,
                                                                        double* __restrict__ w, double* partials,
                                                                        KrylovState* K) {
+  pdl_begin();
   gm_matvec_dots_body<U, NB>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w,
                              partials, K);
 }
@@ -103,6 +107,7 @@ template <int NB, bool FINE>
 __global__ void __launch_bounds__(kVecThreads, 4) gm_dots32_kernel(int64_t S, const float* __restrict__ basis, int j,
                                                                    const float* __restrict__ w, double* partials,
                                                                    KrylovState* K) {
+  pdl_begin();
   gm_dots_body<NB, float, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
@@ -119,12 +124,14 @@ template <int NB, int MODE, typename T, bool FINE>
 __global__ void __launch_bounds__(kVecThreads, kProjectMinBlocks) gm_project_kernel(int64_t S, T* __restrict__ basis, int j,
                                                                   const T* __restrict__ w, double* partials,
                                                                   KrylovState* K) {
+  pdl_begin();
   gm_project_body<NB, MODE, T, FINE>((int)blockIdx.x, (int)gridDim.x, S, basis, j, w, partials, K);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) gm_update_kernel(int64_t S, const T* __restrict__ basis,
                                                                  double* __restrict__ theta, KrylovState* K) {
+  pdl_begin();
   gm_update_body<T>((int)blockIdx.x, (int)gridDim.x, S, basis, theta, K);
 }
 
@@ -488,17 +495,17 @@ static mdp_status launch_matvec(mdp_s* h, const KrylovBuffers<T>& B, double gamm
   const int k = U ? Q.kmax : 0;
   KrylovState* K = kstate(h);
   if (sizeof(T) == sizeof(double)) {
-    gm_matvec_kernel<U, T, T><<<MDP_WAVE((gm_matvec_kernel<U, T, T>)), kVecThreads, 0, st>>>(
-        (const T*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, T, T>, MDP_WAVE((gm_matvec_kernel<U, T, T>)), kVecThreads, 0, st,
+        (const T*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
   } else if (h->pstore == kStoreF16) {
-    gm_matvec_kernel<U, __half, T><<<MDP_WAVE((gm_matvec_kernel<U, __half, T>)), kVecThreads, 0, st>>>(
-        (const __half*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, __half, T>, MDP_WAVE((gm_matvec_kernel<U, __half, T>)), kVecThreads, 0, st,
+        (const __half*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
   } else if (h->pstore == kStoreBF16) {
-    gm_matvec_kernel<U, __nv_bfloat16, T><<<MDP_WAVE((gm_matvec_kernel<U, __nv_bfloat16, T>)), kVecThreads, 0, st>>>(
-        (const __nv_bfloat16*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, __nv_bfloat16, T>, MDP_WAVE((gm_matvec_kernel<U, __nv_bfloat16, T>)), kVecThreads, 0, st,
+        (const __nv_bfloat16*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
   } else {
-    gm_matvec_kernel<U, float, T><<<MDP_WAVE((gm_matvec_kernel<U, float, T>)), kVecThreads, 0, st>>>(
-        (const float*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K);
+    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, float, T>, MDP_WAVE((gm_matvec_kernel<U, float, T>)), kVecThreads, 0, st,
+        (const float*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
   }
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
@@ -514,12 +521,12 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   if constexpr (FINE && sizeof(T) == sizeof(double)) {
     // binary64, single pass: the mat-vec fused with the dots, then the projection
     const Sell& Q = h->Ppi;
-    gm_matvec_dots_kernel<U, NB><<<MDP_WAVE((gm_matvec_dots_kernel<U, NB>)), kVecThreads, 0, st>>>(
-        Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, S, gamma, B.basis, j, B.w, h->partials, K);
+    MDP_CUDA(launch_pdl(gm_matvec_dots_kernel<U, NB>, MDP_WAVE((gm_matvec_dots_kernel<U, NB>)), kVecThreads, 0, st,
+        Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, S, gamma, B.basis, j, B.w, h->partials, K));
     MDP_LAUNCH_CHECK(h);
     if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
-    gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
-        S, B.basis, j, B.w, h->partials, K);
+    MDP_CUDA(launch_pdl(gm_project_kernel<NB, kPlain, T, FINE>, MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st,
+        S, B.basis, j, B.w, h->partials, K));
     MDP_LAUNCH_CHECK(h);
     if (timed && h->gs_on) MDP_CUDA(cudaEventRecord(h->gs_ev[j], st));
     return MDP_OK;
@@ -527,23 +534,23 @@ static mdp_status arnoldi_step(mdp_s* h, const KrylovBuffers<T>& B, double gamma
   mdp_status r = launch_matvec<U>(h, B, gamma, j, st);
   if (r != MDP_OK) return r;
   if (timed) MDP_CUDA(cudaEventRecord(h->mv_ev[2 * j + 1], st));
-  dots_kernel<NB, T, FINE>()<<<MDP_WAVE((dots_kernel<NB, T, FINE>())), kVecThreads, 0, st>>>(S, B.basis, j, B.w,
-                                                                                            h->partials, K);
+  MDP_CUDA(launch_pdl(dots_kernel<NB, T, FINE>(), MDP_WAVE((dots_kernel<NB, T, FINE>())), kVecThreads, 0, st, S, B.basis, j, B.w,
+                                                                                            h->partials, K));
   MDP_LAUNCH_CHECK(h);
   if (refine == MDP_REFINE_NEVER) {
-    gm_project_kernel<NB, kPlain, T, FINE><<<MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st>>>(
-        S, B.basis, j, B.w, h->partials, K);
+    MDP_CUDA(launch_pdl(gm_project_kernel<NB, kPlain, T, FINE>, MDP_WAVE((gm_project_kernel<NB, kPlain, T, FINE>)), kVecThreads, 0, st,
+        S, B.basis, j, B.w, h->partials, K));
     MDP_LAUNCH_CHECK(h);
     if (timed && h->gs_on) MDP_CUDA(cudaEventRecord(h->gs_ev[j], st));
     return MDP_OK;
   }
   if constexpr (!FINE && (NB == 8 || NB == 16 || NB == 32)) {  // re-orthogonalised steps use the coarse widths only
     if (refine == MDP_REFINE_IFNEEDED)
-      gm_project_kernel<NB, kDgks, T, false><<<MDP_WAVE((gm_project_kernel<NB, kDgks, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+      MDP_CUDA(launch_pdl(gm_project_kernel<NB, kDgks, T, false>, MDP_WAVE((gm_project_kernel<NB, kDgks, T, false>)), kVecThreads, 0, st, S, B.basis, j, B.w, h->partials, K));
     else
-      gm_project_kernel<NB, kAlways, T, false><<<MDP_WAVE((gm_project_kernel<NB, kAlways, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+      MDP_CUDA(launch_pdl(gm_project_kernel<NB, kAlways, T, false>, MDP_WAVE((gm_project_kernel<NB, kAlways, T, false>)), kVecThreads, 0, st, S, B.basis, j, B.w, h->partials, K));
     MDP_LAUNCH_CHECK(h);
-    gm_project_kernel<NB, kSecond, T, false><<<MDP_WAVE((gm_project_kernel<NB, kSecond, T, false>)), kVecThreads, 0, st>>>(S, B.basis, j, B.w, h->partials, K);
+    MDP_CUDA(launch_pdl(gm_project_kernel<NB, kSecond, T, false>, MDP_WAVE((gm_project_kernel<NB, kSecond, T, false>)), kVecThreads, 0, st, S, B.basis, j, B.w, h->partials, K));
     MDP_LAUNCH_CHECK(h);
     return MDP_OK;
   } else {
@@ -654,9 +661,9 @@ template <bool U, typename T>
 static mdp_status gm_residual(mdp_s* h, const KrylovBuffers<T>& B, double gamma, const double* theta,
                               cudaStream_t st) {
   const Sell& Q = h->Ppi;
-  gm_residual_kernel<U, T><<<MDP_WAVE((gm_residual_kernel<U, T>)), kVecThreads, 0, st>>>(Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+  MDP_CUDA(launch_pdl(gm_residual_kernel<U, T>, MDP_WAVE((gm_residual_kernel<U, T>)), kVecThreads, 0, st, Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
                                                                    gamma, theta, h->gpi, B.basis, h->partials,
-                                                                   kstate(h));
+                                                                   kstate(h)));
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
@@ -772,7 +779,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
       r = arnoldi_dispatch<U>(h, B, gamma, j, refine, st);
       if (r != MDP_OK) return r;
     }
-    gm_update_kernel<T><<<MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st>>>(h->S, B.basis, theta, K);
+    MDP_CUDA(launch_pdl(gm_update_kernel<T>, MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st, h->S, B.basis, theta, K));
     MDP_LAUNCH_CHECK(h);
     r = gm_residual<U>(h, B, gamma, theta, st);
     if (r != MDP_OK) return r;
@@ -990,7 +997,7 @@ static mdp_status steps_launch(mdp_s* h, double gamma, int j0, int j1, int refin
 template <bool U, typename T>
 static mdp_status tail_launch(mdp_s* h, double gamma, double* theta, cudaStream_t st) {
   const KrylovBuffers<T> B = buffers(h, (T*)nullptr);
-  gm_update_kernel<T><<<MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st>>>(h->S, B.basis, theta, kstate(h));
+  MDP_CUDA(launch_pdl(gm_update_kernel<T>, MDP_WAVE(gm_update_kernel<T>), kVecThreads, 0, st, h->S, B.basis, theta, kstate(h)));
   MDP_LAUNCH_CHECK(h);
   return gm_residual<U>(h, B, gamma, theta, st);
 }

@@ -54,6 +54,36 @@ struct NvtxRange {
     if (e_ != cudaSuccess) return ::mdp::cuda_fail(e_, #call); \
   } while (0)
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with launch_pdl
+// may be scheduled while the previous kernel on its stream is still finishing, so its
+// launch and block scheduling overlap that kernel's tail (the last block's grid
+// reduction).  Every such kernel calls pdl_begin() before touching memory:
+// griddepcontrol.wait returns once the previous kernel has completed and its writes
+// are visible, so results and stream order are unchanged; launch_dependents then
+// lets the next kernel start launching.  Both are no-ops in a launch without the
+// attribute.  A probe of back-to-back dependent reducing kernels at 10^6 states
+// measured about 2 us less per kernel boundary.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+  static_assert(sizeof...(KArgs) == sizeof...(Args), "kernel argument count");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Sliced-ELL (slice height 32) copy of a row-major matrix: slice q holds rows
 // 32q..32q+31, each padded to the slice's width w.  The first w & ~3 entries of
 // a row are stored in chunks of 4 consecutive entries (chunk c of lane l at
