@@ -364,8 +364,8 @@ def run_serving(n, slots=4, seed=5):
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, size=n)
     arrivals = np.cumsum(gaps) - gaps[0]
 
-    def drive(arr, batch_max):
-        svc = SolveService(slots=slots, hbm_budget=120 << 30, batch_max=batch_max).start()
+    def drive(arr, batch_max, graph=True):
+        svc = SolveService(slots=slots, hbm_budget=120 << 30, batch_max=batch_max, graph=graph).start()
         t0 = svc.now()
         for r, a in zip(reqs, arr):
             wait = t0 + a - svc.now()
@@ -381,6 +381,8 @@ def run_serving(n, slots=4, seed=5):
         return out, summ, svc
 
     res, cont, svc = drive(arrivals, 1)
+    # the same arrivals served by stream-driven solves
+    _, cont_stream, _ = drive(arrivals, 1, graph=False)
     # the same arrivals, and a burst of all n at once, with waiting requests solved
     # together by mdp_solve_batch (up to 8 per call)
     resb, cont_b, _ = drive(arrivals, 8)
@@ -407,6 +409,7 @@ def run_serving(n, slots=4, seed=5):
             "one_at_a_time_stream_driven_mean_s": float(service_stream.mean()),
             "continuous": cont, "one_at_a_time": fifo_one_at_a_time(arrivals, service),
             "one_at_a_time_stream_driven": fifo_one_at_a_time(arrivals, service_stream),
+            "continuous_stream_driven": cont_stream,
             "continuous_batched": cont_b, "burst_continuous": burst1, "burst_batched": burst8,
             "peak_in_flight": svc.peak_in_flight, "results_equal_alone": bool(same),
             "statuses_alone": {int(k): int(v) for k, v in zip(*np.unique([a.status for a in alone], return_counts=True))},

@@ -111,10 +111,10 @@ __global__ void bb_extract_kernel(const BatchProblem* __restrict__ P, const int3
   BATCH_PROLOGUE
   if (p.suniform)
     extract_policy_body<true>(bid, nb, p.sval, p.scol, p.soff, p.slen, p.skmax, p.g, p.pi, p.S, p.A, p.pval, p.pcol,
-                              p.poff, p.plen, p.gpi, p.pval32, p.pval16, p.pstore);
+                              p.poff, p.plen, p.gpi, p.pval32, p.pval16, p.pstore, nullptr, nullptr);
   else
     extract_policy_body<false>(bid, nb, p.sval, p.scol, p.soff, p.slen, p.skmax, p.g, p.pi, p.S, p.A, p.pval, p.pcol,
-                               p.poff, p.plen, p.gpi, p.pval32, p.pval16, p.pstore);
+                               p.poff, p.plen, p.gpi, p.pval32, p.pval16, p.pstore, nullptr, nullptr);
 }
 
 __global__ void __launch_bounds__(kVecThreads) bb_residual_kernel(const BatchProblem* __restrict__ P,

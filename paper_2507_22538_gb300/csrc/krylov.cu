@@ -63,15 +63,17 @@ __global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* 
   gm_residual_body<U, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, theta, b, u0, partials, K);
 }
 
-template <bool U, typename TP, typename T>
+template <bool U, typename TP, typename T, typename TC = int32_t>
 __global__ void __launch_bounds__(kVecThreads) gm_matvec_kernel(const TP* __restrict__ pval,
-                                                                 const int32_t* __restrict__ pcol,
+                                                                 const TC* __restrict__ pcol,
                                                                  const int64_t* __restrict__ poff,
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
                                                                  double gamma, const T* __restrict__ basis, int j,
-                                                                 T* __restrict__ w, const KrylovState* K) {
+                                                                 T* __restrict__ w, const KrylovState* K,
+                                                                 const int32_t* __restrict__ cbase) {
   pdl_begin();
-  gm_matvec_body<U, TP, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w, K);
+  gm_matvec_body<U, TP, T, TC>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, basis, j, w, K,
+                               cbase);
 }
 
 template <int NB, typename T, bool FINE>
@@ -489,24 +491,38 @@ static KrylovBuffers<float> buffers(mdp_s* h, float*) {
   return {h->pstore == kStoreF32 ? (const void*)h->pval32 : (const void*)h->pval16, h->basis32, h->w32};
 }
 
-template <bool U, typename T>
-static mdp_status launch_matvec(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, cudaStream_t st) {
+// The mat-vec of an Arnoldi step with policy values of type TP; the binary32 cycle of a
+// near-diagonal MDP reads the 16-bit column offsets (4 instead of 6 bytes per entry
+// with 16-bit values), with the same products and sums.
+template <bool U, typename TP, typename T>
+static mdp_status launch_matvec_as(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, cudaStream_t st) {
   const Sell& Q = h->Ppi;
   const int k = U ? Q.kmax : 0;
   KrylovState* K = kstate(h);
-  if (sizeof(T) == sizeof(double)) {
-    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, T, T>, MDP_WAVE((gm_matvec_kernel<U, T, T>)), kVecThreads, 0, st,
-        (const T*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
-  } else if (h->pstore == kStoreF16) {
-    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, __half, T>, MDP_WAVE((gm_matvec_kernel<U, __half, T>)), kVecThreads, 0, st,
-        (const __half*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
-  } else if (h->pstore == kStoreBF16) {
-    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, __nv_bfloat16, T>, MDP_WAVE((gm_matvec_kernel<U, __nv_bfloat16, T>)), kVecThreads, 0, st,
-        (const __nv_bfloat16*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
-  } else {
-    MDP_CUDA(launch_pdl(gm_matvec_kernel<U, float, T>, MDP_WAVE((gm_matvec_kernel<U, float, T>)), kVecThreads, 0, st,
-        (const float*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K));
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (h->pcol16) {
+      MDP_CUDA(launch_pdl(gm_matvec_kernel<U, TP, T, int16_t>, MDP_WAVE((gm_matvec_kernel<U, TP, T, int16_t>)),
+                          kVecThreads, 0, st, (const TP*)B.pval, (const int16_t*)h->pcol16, Q.off, Q.len, k, h->S,
+                          gamma, B.basis, j, B.w, K, (const int32_t*)h->pcolbase));
+      return MDP_OK;
+    }
   }
+  MDP_CUDA(launch_pdl(gm_matvec_kernel<U, TP, T>, MDP_WAVE((gm_matvec_kernel<U, TP, T>)), kVecThreads, 0, st,
+                      (const TP*)B.pval, Q.col, Q.off, Q.len, k, h->S, gamma, B.basis, j, B.w, K,
+                      (const int32_t*)nullptr));
+  return MDP_OK;
+}
+
+template <bool U, typename T>
+static mdp_status launch_matvec(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, cudaStream_t st) {
+  if (sizeof(T) == sizeof(double))
+    MDP_TRY((launch_matvec_as<U, T, T>(h, B, gamma, j, st)));
+  else if (h->pstore == kStoreF16)
+    MDP_TRY((launch_matvec_as<U, __half, T>(h, B, gamma, j, st)));
+  else if (h->pstore == kStoreBF16)
+    MDP_TRY((launch_matvec_as<U, __nv_bfloat16, T>(h, B, gamma, j, st)));
+  else
+    MDP_TRY((launch_matvec_as<U, float, T>(h, B, gamma, j, st)));
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
@@ -671,9 +687,9 @@ static mdp_status gm_residual(mdp_s* h, const KrylovBuffers<T>& B, double gamma,
 // Algorithmic bytes of the inner solver: one application of P_pi reads the
 // policy's rows (value + 4 B column per entry) and its x once; the other vector
 // accesses move one element per state.
-static void add_matvec_bytes(mdp_s* h, int n, size_t value_bytes, size_t vec_bytes) {
+static void add_matvec_bytes(mdp_s* h, int n, size_t value_bytes, size_t vec_bytes, size_t col_bytes = 4) {
   const double entries = (double)h->S * (double)h->Ppi.kmax;
-  h->inner_bytes += n * (entries * (double)(value_bytes + 4) + (double)h->S * (double)vec_bytes);
+  h->inner_bytes += n * (entries * (double)(value_bytes + col_bytes) + (double)h->S * (double)vec_bytes);
 }
 
 static void add_vector_bytes(mdp_s* h, int64_t nvec, size_t vec_bytes) {
@@ -691,7 +707,7 @@ static void count_cycle(mdp_s* h, int steps) {
     h->matvecs += 1;
     h->vreads += j + (j + 2);
     h->vwrites += 2;
-    add_matvec_bytes(h, 1, vbytes, sizeof(T));
+    add_matvec_bytes(h, 1, vbytes, sizeof(T), (sizeof(T) == sizeof(float) && h->pcol16) ? 2 : 4);
     add_vector_bytes(h, j + (j + 2) + 2, sizeof(T));
   }
   h->vreads += steps + 1;
@@ -730,7 +746,8 @@ static mdp_status add_matvec_times(mdp_s* h, int n, size_t value_bytes, size_t v
     h->mv_timed += 1;
     // algorithmic bytes of the timed launch: the policy's rows, u_j read and w written,
     // and with the fused binary64 dots the j other basis vectors
-    h->mv_bytes += entries * (double)(value_bytes + 4) + 2.0 * S * (double)vec_bytes;
+    const double col_bytes = (vec_bytes == sizeof(float) && h->pcol16) ? 2.0 : 4.0;  // 16-bit offsets
+    h->mv_bytes += entries * ((double)value_bytes + col_bytes) + 2.0 * S * (double)vec_bytes;
     if (h->gs_on) {
       h->mv_bytes += (double)j * S * (double)vec_bytes;
       MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j + 1], h->gs_ev[j]));
@@ -1038,7 +1055,7 @@ void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int6
   h->matvecs += steps + cycles;
   h->vreads += sq + 2 * steps + 2 * cycles;
   h->vwrites += 2 * steps + 2 * cycles;
-  add_matvec_bytes(h, (int)steps, vbytes, sT);
+  add_matvec_bytes(h, (int)steps, vbytes, sT, (mixed && h->pcol16) ? 2 : 4);
   add_vector_bytes(h, 2 * tri + 5 * steps, sT);
   add_vector_bytes(h, 3 * cycles, sizeof(double));
   add_matvec_bytes(h, (int)cycles, sizeof(double), sizeof(double));

@@ -42,15 +42,19 @@ enum : int {
 };
 
 // sum_j P_pi[s, j] x[col_j] for state s (lane l of slice s/32), in the type of x.
-template <bool UNIFORM, typename TP, typename TX>
-__device__ __forceinline__ TX policy_row_dot(const TP* __restrict__ pval, const int32_t* __restrict__ pcol,
+// With 16-bit columns (TC = int16_t) each entry holds col_j - cbase[s].
+template <bool UNIFORM, typename TP, typename TX, typename TC = int32_t>
+__device__ __forceinline__ TX policy_row_dot(const TP* __restrict__ pval, const TC* __restrict__ pcol,
                                              const int64_t* __restrict__ poff, const int32_t* __restrict__ plen,
-                                             int k, int64_t s, const TX* __restrict__ x) {
+                                             int k, int64_t s, const TX* __restrict__ x,
+                                             const int32_t* __restrict__ cbase = nullptr) {
   const int64_t q = s / kSlice;
   const int n = UNIFORM ? k : plen[s];
   const int w = UNIFORM ? k : (int)((poff[q + 1] - poff[q]) / kSlice);
   const int64_t base = UNIFORM ? q * kSlice * (int64_t)k : poff[q];
-  return sell_row_dot(pval, pcol, base, w, (int)(s % kSlice), n, x);
+  const TX* xs = x;
+  if constexpr (sizeof(TC) == sizeof(int16_t)) xs = x + cbase[s];
+  return sell_row_dot<TP, TX, false, TC>(pval, pcol, base, w, (int)(s % kSlice), n, xs);
 }
 
 // Warp reduce-scatter of N values per lane (N a power of two, N <= 32): each
@@ -282,19 +286,20 @@ __device__ __forceinline__ void gm_residual_body(int bid, int nb, const double* 
 // Arnoldi step, part 1: w = J v_j = sigma_j (u_j - gamma P_pi u_j).  A lean
 // kernel (no reductions, few registers) so that enough warps are resident to
 // keep the row and gather loads of P_pi in flight.
-template <bool U, typename TP, typename T>
+template <bool U, typename TP, typename T, typename TC = int32_t>
 __device__ __forceinline__ void gm_matvec_body(int bid, int nb, const TP* __restrict__ pval,
-                                                                 const int32_t* __restrict__ pcol,
+                                                                 const TC* __restrict__ pcol,
                                                                  const int64_t* __restrict__ poff,
                                                                  const int32_t* __restrict__ plen, int k, int64_t S,
                                                                  double gamma, const T* __restrict__ basis, int j,
-                                                                 T* __restrict__ w, const KrylovState* K) {
+                                                                 T* __restrict__ w, const KrylovState* K,
+                                                                 const int32_t* __restrict__ cbase = nullptr) {
   if (K->flags & (kCycleStop | kSolveDone)) return;
   const T sj = (T)K->sigma[j];
   const T g = (T)gamma;
   const T* uj = basis + (int64_t)j * S;
   for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
-    const T px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj);
+    const T px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, uj, cbase);
     w[s] = sj * (uj[s] - g * px);
   }
 }

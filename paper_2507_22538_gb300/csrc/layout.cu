@@ -69,10 +69,10 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
                                      const TV* __restrict__ val, const double* __restrict__ g, int64_t R,
                                      int64_t S, int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
                                      int* __restrict__ kmin, int* __restrict__ kmax, int* __restrict__ f16_ok,
-                                     int* __restrict__ bf16_ok) {
+                                     int* __restrict__ bf16_ok, int A, int* __restrict__ near_ok) {
   int bad = 0;
   int lmin = 0x7fffffff, lmax = 0;
-  bool a16 = true, b16 = true;
+  bool a16 = true, b16 = true, near = true;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
     int64_t lo = rp[r], hi = rp[r + 1];
     int l = 0;
@@ -85,10 +85,12 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
     } else {
       l = (int)(hi - lo);
       double sum = 0.0;
+      const int c0 = col[lo];  // the row's first column: the base of its 16-bit offsets
       for (int64_t j = lo; j < hi; ++j) {
         int c = col[j];
         double v = widen(val[j]);
         if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
+        near &= ((int64_t)c - c0 >= -32768 && (int64_t)c - c0 <= 32767);
         if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
         const uint64_t bits = (uint64_t)__double_as_longlong(v);
         a16 &= exact_in(bits, 10, -14, 15);
@@ -107,6 +109,7 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
   atomicMax(kmax, lmax);
   if (!__all_sync(0xffffffffu, a16) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
   if (!__all_sync(0xffffffffu, b16) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
+  if (!__all_sync(0xffffffffu, near) && (threadIdx.x & 31) == 0) atomicAnd(near_ok, 0);
 }
 
 // Width of each slice of `rows` rows: the longest row among its 32.
@@ -164,8 +167,9 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
                                       double* __restrict__ pval, int32_t* __restrict__ pcol,
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi, float* __restrict__ pval32,
-                                      uint16_t* __restrict__ pval16, int store16) {
-  extract_policy_body<UNIFORM>((int)blockIdx.x, (int)gridDim.x, sval, scol, off, len, kmax, g, pi, S, A, pval, pcol, poff, plen, gpi, pval32, pval16, store16);
+                                      uint16_t* __restrict__ pval16, int store16, int16_t* __restrict__ pcol16,
+                                      int32_t* __restrict__ pcolbase) {
+  extract_policy_body<UNIFORM>((int)blockIdx.x, (int)gridDim.x, sval, scol, off, len, kmax, g, pi, S, A, pval, pcol, poff, plen, gpi, pval32, pval16, store16, pcol16, pcolbase);
 }
 
 static int grid_for(int64_t n, int threads, int sm_count) {
@@ -264,12 +268,12 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
     extract_policy_kernel<true><<<blocks, 256, 0, st>>>(
         P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,
         want32 && h->pstore == kStoreF32 ? h->pval32 : nullptr, want32 && h->pstore != kStoreF32 ? h->pval16 : nullptr,
-        h->pstore);
+        h->pstore, want32 ? h->pcol16 : nullptr, want32 ? h->pcolbase : nullptr);
   else
     extract_policy_kernel<false><<<blocks, 256, 0, st>>>(
         P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,
         want32 && h->pstore == kStoreF32 ? h->pval32 : nullptr, want32 && h->pstore != kStoreF32 ? h->pval16 : nullptr,
-        h->pstore);
+        h->pstore, want32 ? h->pcol16 : nullptr, want32 ? h->pcolbase : nullptr);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   return MDP_OK;
@@ -293,6 +297,8 @@ static void destroy_handle(mdp_s* h) {
   dfree(st, h->basis);
   dfree(st, h->pval32);
   dfree(st, h->pval16);
+  dfree(st, h->pcol16);
+  dfree(st, h->pcolbase);
   dfree(st, h->basis32);
   dfree(st, h->w32);
   dfree(st, h->tfq);
@@ -320,6 +326,8 @@ static void destroy_handle(mdp_s* h) {
 mdp_status ensure_mixed(mdp_s* h, int nvec) {
   if (h->pstore == kStoreF32 && !h->pval32) MDP_TRY(dalloc(h, &h->pval32, h->Ppi.nstored, "FP32 policy values"));
   if (h->pstore != kStoreF32 && !h->pval16) MDP_TRY(dalloc(h, &h->pval16, h->Ppi.nstored, "16-bit policy values"));
+  if (h->col16 && !h->pcol16) MDP_TRY(dalloc(h, &h->pcol16, h->Ppi.nstored, "16-bit policy column offsets"));
+  if (h->col16 && !h->pcolbase) MDP_TRY(dalloc(h, &h->pcolbase, h->S, "policy row base columns"));
   if (!h->w32) MDP_TRY(dalloc(h, &h->w32, h->S, "FP32 w"));
   if (nvec > h->basis32_cap) {
     dfree(h->stream, h->basis32);
@@ -439,31 +447,35 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_TRY(dalloc(h, &dlen, R, "row lengths"));
   struct FreeLen { cudaStream_t st; int32_t** p; ~FreeLen() { dfree(st, *p); } } free_len{st, &dlen};
   int* dflags = (int*)h->sc;
-  int init[5] = {0, 0x7fffffff, 0, 1, 1};
+  int init[6] = {0, 0x7fffffff, 0, 1, 1, 1};
   MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
   {
     const int vb = grid_for(R, 256, h->sm_count);
     switch (val_type) {
       case MDP_F32:
         validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const float*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
+                                                 dflags + 5);
         break;
       case MDP_F16:
         validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __half*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
+                                                 dflags + 5);
         break;
       case MDP_BF16:
         validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __nv_bfloat16*)dval, h->g, R, S, nnz, dlen,
-                                                 dflags, dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+                                                 dflags, dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
+                                                 dflags + 5);
         break;
       default:
         validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const double*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4);
+                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
+                                                 dflags + 5);
     }
   }
   h->launches++;
   MDP_CUDA(cudaGetLastError());
-  int res[5];
+  int res[6];
   MDP_CUDA(cudaMemcpyAsync(res, dflags, sizeof(res), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaStreamSynchronize(st));
   if (res[0]) {
@@ -482,6 +494,10 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
 
   // narrowest exact storage for the mixed solver's copies of the policy rows
   h->pstore = res[3] ? kStoreF16 : (res[4] ? kStoreBF16 : kStoreF32);
+  // every column within 32767 states of its row's first column (banded and grid MDPs,
+  // and every MDP of at most 32,768 states): the mixed solver's copy of the policy
+  // rows then stores 16-bit column offsets (2 B per entry instead of 4)
+  h->col16 = res[5] != 0;
 
   // stacked matrix in sliced layout
   MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));

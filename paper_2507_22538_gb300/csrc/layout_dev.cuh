@@ -12,7 +12,10 @@ namespace mdp {
 // per (state, 4-entry chunk) with the state fastest: each warp writes whole
 // contiguous chunks and each thread reads one 32-byte run of its row.  States
 // whose pi(s) lies outside [0, A) get an empty row (zero values, column 0) and
-// g_pi = NaN.
+// g_pi = NaN.  With pcol16 set (every column within 32767 of its row's first
+// column), the mixed solver's column copy is written too: the row's first column as
+// pcolbase[s] and column - pcolbase[s] as int16 per entry (base 0 and offsets 0 for
+// an empty row).
 __device__ __forceinline__ void put_narrow(float* p32, uint16_t* p16, int store16, int64_t i, double v) {
   if (p32) p32[i] = (float)v;
   if (p16) p16[i] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v)) : __bfloat16_as_ushort(__double2bfloat16(v));
@@ -25,7 +28,8 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
                                       double* __restrict__ pval, int32_t* __restrict__ pcol,
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi, float* __restrict__ pval32,
-                                      uint16_t* __restrict__ pval16, int store16) {
+                                      uint16_t* __restrict__ pval16, int store16, int16_t* __restrict__ pcol16,
+                                      int32_t* __restrict__ pcolbase) {
   const int nunits = (kmax + kChunk - 1) / kChunk;
   const int64_t work = S * (int64_t)nunits;
   for (int64_t w = bid * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)nb * blockDim.x) {
@@ -46,6 +50,8 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
     const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
     const int pl = (int)(s % kSlice), sl = (int)(r % kSlice);
     const int j0 = u * kChunk;
+    const int cbase = (pcol16 && n > 0) ? scol[sell_at(sbase, sw, sl, 0)] : 0;  // the row's first column
+    if (pcol16 && u == 0) pcolbase[s] = cbase;
     if (UNIFORM && ok && j0 + kChunk <= (kmax & ~(kChunk - 1))) {  // whole chunk on both sides
       double v[kChunk];
       int c[kChunk];
@@ -59,6 +65,9 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
       if (pval16)
 #pragma unroll
         for (int e = 0; e < kChunk; ++e) put_narrow(nullptr, pval16, store16, di + e, v[e]);
+      if (pcol16)
+        *reinterpret_cast<short4*>(pcol16 + di) = make_short4((short)(c[0] - cbase), (short)(c[1] - cbase),
+                                                              (short)(c[2] - cbase), (short)(c[3] - cbase));
       continue;
     }
     for (int j = j0; j < j0 + kChunk && j < pw; ++j) {
@@ -67,12 +76,15 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
         const int64_t si = sell_at(sbase, sw, sl, j);
         const double v = sval[si];
         pval[di] = v;
-        pcol[di] = scol[si];
+        const int c = scol[si];
+        pcol[di] = c;
         put_narrow(pval32, pval16, store16, di, v);
+        if (pcol16) pcol16[di] = (int16_t)(c - cbase);
       } else if (UNIFORM) {
         pval[di] = 0.0;
         pcol[di] = 0;
         put_narrow(pval32, pval16, store16, di, 0.0);
+        if (pcol16) pcol16[di] = 0;
       }
     }
   }

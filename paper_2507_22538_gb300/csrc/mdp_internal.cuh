@@ -147,6 +147,12 @@ struct mdp_s {
   // 1 = binary16, 2 = bfloat16 (the mixed solver's policy rows then use it)
   int pstore = 0;
   uint16_t* pval16 = nullptr;  // [Ppi.nstored], binary16 or bfloat16 bits
+  // every column of P within 32767 of its row's first column (found at creation): the
+  // mixed solver's policy rows then also keep column - base as int16, base = the row's
+  // first column
+  bool col16 = false;
+  int16_t* pcol16 = nullptr;   // [Ppi.nstored]
+  int32_t* pcolbase = nullptr; // [S]
   float* basis32 = nullptr;  // [(restart + 1) * S]
   int basis32_cap = 0;
   float* w32 = nullptr;      // [S]

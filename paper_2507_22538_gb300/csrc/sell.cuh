@@ -43,6 +43,11 @@ __device__ __forceinline__ void load_chunk(const int32_t* p, int (&v)[kChunk]) {
   const int4 a = *reinterpret_cast<const int4*>(p);
   v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
 }
+// 16-bit column offsets (the mixed solver's policy rows of a near-diagonal matrix)
+__device__ __forceinline__ void load_chunk(const int16_t* p, int (&v)[kChunk]) {
+  const short4 a = *reinterpret_cast<const short4*>(p);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
+}
 
 // One chunk of binary64 values with a single 32-byte load (256-bit vector load of the
 // read-only path); the chunk starts on a 32-byte boundary (a multiple of 4 elements
@@ -64,11 +69,12 @@ __device__ __forceinline__ void load_vals(const TP* p, TP (&v)[kChunk]) {
 // sum_j val[j] * x[col[j]] over the n entries of lane `lane`'s row in a slice
 // (start `base`, width w; n <= w), in ascending j, accumulated in TX.  Full
 // chunks go two at a time (8 independent loads in flight), the rest one by one.
-template <typename TP, typename TX, bool V256 = false>
-__device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const int32_t* __restrict__ col, int64_t base,
+// TC is int32_t (columns) or int16_t (offsets from a base the caller folds into x).
+template <typename TP, typename TX, bool V256 = false, typename TC = int32_t>
+__device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const TC* __restrict__ col, int64_t base,
                                            int w, int lane, int n, const TX* __restrict__ x) {
   const TP* vp = val + base + lane * kChunk;
-  const int32_t* cp = col + base + lane * kChunk;
+  const TC* cp = col + base + lane * kChunk;
   constexpr int64_t kStride = kSlice * kChunk;
   const int nc = n / kChunk;  // n <= w, so full chunks all lie in the chunked part
   TX acc = TX(0);

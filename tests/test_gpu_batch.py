@@ -247,3 +247,27 @@ def test_graph_batch_nan_member():
     graph = _batch_v0(ms, _graph_opts([_opts(m, 1e-9, 1e-3, 30, 1000) for m in ms]), V0)
     _same_results(stream, graph, [m.name for m in ms])
     assert graph[1][0] == mdp.MDP_OK and graph[1][1] == mdp.MDP_ERR_NUMERIC
+
+
+@pytest.mark.parametrize("make", [lambda: banded_birth_death(40000, 20, 16, 0.999, quant_bits=11),
+                                  lambda: random_sparse(40000, 6, 12, 0.99, seed=9, quant_bits=11)],
+                         ids=["banded_near_diagonal", "random_far_columns"])
+def test_mixed_column_offsets_equal_int32_columns(make):
+    """A mixed-precision solve whose policy rows keep 16-bit column offsets (every column
+    within 32767 states of its row's state: the banded MDP) or 32-bit columns (random
+    columns over 40,000 states) gives the batched solver's results, which always read
+    32-bit columns, bit for bit; the oracle's Bellman residual certifies the answer."""
+    import torch
+
+    from paper_2507_22538_gb300 import mdp
+    from tests._util import q_tolerance
+    m = make()
+    o = _opts(m, 1e-8, 1e-3, 30, 1000, MIXED)
+    st, V, pi, s1 = _alone(m, o)
+    status, Vb, pib, stats = _batch([m], [_opts(m, 1e-8, 1e-3, 30, 1000, MIXED)])
+    assert st == mdp.MDP_OK and status[0] == mdp.MDP_OK
+    assert np.array_equal(V, Vb[0]) and np.array_equal(pi, pib[0])
+    assert (s1.outer_iters, s1.inner_iters_total) == (stats[0].outer_iters, stats[0].inner_iters_total)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    Q = O.q_values(P, m.g, m.gamma, V, m.S, m.A)
+    assert float(np.max(np.abs(Q.min(axis=1) - V))) <= 1e-8 + q_tolerance(m, V)
