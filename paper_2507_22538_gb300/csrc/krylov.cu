@@ -491,15 +491,15 @@ static KrylovBuffers<float> buffers(mdp_s* h, float*) {
   return {h->pstore == kStoreF32 ? (const void*)h->pval32 : (const void*)h->pval16, h->basis32, h->w32};
 }
 
-// The mat-vec of an Arnoldi step with policy values of type TP; the binary32 cycle of a
-// near-diagonal MDP reads the 16-bit column offsets (4 instead of 6 bytes per entry
-// with 16-bit values), with the same products and sums.
+// The mat-vec of an Arnoldi step with policy values of type TP; the binary32 cycle of an
+// MDP whose rows span at most 32767 columns reads 16-bit values with 16-bit column
+// offsets (4 instead of 6 bytes per entry), with the same products and sums.
 template <bool U, typename TP, typename T>
 static mdp_status launch_matvec_as(mdp_s* h, const KrylovBuffers<T>& B, double gamma, int j, cudaStream_t st) {
   const Sell& Q = h->Ppi;
   const int k = U ? Q.kmax : 0;
   KrylovState* K = kstate(h);
-  if constexpr (sizeof(T) == sizeof(float)) {
+  if constexpr (sizeof(T) == sizeof(float) && sizeof(TP) == 2) {
     if (h->pcol16) {
       MDP_CUDA(launch_pdl(gm_matvec_kernel<U, TP, T, int16_t>, MDP_WAVE((gm_matvec_kernel<U, TP, T, int16_t>)),
                           kVecThreads, 0, st, (const TP*)B.pval, (const int16_t*)h->pcol16, Q.off, Q.len, k, h->S,

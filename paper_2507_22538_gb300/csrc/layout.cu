@@ -168,8 +168,15 @@ __global__ void extract_policy_kernel(const double* __restrict__ sval, const int
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi, float* __restrict__ pval32,
                                       uint16_t* __restrict__ pval16, int store16, int16_t* __restrict__ pcol16,
-                                      int32_t* __restrict__ pcolbase) {
+                                      const int32_t* __restrict__ pcolbase) {
   extract_policy_body<UNIFORM>((int)blockIdx.x, (int)gridDim.x, sval, scol, off, len, kmax, g, pi, S, A, pval, pcol, poff, plen, gpi, pval32, pval16, store16, pcol16, pcolbase);
+}
+
+template <bool UNIFORM>
+__global__ void policy_base_kernel(const int32_t* __restrict__ scol, const int64_t* __restrict__ off,
+                                   const int32_t* __restrict__ len, int kmax, const int32_t* __restrict__ pi, int64_t S,
+                                   int A, int32_t* __restrict__ pcolbase) {
+  policy_base_body<UNIFORM>((int)blockIdx.x, (int)gridDim.x, scol, off, len, kmax, pi, S, A, pcolbase);
 }
 
 static int grid_for(int64_t n, int threads, int sm_count) {
@@ -264,6 +271,15 @@ mdp_status extract_policy(mdp_s* h, const int32_t* pi, bool want32, cudaStream_t
   const Sell& P = h->P;
   Sell& Q = h->Ppi;
   const int blocks = extract_blocks(h);
+  if (want32 && h->pcol16) {  // the base columns of the 16-bit offsets first
+    const int bb = grid_for(h->S, 256, h->sm_count);
+    if (P.uniform)
+      policy_base_kernel<true><<<bb, 256, 0, st>>>(P.col, P.off, P.len, P.kmax, pi, h->S, h->A, h->pcolbase);
+    else
+      policy_base_kernel<false><<<bb, 256, 0, st>>>(P.col, P.off, P.len, P.kmax, pi, h->S, h->A, h->pcolbase);
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+  }
   if (P.uniform)
     extract_policy_kernel<true><<<blocks, 256, 0, st>>>(
         P.val, P.col, P.off, P.len, P.kmax, h->g, pi, h->S, h->A, Q.val, Q.col, Q.off, Q.len, h->gpi,
@@ -326,8 +342,12 @@ static void destroy_handle(mdp_s* h) {
 mdp_status ensure_mixed(mdp_s* h, int nvec) {
   if (h->pstore == kStoreF32 && !h->pval32) MDP_TRY(dalloc(h, &h->pval32, h->Ppi.nstored, "FP32 policy values"));
   if (h->pstore != kStoreF32 && !h->pval16) MDP_TRY(dalloc(h, &h->pval16, h->Ppi.nstored, "16-bit policy values"));
-  if (h->col16 && !h->pcol16) MDP_TRY(dalloc(h, &h->pcol16, h->Ppi.nstored, "16-bit policy column offsets"));
-  if (h->col16 && !h->pcolbase) MDP_TRY(dalloc(h, &h->pcolbase, h->S, "policy row base columns"));
+  // 16-bit column offsets go with 16-bit values (4 instead of 6 bytes per entry); beside
+  // binary32 values they measured 1% slower on the whole mixed solve than 32-bit columns
+  if (h->col16 && h->pstore != kStoreF32) {
+    if (!h->pcol16) MDP_TRY(dalloc(h, &h->pcol16, h->Ppi.nstored, "16-bit policy column offsets"));
+    if (!h->pcolbase) MDP_TRY(dalloc(h, &h->pcolbase, h->S, "policy row base columns"));
+  }
   if (!h->w32) MDP_TRY(dalloc(h, &h->w32, h->S, "FP32 w"));
   if (nvec > h->basis32_cap) {
     dfree(h->stream, h->basis32);

@@ -21,6 +21,26 @@ __device__ __forceinline__ void put_narrow(float* p32, uint16_t* p16, int store1
   if (p16) p16[i] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v)) : __bfloat16_as_ushort(__double2bfloat16(v));
 }
 
+// The base column of each policy row for the 16-bit offsets: the first column of
+// row s*A + pi(s) (0 for an empty row), one thread per state, so that the gather's
+// threads read it with one coalesced load per warp instead of each its own sector.
+template <bool UNIFORM>
+__device__ __forceinline__ void policy_base_body(int bid, int nb, const int32_t* __restrict__ scol,
+                                                 const int64_t* __restrict__ off, const int32_t* __restrict__ len,
+                                                 int kmax, const int32_t* __restrict__ pi, int64_t S, int A,
+                                                 int32_t* __restrict__ pcolbase) {
+  for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
+    const int a = pi[s];
+    const bool ok = (a >= 0 && a < A);
+    const int64_t r = s * A + (ok ? a : 0);
+    const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
+    const int64_t q = r / kSlice;
+    const int sw = UNIFORM ? kmax : (int)((off[q + 1] - off[q]) / kSlice);
+    const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
+    pcolbase[s] = n > 0 ? scol[sell_at(sbase, sw, (int)(r % kSlice), 0)] : 0;
+  }
+}
+
 template <bool UNIFORM>
 __device__ __forceinline__ void extract_policy_body(int bid, int nb, const double* __restrict__ sval, const int32_t* __restrict__ scol,
                                       const int64_t* __restrict__ off, const int32_t* __restrict__ len, int kmax,
@@ -29,7 +49,7 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
                                       const int64_t* __restrict__ poff, int32_t* __restrict__ plen,
                                       double* __restrict__ gpi, float* __restrict__ pval32,
                                       uint16_t* __restrict__ pval16, int store16, int16_t* __restrict__ pcol16,
-                                      int32_t* __restrict__ pcolbase) {
+                                      const int32_t* __restrict__ pcolbase) {
   const int nunits = (kmax + kChunk - 1) / kChunk;
   const int64_t work = S * (int64_t)nunits;
   for (int64_t w = bid * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)nb * blockDim.x) {
@@ -50,8 +70,7 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
     const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
     const int pl = (int)(s % kSlice), sl = (int)(r % kSlice);
     const int j0 = u * kChunk;
-    const int cbase = (pcol16 && n > 0) ? scol[sell_at(sbase, sw, sl, 0)] : 0;  // the row's first column
-    if (pcol16 && u == 0) pcolbase[s] = cbase;
+    const int cbase = pcol16 ? pcolbase[s] : 0;  // the row's first column (policy_base_body)
     if (UNIFORM && ok && j0 + kChunk <= (kmax & ~(kChunk - 1))) {  // whole chunk on both sides
       double v[kChunk];
       int c[kChunk];
