@@ -55,6 +55,31 @@ def bellman_bytes():
 
 
 
+_DGEMM = {}
+
+
+def fp64_dgemm_tflops(n=4096, reps=5):
+    """Measured FP64 rate of this GPU: torch.matmul of two n x n binary64 matrices (cuBLAS
+    DGEMM), best of `reps`, 2 n^3 flops each; measured once per process."""
+    if "v" not in _DGEMM:
+        import torch
+        a = torch.rand(n, n, dtype=torch.float64, device="cuda")
+        b = torch.rand(n, n, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) * 1e-3
+            best = t if best is None else min(best, t)
+        _DGEMM["v"] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    return _DGEMM["v"]
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -281,6 +306,29 @@ def run_cpu_oracle_worker(args):
     t, info = cpu_oracle_solve(save_v=args.cpu_oracle_worker)
     print(json.dumps({"seconds": t, "info": info, **cpu_info()}), flush=True)
     return 0
+
+
+def cpu_oracle_all_cores():
+    """The same oracle solve with its BLAS allowed every host core (run after the GPU
+    sections, so it disturbs none of them); scipy's sparse products, most of the solve,
+    stay single-threaded, so this is the oracle as it stands with all cores available,
+    not a parallelised oracle."""
+    nthreads = os.cpu_count() or 1
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(nthreads)
+    fd, npz = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        child = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-worker", npz], input="go\n",
+                               capture_output=True, text=True, env=env, timeout=600)
+        rec = json.loads(child.stdout.strip().splitlines()[-1])
+        return {"value": rec["seconds"], "unit": "s", "threads": nthreads,
+                "note": "BLAS threads = host cores; the sparse products stay single-threaded"}
+    except (subprocess.TimeoutExpired, ValueError, IndexError, KeyError) as e:
+        return {"value": None, "unit": "s", "threads": nthreads, "note": f"failed: {e}"}
+    finally:
+        os.unlink(npz)
 
 
 REFERENCE_BUDGET_S = 150.0  # the reference arm stops timing further solves after this much wall time
@@ -1155,8 +1203,8 @@ def main():
             ev.record(stream)
             marks.append(ev)
             for key in ("outer_iters", "inner_iters_total", "kernel_launches", "bellman_sweeps", "bellman_ms",
-                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed", "matvec_bytes", "gs_ms", "gs_flops",
-                        "gs_timed"):
+                        "inner_ms", "inner_bytes", "matvec_ms", "matvecs_timed", "matvec_bytes", "matvec_flops", "gs_ms",
+                        "gs_flops", "gs_timed"):
                 totals[key] = totals.get(key, 0) + s[key]
             totals["final_residual"] = max(totals.get("final_residual", 0.0), s["final_residual"])
         e1.record(stream)
@@ -1360,6 +1408,13 @@ def main():
                "launches_timed": int(totals["matvecs_timed"]),
                # every Arnoldi step launches one of them; the timed ones are a sample
                "share_of_step": mv_ms * totals["inner_iters_total"] / (ms * args.steps)}
+    # the same launches against the FP64 pipe: 2 (k + j + 2) flops per state (row, dots, w)
+    mv_tflops = totals["matvec_flops"] / (totals["matvec_ms"] * 1e-3) / 1e12 if totals["matvec_ms"] > 0 else None
+    roof_mv["fp64"] = {"bound": "alu", "achieved": mv_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": mv_tflops / FP64_PEAK_TFLOPS if mv_tflops else None,
+                       "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz",
+                       "dgemm_tflops": fp64_dgemm_tflops(),
+                       "frac_of_dgemm": (mv_tflops / fp64_dgemm_tflops()) if mv_tflops and fp64_dgemm_tflops() else None}
     # the FP64 projection of the sampled steps (u_{j+1} = w - sum c_i u_i and ||u||^2): FP64-pipe bound
     gs_tflops = totals["gs_flops"] / (totals["gs_ms"] * 1e-3) / 1e12 if totals["gs_ms"] > 0 else None
     fp64_peak = FP64_PEAK_TFLOPS
@@ -1369,7 +1424,9 @@ def main():
                "frac": gs_tflops / fp64_peak if gs_tflops else None,
                "peak_kind": "derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
                "traffic": None, "launches_timed": int(totals["gs_timed"]),
-               "avg_launch_ms": totals["gs_ms"] / max(1, totals["gs_timed"])}
+               "avg_launch_ms": totals["gs_ms"] / max(1, totals["gs_timed"]),
+               "dgemm_tflops": fp64_dgemm_tflops(),
+               "frac_of_dgemm": (gs_tflops / fp64_dgemm_tflops()) if gs_tflops and fp64_dgemm_tflops() else None}
     inner_roof = {"phase": "inner GMRES solves (all kernels and host round trips)",
                   "achieved": inner_gbs, "unit": "GB/s", "frac": inner_gbs / peak if inner_gbs else None,
                   "bytes": totals["inner_bytes"] / args.steps, "ms_per_step": totals["inner_ms"] / args.steps}
@@ -1449,6 +1506,8 @@ def main():
                                     "sample": f"oracle child failed: {e}; {err[-400:]}"}
         finally:
             os.unlink(oracle_npz)
+        if line["cpu_baseline"].get("value"):
+            line["cpu_baseline"]["all_cores"] = cpu_oracle_all_cores()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

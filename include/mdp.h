@@ -131,6 +131,9 @@ typedef struct {
   double matvec_bytes;        /* algorithmic bytes of the kernels timed in matvec_ms: the policy's rows,
                                  u_j read, w written, and with the fused FP64 dots the j other basis
                                  vectors of step j (record_timing only) */
+  double matvec_flops;        /* FP64 flops of the kernels timed in matvec_ms when the mat-vec also forms the
+                                 Gram-Schmidt dots (FP64 single-pass steps): 2 (k + j + 2) per state for
+                                 step j, k entries per row (record_timing only; 0 otherwise) */
 } mdp_solve_stats;
 
 /* Fill *opts with the Table 1 defaults (gamma is set to 0: the caller must set it). */

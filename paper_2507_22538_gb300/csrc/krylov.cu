@@ -750,6 +750,8 @@ static mdp_status add_matvec_times(mdp_s* h, int n, size_t value_bytes, size_t v
     h->mv_bytes += entries * ((double)value_bytes + col_bytes) + 2.0 * S * (double)vec_bytes;
     if (h->gs_on) {
       h->mv_bytes += (double)j * S * (double)vec_bytes;
+      // the fused kernel's FP64 work: the row (k fused multiply-adds), the j + 1 dots and w
+      h->mv_flops += 2.0 * ((double)h->Ppi.kmax + (double)j + 2.0) * S;
       MDP_CUDA(cudaEventElapsedTime(&ms, h->mv_ev[2 * j + 1], h->gs_ev[j]));
       h->gs_ms += ms;
       h->gs_flops += 2.0 * (double)(j + 2) * S;  // the projection: j + 1 products and ||u||^2

@@ -51,59 +51,61 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
                                       uint16_t* __restrict__ pval16, int store16, int16_t* __restrict__ pcol16,
                                       const int32_t* __restrict__ pcolbase) {
   const int nunits = (kmax + kChunk - 1) / kChunk;
-  const int64_t work = S * (int64_t)nunits;
-  for (int64_t w = bid * (int64_t)blockDim.x + threadIdx.x; w < work; w += (int64_t)nb * blockDim.x) {
-    const int64_t s = w % S;
-    const int u = (int)(w / S);
-    const int a = pi[s];
-    const bool ok = (a >= 0 && a < A);
-    const int64_t r = s * A + (ok ? a : 0);
-    const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
-    if (u == 0) {
-      if (!UNIFORM) plen[s] = n;
-      gpi[s] = ok ? g[r] : __longlong_as_double(0x7ff8000000000000ULL);
-    }
-    const int64_t ps = s / kSlice, q = r / kSlice;
-    const int pw = UNIFORM ? kmax : (int)((poff[ps + 1] - poff[ps]) / kSlice);  // destination slice width
-    const int sw = UNIFORM ? kmax : (int)((off[q + 1] - off[q]) / kSlice);      // source slice width
-    const int64_t pbase = UNIFORM ? ps * kSlice * (int64_t)kmax : poff[ps];
-    const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
-    const int pl = (int)(s % kSlice), sl = (int)(r % kSlice);
-    const int j0 = u * kChunk;
-    const int cbase = pcol16 ? pcolbase[s] : 0;  // the row's first column (policy_base_body)
-    if (UNIFORM && ok && j0 + kChunk <= (kmax & ~(kChunk - 1))) {  // whole chunk on both sides
-      double v[kChunk];
-      int c[kChunk];
-      const int64_t si = sell_at(sbase, sw, sl, j0), di = sell_at(pbase, pw, pl, j0);
-      load_chunk(sval + si, v);
-      load_chunk(scol + si, c);
-      *reinterpret_cast<double2*>(pval + di) = make_double2(v[0], v[1]);
-      *reinterpret_cast<double2*>(pval + di + 2) = make_double2(v[2], v[3]);
-      *reinterpret_cast<int4*>(pcol + di) = make_int4(c[0], c[1], c[2], c[3]);
-      if (pval32) *reinterpret_cast<float4*>(pval32 + di) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-      if (pval16)
-#pragma unroll
-        for (int e = 0; e < kChunk; ++e) put_narrow(nullptr, pval16, store16, di + e, v[e]);
-      if (pcol16)
-        *reinterpret_cast<short4*>(pcol16 + di) = make_short4((short)(c[0] - cbase), (short)(c[1] - cbase),
-                                                              (short)(c[2] - cbase), (short)(c[3] - cbase));
-      continue;
-    }
-    for (int j = j0; j < j0 + kChunk && j < pw; ++j) {
-      const int64_t di = sell_at(pbase, pw, pl, j);
-      if (j < n) {
-        const int64_t si = sell_at(sbase, sw, sl, j);
-        const double v = sval[si];
-        pval[di] = v;
-        const int c = scol[si];
-        pcol[di] = c;
-        put_narrow(pval32, pval16, store16, di, v);
-        if (pcol16) pcol16[di] = (int16_t)(c - cbase);
-      } else if (UNIFORM) {
-        pval[di] = 0.0;
-        pcol[di] = 0;
-        put_narrow(pval32, pval16, store16, di, 0.0);
-        if (pcol16) pcol16[di] = 0;
+  // chunk u outermost, states grid-strided inside: the work of the flat (u, s) loop
+  // without a 64-bit division per unit
+  const int64_t start = bid * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)nb * blockDim.x;
+  for (int u = 0; u < nunits; ++u) {
+    for (int64_t s = start; s < S; s += stride) {
+      const int a = pi[s];
+      const bool ok = (a >= 0 && a < A);
+      const int64_t r = s * A + (ok ? a : 0);
+      const int n = !ok ? 0 : (UNIFORM ? kmax : len[r]);
+      if (u == 0) {
+        if (!UNIFORM) plen[s] = n;
+        gpi[s] = ok ? g[r] : __longlong_as_double(0x7ff8000000000000ULL);
+      }
+      const int64_t ps = s / kSlice, q = r / kSlice;
+      const int pw = UNIFORM ? kmax : (int)((poff[ps + 1] - poff[ps]) / kSlice);  // destination slice width
+      const int sw = UNIFORM ? kmax : (int)((off[q + 1] - off[q]) / kSlice);      // source slice width
+      const int64_t pbase = UNIFORM ? ps * kSlice * (int64_t)kmax : poff[ps];
+      const int64_t sbase = UNIFORM ? q * kSlice * (int64_t)kmax : off[q];
+      const int pl = (int)(s % kSlice), sl = (int)(r % kSlice);
+      const int j0 = u * kChunk;
+      const int cbase = pcol16 ? pcolbase[s] : 0;  // the row's first column (policy_base_body)
+      if (UNIFORM && ok && j0 + kChunk <= (kmax & ~(kChunk - 1))) {  // whole chunk on both sides
+        double v[kChunk];
+        int c[kChunk];
+        const int64_t si = sell_at(sbase, sw, sl, j0), di = sell_at(pbase, pw, pl, j0);
+        load_chunk(sval + si, v);
+        load_chunk(scol + si, c);
+        *reinterpret_cast<double2*>(pval + di) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(pval + di + 2) = make_double2(v[2], v[3]);
+        *reinterpret_cast<int4*>(pcol + di) = make_int4(c[0], c[1], c[2], c[3]);
+        if (pval32) *reinterpret_cast<float4*>(pval32 + di) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        if (pval16)
+  #pragma unroll
+          for (int e = 0; e < kChunk; ++e) put_narrow(nullptr, pval16, store16, di + e, v[e]);
+        if (pcol16)
+          *reinterpret_cast<short4*>(pcol16 + di) = make_short4((short)(c[0] - cbase), (short)(c[1] - cbase),
+                                                                (short)(c[2] - cbase), (short)(c[3] - cbase));
+        continue;
+      }
+      for (int j = j0; j < j0 + kChunk && j < pw; ++j) {
+        const int64_t di = sell_at(pbase, pw, pl, j);
+        if (j < n) {
+          const int64_t si = sell_at(sbase, sw, sl, j);
+          const double v = sval[si];
+          pval[di] = v;
+          const int c = scol[si];
+          pcol[di] = c;
+          put_narrow(pval32, pval16, store16, di, v);
+          if (pcol16) pcol16[di] = (int16_t)(c - cbase);
+        } else if (UNIFORM) {
+          pval[di] = 0.0;
+          pcol[di] = 0;
+          put_narrow(pval32, pval16, store16, di, 0.0);
+          if (pcol16) pcol16[di] = 0;
+        }
       }
     }
   }

@@ -180,7 +180,7 @@ struct mdp_s {
   // record_timing: events around the Arnoldi mat-vec of every GMRES step (created on first use)
   int timing = 0;
   cudaEvent_t mv_ev[2 * mdp::kMaxBasis] = {};
-  double mv_ms = 0.0, mv_bytes = 0.0;
+  double mv_ms = 0.0, mv_bytes = 0.0, mv_flops = 0.0;
   int64_t mv_timed = 0;
   // and after the projection of the same steps (FP64 single-pass steps, whose mat-vec also forms the dots)
   cudaEvent_t gs_ev[mdp::kMaxBasis] = {};

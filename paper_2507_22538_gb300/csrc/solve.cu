@@ -262,7 +262,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   const int64_t launches0 = h->launches;
   const int64_t matvecs0 = h->matvecs, vreads0 = h->vreads, vwrites0 = h->vwrites;
   const double ibytes0 = h->inner_bytes;
-  const double mv_ms0 = h->mv_ms, mv_bytes0 = h->mv_bytes;
+  const double mv_ms0 = h->mv_ms, mv_bytes0 = h->mv_bytes, mv_flops0 = h->mv_flops;
   const int64_t mv_timed0 = h->mv_timed;
   const double gs_ms0 = h->gs_ms, gs_flops0 = h->gs_flops;
   const int64_t gs_timed0 = h->gs_timed;
@@ -358,6 +358,7 @@ mdp_status mdp_solve(mdp_handle h, const mdp_solve_opts* o, double* V, int32_t* 
   local.inner_bytes = h->inner_bytes - ibytes0;
   local.matvec_ms = h->mv_ms - mv_ms0;
   local.matvec_bytes = h->mv_bytes - mv_bytes0;
+  local.matvec_flops = h->mv_flops - mv_flops0;
   local.matvecs_timed = h->mv_timed - mv_timed0;
   local.gs_ms = h->gs_ms - gs_ms0;
   local.gs_flops = h->gs_flops - gs_flops0;

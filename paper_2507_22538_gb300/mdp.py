@@ -56,7 +56,8 @@ class mdp_solve_stats(ctypes.Structure):
                 ("policy_value_bytes", ctypes.c_int32), ("matvec_ms", ctypes.c_double),
                 ("matvecs_timed", ctypes.c_int64), ("gs_ms", ctypes.c_double), ("gs_flops", ctypes.c_double),
                 ("gs_timed", ctypes.c_int64), ("bellman_value_bytes", ctypes.c_int32),
-                ("bellman_rows_fp64", ctypes.c_int64), ("matvec_bytes", ctypes.c_double)]
+                ("bellman_rows_fp64", ctypes.c_int64), ("matvec_bytes", ctypes.c_double),
+                ("matvec_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
