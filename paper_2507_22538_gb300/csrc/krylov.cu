@@ -50,17 +50,18 @@ __global__ void __launch_bounds__(kVecThreads) policy_apply_kernel(const double*
 }
 
 // GMRES passes (bodies in krylov_dev.cuh), one problem per launch.
-template <bool U, typename T>
-__global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const double* __restrict__ pval,
-                                                                   const int32_t* __restrict__ pcol,
+template <bool U, typename T, typename TP = double, typename TC = int32_t>
+__global__ void __launch_bounds__(kVecThreads) gm_residual_kernel(const TP* __restrict__ pval,
+                                                                   const TC* __restrict__ pcol,
                                                                    const int64_t* __restrict__ poff,
                                                                    const int32_t* __restrict__ plen, int k, int64_t S,
                                                                    double gamma, const double* __restrict__ theta,
                                                                    const double* __restrict__ b,
                                                                    T* __restrict__ u0, double* partials,
-                                                                   KrylovState* K) {
+                                                                   KrylovState* K, const int32_t* __restrict__ cbase) {
   pdl_begin();
-  gm_residual_body<U, T>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, theta, b, u0, partials, K);
+  gm_residual_body<U, T, TP, TC>((int)blockIdx.x, (int)gridDim.x, pval, pcol, poff, plen, k, S, gamma, theta, b, u0,
+                                 partials, K, cbase);
 }
 
 template <bool U, typename TP, typename T, typename TC = int32_t>
@@ -677,9 +678,29 @@ template <bool U, typename T>
 static mdp_status gm_residual(mdp_s* h, const KrylovBuffers<T>& B, double gamma, const double* theta,
                               cudaStream_t st) {
   const Sell& Q = h->Ppi;
-  MDP_CUDA(launch_pdl(gm_residual_kernel<U, T>, MDP_WAVE((gm_residual_kernel<U, T>)), kVecThreads, 0, st, Q.val, Q.col, Q.off, Q.len, U ? Q.kmax : 0, h->S,
-                                                                   gamma, theta, h->gpi, B.basis, h->partials,
-                                                                   kstate(h)));
+  // the grid of the binary64-row kernel in every variant: the batched solver sums the
+  // same block partials in the same order
+  const int grid = MDP_WAVE((gm_residual_kernel<U, T>));
+  bool done = false;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (h->pcol16) {  // the mixed solver's exact 16-bit rows (the gather wrote no binary64 copy)
+      done = true;
+      if (h->pstore == kStoreF16)
+        MDP_CUDA(launch_pdl(gm_residual_kernel<U, T, __half, int16_t>, grid, kVecThreads, 0, st,
+                            (const __half*)h->pval16, (const int16_t*)h->pcol16, Q.off, Q.len, U ? Q.kmax : 0, h->S,
+                            gamma, theta, h->gpi, B.basis, h->partials, kstate(h), (const int32_t*)h->pcolbase));
+      else
+        MDP_CUDA(launch_pdl(gm_residual_kernel<U, T, __nv_bfloat16, int16_t>, grid, kVecThreads, 0, st,
+                            (const __nv_bfloat16*)h->pval16, (const int16_t*)h->pcol16, Q.off, Q.len,
+                            U ? Q.kmax : 0, h->S, gamma, theta, h->gpi, B.basis, h->partials, kstate(h),
+                            (const int32_t*)h->pcolbase));
+    }
+  }
+  if (!done) {
+    MDP_CUDA(launch_pdl(gm_residual_kernel<U, T>, grid, kVecThreads, 0, st, Q.val, Q.col, Q.off, Q.len,
+                        U ? Q.kmax : 0, h->S, gamma, theta, h->gpi, B.basis, h->partials, kstate(h),
+                        (const int32_t*)nullptr));
+  }
   MDP_LAUNCH_CHECK(h);
   return MDP_OK;
 }
@@ -694,6 +715,13 @@ static void add_matvec_bytes(mdp_s* h, int n, size_t value_bytes, size_t vec_byt
 
 static void add_vector_bytes(mdp_s* h, int64_t nvec, size_t vec_bytes) {
   h->inner_bytes += (double)nvec * (double)h->S * (double)vec_bytes;
+}
+
+// n restart residuals (binary64 sums over the policy's rows, x = theta): the binary64
+// rows, or the mixed solver's exact 16-bit rows with 16-bit column offsets.
+static void add_residual_bytes(mdp_s* h, int64_t n, bool mixed) {
+  const bool r16 = mixed && h->pcol16;
+  add_matvec_bytes(h, (int)n, r16 ? 2 : sizeof(double), sizeof(double), r16 ? 2 : 4);
 }
 
 // Work of `steps` Arnoldi steps without re-orthogonalisation (one pass would do):
@@ -717,7 +745,7 @@ static void count_cycle(mdp_s* h, int steps) {
   h->matvecs += 1;
   h->vreads += 1;
   h->vwrites += 1;
-  add_matvec_bytes(h, 1, sizeof(double), sizeof(double));
+  add_residual_bytes(h, 1, sizeof(T) == sizeof(float));
   add_vector_bytes(h, 1, sizeof(double));
   add_vector_bytes(h, 1, sizeof(T));
 }
@@ -780,7 +808,7 @@ static mdp_status gmres(mdp_s* h, double gamma, double* theta, int m, int refine
   h->matvecs += 1;
   h->vreads += 1;
   h->vwrites += 1;
-  add_matvec_bytes(h, 1, sizeof(double), sizeof(double));
+  add_residual_bytes(h, 1, sizeof(T) == sizeof(float));
   add_vector_bytes(h, 1, sizeof(double));
   add_vector_bytes(h, 1, sizeof(T));
   KrylovHeader hd{};
@@ -1049,7 +1077,7 @@ void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int6
   h->matvecs += solves;
   h->vreads += solves;
   h->vwrites += solves;
-  add_matvec_bytes(h, (int)solves, sizeof(double), sizeof(double));
+  add_residual_bytes(h, solves, mixed);
   add_vector_bytes(h, solves, sizeof(double));
   add_vector_bytes(h, solves, sT);
   // count_cycle summed in closed form: sum_j (2 j + 2) = n^2 + n over a cycle of n steps
@@ -1060,7 +1088,7 @@ void gmres_count_work(mdp_s* h, bool mixed, int64_t solves, int64_t cycles, int6
   add_matvec_bytes(h, (int)steps, vbytes, sT, (mixed && h->pcol16) ? 2 : 4);
   add_vector_bytes(h, 2 * tri + 5 * steps, sT);
   add_vector_bytes(h, 3 * cycles, sizeof(double));
-  add_matvec_bytes(h, (int)cycles, sizeof(double), sizeof(double));
+  add_residual_bytes(h, cycles, mixed);
   add_vector_bytes(h, cycles, sT);
 }
 

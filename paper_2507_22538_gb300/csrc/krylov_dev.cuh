@@ -251,20 +251,24 @@ __device__ inline void finish_step(KrylovState* K, int j) {
 // ---- GMRES pass bodies -------------------------------------------------------------
 
 // GMRES (re)start: u_0 = r = b - J theta and beta_0 = ||r||_2; prepares the next
-// cycle, or ends the solve when beta_0 < tol or the iteration cap is reached.
-template <bool U, typename T>
-__device__ __forceinline__ void gm_residual_body(int bid, int nb, const double* __restrict__ pval,
-                                                                   const int32_t* __restrict__ pcol,
+// cycle, or ends the solve when beta_0 < tol or the iteration cap is reached.  The
+// policy's values come as binary64, or (TP 16-bit, with 16-bit column offsets from
+// cbase) as the exact 16-bit copy of the mixed solver, widened exactly: the same
+// binary64 sums either way.
+template <bool U, typename T, typename TP = double, typename TC = int32_t>
+__device__ __forceinline__ void gm_residual_body(int bid, int nb, const TP* __restrict__ pval,
+                                                                   const TC* __restrict__ pcol,
                                                                    const int64_t* __restrict__ poff,
                                                                    const int32_t* __restrict__ plen, int k, int64_t S,
                                                                    double gamma, const double* __restrict__ theta,
                                                                    const double* __restrict__ b,
                                                                    T* __restrict__ u0, double* partials,
-                                                                   KrylovState* K) {
+                                                                   KrylovState* K,
+                                                                   const int32_t* __restrict__ cbase = nullptr) {
   if (K->flags & kSolveDone) return;
   double d[1] = {0.0};
   for (int64_t s = bid * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)nb * blockDim.x) {
-    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, theta);
+    const double px = policy_row_dot<U>(pval, pcol, poff, plen, k, s, theta, cbase);
     const double r = b[s] - (theta[s] - gamma * px);
     d[0] = fma(r, r, d[0]);
     u0[s] = (T)r;

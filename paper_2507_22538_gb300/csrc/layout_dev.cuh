@@ -12,13 +12,33 @@ namespace mdp {
 // per (state, 4-entry chunk) with the state fastest: each warp writes whole
 // contiguous chunks and each thread reads one 32-byte run of its row.  States
 // whose pi(s) lies outside [0, A) get an empty row (zero values, column 0) and
-// g_pi = NaN.  With pcol16 set (every column within 32767 of its row's first
-// column), the mixed solver's column copy is written too: the row's first column as
-// pcolbase[s] and column - pcolbase[s] as int16 per entry (base 0 and offsets 0 for
-// an empty row).
+// g_pi = NaN.  With pcol16 set (the mixed solver of an MDP with 16-bit values whose
+// every row stays within 32767 columns of its first column), the rows go out as the
+// 16-bit values and column - pcolbase[s] as int16 per entry (offsets 0 for an empty
+// row; pcolbase written beforehand by policy_base_body), and no binary64 copy is
+// written: every pass of that solver reads the 16-bit rows.
+// The 16-bit pattern of a value that is exact in binary16 (store16 = kStoreF16) or
+// bfloat16 (checked at creation), from its binary64 fields with integer operations for
+// zeros and normal numbers (GB300's FP64 pipe is kept for arithmetic); other values
+// take the library conversion.
+__device__ __forceinline__ uint16_t narrow_exact(double v, int store16) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 63) << 15;
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if ((b << 1) == 0ull) return (uint16_t)sign;  // +-0
+  if (store16 == kStoreF16) {
+    if (e - 1009u < 30u && (b & ((1ull << 42) - 1)) == 0ull)  // normal binary16, no bits lost
+      return (uint16_t)(sign | ((e - 1008u) << 10) | (unsigned)((b >> 42) & 0x3ffu));
+    return __half_as_ushort(__double2half(v));
+  }
+  if (e - 897u < 254u && (b & ((1ull << 45) - 1)) == 0ull)  // normal bfloat16, no bits lost
+    return (uint16_t)(sign | ((e - 896u) << 7) | (unsigned)((b >> 45) & 0x7fu));
+  return __bfloat16_as_ushort(__double2bfloat16(v));
+}
+
 __device__ __forceinline__ void put_narrow(float* p32, uint16_t* p16, int store16, int64_t i, double v) {
   if (p32) p32[i] = (float)v;
-  if (p16) p16[i] = (store16 == kStoreF16) ? __half_as_ushort(__double2half(v)) : __bfloat16_as_ushort(__double2bfloat16(v));
+  if (p16) p16[i] = narrow_exact(v, store16);
 }
 
 // The base column of each policy row for the 16-bit offsets: the first column of
@@ -78,9 +98,11 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
         const int64_t si = sell_at(sbase, sw, sl, j0), di = sell_at(pbase, pw, pl, j0);
         load_chunk(sval + si, v);
         load_chunk(scol + si, c);
-        *reinterpret_cast<double2*>(pval + di) = make_double2(v[0], v[1]);
-        *reinterpret_cast<double2*>(pval + di + 2) = make_double2(v[2], v[3]);
-        *reinterpret_cast<int4*>(pcol + di) = make_int4(c[0], c[1], c[2], c[3]);
+        if (!pcol16) {
+          *reinterpret_cast<double2*>(pval + di) = make_double2(v[0], v[1]);
+          *reinterpret_cast<double2*>(pval + di + 2) = make_double2(v[2], v[3]);
+          *reinterpret_cast<int4*>(pcol + di) = make_int4(c[0], c[1], c[2], c[3]);
+        }
         if (pval32) *reinterpret_cast<float4*>(pval32 + di) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
         if (pval16)
   #pragma unroll
@@ -95,16 +117,22 @@ __device__ __forceinline__ void extract_policy_body(int bid, int nb, const doubl
         if (j < n) {
           const int64_t si = sell_at(sbase, sw, sl, j);
           const double v = sval[si];
-          pval[di] = v;
           const int c = scol[si];
-          pcol[di] = c;
+          if (pcol16) {
+            pcol16[di] = (int16_t)(c - cbase);
+          } else {
+            pval[di] = v;
+            pcol[di] = c;
+          }
           put_narrow(pval32, pval16, store16, di, v);
-          if (pcol16) pcol16[di] = (int16_t)(c - cbase);
         } else if (UNIFORM) {
-          pval[di] = 0.0;
-          pcol[di] = 0;
+          if (pcol16) {
+            pcol16[di] = 0;
+          } else {
+            pval[di] = 0.0;
+            pcol[di] = 0;
+          }
           put_narrow(pval32, pval16, store16, di, 0.0);
-          if (pcol16) pcol16[di] = 0;
         }
       }
     }

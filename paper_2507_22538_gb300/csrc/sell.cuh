@@ -49,6 +49,36 @@ __device__ __forceinline__ void load_chunk(const int16_t* p, int (&v)[kChunk]) {
   v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
 }
 
+// A stored value in the accumulation type TX.  A binary16 or bfloat16 value becomes
+// binary64 by rebuilding its IEEE fields with integer operations and selects, no
+// branch (normal numbers, zeros, subnormals -- normalised by their leading bit --,
+// infinities and NaNs): the same value, without spending GB300's scarce FP64 pipe on
+// a format conversion per entry.  `mb` mantissa bits, exponent field width `eb`.
+template <int mb, int eb>
+__device__ __forceinline__ double widen_bits(unsigned b) {
+  constexpr unsigned kEmax = (1u << eb) - 1u;
+  constexpr int kBias = (1 << (eb - 1)) - 1;
+  const unsigned e = (b >> mb) & kEmax, m = b & ((1u << mb) - 1u);
+  const int p = 31 - __clz(m);  // leading bit of a subnormal's mantissa (m > 0)
+  // binary64 exponent field: normal e - bias + 1023; subnormal p - (bias - 1 + mb) + 1023
+  const unsigned E = e == kEmax ? 2047u : (e != 0u ? e + (1023u - kBias) : (m != 0u ? (unsigned)(p + 1024 - kBias - mb) : 0u));
+  const unsigned long long M = e != 0u ? (unsigned long long)m << (52 - mb)
+                                       : ((unsigned long long)m << (52 - p)) & ((1ull << 52) - 1ull);  // m = 0: 0
+  return __longlong_as_double((long long)(((unsigned long long)(b >> (mb + eb)) << 63) | ((unsigned long long)E << 52) | M));
+}
+template <typename TX, typename TP>
+__device__ __forceinline__ TX widen(TP v) {
+  return static_cast<TX>(v);
+}
+template <>
+__device__ __forceinline__ double widen<double, __half>(__half v) {
+  return widen_bits<10, 5>(__half_as_ushort(v));
+}
+template <>
+__device__ __forceinline__ double widen<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return widen_bits<7, 8>(__bfloat16_as_ushort(v));
+}
+
 // One chunk of binary64 values with a single 32-byte load (256-bit vector load of the
 // read-only path); the chunk starts on a 32-byte boundary (a multiple of 4 elements
 // from a 256-byte aligned slice).
@@ -87,9 +117,9 @@ __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const TC*
     load_chunk(cp + c * kStride, c0);
     load_chunk(cp + (c + 1) * kStride, c1);
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u) acc = fma(static_cast<TX>(v0[u]), __ldg(x + c0[u]), acc);
+    for (int u = 0; u < kChunk; ++u) acc = fma(widen<TX>(v0[u]), __ldg(x + c0[u]), acc);
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u) acc = fma(static_cast<TX>(v1[u]), __ldg(x + c1[u]), acc);
+    for (int u = 0; u < kChunk; ++u) acc = fma(widen<TX>(v1[u]), __ldg(x + c1[u]), acc);
   }
   if (c < nc) {
     TP v0[kChunk];
@@ -97,11 +127,11 @@ __device__ __forceinline__ TX sell_row_dot(const TP* __restrict__ val, const TC*
     load_vals<V256>(vp + c * kStride, v0);
     load_chunk(cp + c * kStride, c0);
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u) acc = fma(static_cast<TX>(v0[u]), __ldg(x + c0[u]), acc);
+    for (int u = 0; u < kChunk; ++u) acc = fma(widen<TX>(v0[u]), __ldg(x + c0[u]), acc);
   }
   for (int j = nc * kChunk; j < n; ++j) {
     const int64_t i = sell_at(base, w, lane, j);
-    acc = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc);
+    acc = fma(widen<TX>(val[i]), __ldg(x + col[i]), acc);
   }
   return acc;
 }
@@ -138,20 +168,20 @@ __device__ __forceinline__ void sell_row_dot2(const TP* __restrict__ val, const 
     }
     if (has0) {
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u) acc0 = fma(static_cast<TX>(v0[u]), __ldg(x + c0[u]), acc0);
+      for (int u = 0; u < kChunk; ++u) acc0 = fma(widen<TX>(v0[u]), __ldg(x + c0[u]), acc0);
     }
     if (has1) {
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u) acc1 = fma(static_cast<TX>(v1[u]), __ldg(x + c1[u]), acc1);
+      for (int u = 0; u < kChunk; ++u) acc1 = fma(widen<TX>(v1[u]), __ldg(x + c1[u]), acc1);
     }
   }
   for (int j = nc0 * kChunk; j < n0; ++j) {
     const int64_t i = sell_at(base0, w0, lane, j);
-    acc0 = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc0);
+    acc0 = fma(widen<TX>(val[i]), __ldg(x + col[i]), acc0);
   }
   for (int j = nc1 * kChunk; j < n1; ++j) {
     const int64_t i = sell_at(base1, w1, lane, j);
-    acc1 = fma(static_cast<TX>(val[i]), __ldg(x + col[i]), acc1);
+    acc1 = fma(widen<TX>(val[i]), __ldg(x + col[i]), acc1);
   }
 }
 
