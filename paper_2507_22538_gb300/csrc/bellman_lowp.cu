@@ -46,12 +46,12 @@ __device__ __forceinline__ float lp_to_float(__nv_bfloat16 v) { return __bfloat1
 
 // binary32 screen of one row: acc = sum_j p_j x[col_j] and mag = sum_j p_j |x[col_j]|
 // in ascending j (the row walk of sell_row_dot).
-template <typename TP>
-__device__ __forceinline__ void lowp_row_dot(const TP* __restrict__ val, const int32_t* __restrict__ col,
+template <typename TP, typename TC>
+__device__ __forceinline__ void lowp_row_dot(const TP* __restrict__ val, const TC* __restrict__ col,
                                              int64_t base, int w, int lane, int n, const float* __restrict__ x,
                                              float& acc, float& mag) {
   const TP* vp = val + base + lane * kChunk;
-  const int32_t* cp = col + base + lane * kChunk;
+  const TC* cp = col + base + lane * kChunk;
   constexpr int64_t kStride = kSlice * kChunk;
   const int nc = n / kChunk;
   float a = 0.f, m = 0.f;
@@ -105,9 +105,12 @@ __device__ __forceinline__ void lowp_row_dot(const TP* __restrict__ val, const i
   mag = m;
 }
 
-template <bool UNIFORM, typename TP>
+// TC: int32_t columns, or int16_t offsets from each row's first column (cbase[r]; the
+// MDP's every row within 32767 columns of its first): 4 instead of 6 bytes per entry.
+template <bool UNIFORM, typename TP, typename TC>
 __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_kernel(
-    const TP* __restrict__ sval, const int32_t* __restrict__ scol, const int64_t* __restrict__ off,
+    const TP* __restrict__ sval, const TC* __restrict__ scol, const int32_t* __restrict__ cbase,
+    const int64_t* __restrict__ off,
     const int32_t* __restrict__ len, int k, const float* __restrict__ g32, const double* __restrict__ g,
     const float* __restrict__ Vf, const double* __restrict__ V, int64_t S, int A, int TS, double gamma, float gammaf,
     double* __restrict__ TV, int32_t* __restrict__ pi, unsigned long long* __restrict__ resmax,
@@ -137,7 +140,9 @@ __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_ker
         const int w = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
         const int64_t base = UNIFORM ? q * kSlice * (int64_t)k : off[q];
         float acc, mag;
-        lowp_row_dot(sval, scol, base, w, lane, n, Vf, acc, mag);
+        const float* xr = Vf;
+        if constexpr (sizeof(TC) == sizeof(int16_t)) xr = Vf + cbase[r];
+        lowp_row_dot(sval, scol, base, w, lane, n, xr, acc, mag);
         const float gq = g32[r];
         const float qt = fmaf(gammaf, acc, gq);
         const float e = gammaf * ((float)(n + 4) * 0x1p-23f) * mag + 0x1p-22f * (fabsf(qt) + fabsf(gq)) + 0x1p-120f;
@@ -175,7 +180,9 @@ __global__ void __launch_bounds__(kBellThreads, kBellMinBlocks) bellman_lowp_ker
       const int n = UNIFORM ? k : len[r];
       const int w = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
       const int64_t base = UNIFORM ? q * kSlice * (int64_t)k : off[q];
-      const double acc = sell_row_dot(sval, scol, base, w, ln, n, V);
+      const double* xr = V;
+      if constexpr (sizeof(TC) == sizeof(int16_t)) xr = V + cbase[r];
+      const double acc = sell_row_dot<TP, double, false, TC>(sval, scol, base, w, ln, n, xr);
       qd[lr] = fma(gamma, acc, g[r]);
     }
     if (threadIdx.x == 0) cand_total += (unsigned long long)nc;
@@ -230,6 +237,27 @@ __global__ void __launch_bounds__(256) lowp_pack_kernel(const double* __restrict
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += stride) g32[r] = __double2float_rn(g[r]);
 }
 
+// The 16-bit column offsets of the stacked matrix (with col16): each row's first
+// column as its base, every entry's column minus that base (one thread per row).
+template <bool UNIFORM>
+__global__ void __launch_bounds__(256) lowp_col16_kernel(const int32_t* __restrict__ col, const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ len, int k, int64_t R,
+                                                         int16_t* __restrict__ col16, int32_t* __restrict__ base) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = r / kSlice;
+    const int lane = (int)(r % kSlice);
+    const int n = UNIFORM ? k : len[r];
+    const int w = UNIFORM ? k : (int)((off[q + 1] - off[q]) / kSlice);
+    const int64_t sb = UNIFORM ? q * kSlice * (int64_t)k : off[q];
+    const int c0 = n > 0 ? col[sell_at(sb, w, lane, 0)] : 0;
+    base[r] = c0;
+    for (int j = 0; j < n; ++j) {
+      const int64_t i = sell_at(sb, w, lane, j);
+      col16[i] = (int16_t)(col[i] - c0);
+    }
+  }
+}
+
 static size_t lowp_smem_for(int ts, int A) { return (size_t)ts * A * kLowpSmemPerRow + 16; }
 static size_t lowp_smem(const mdp_s* h) { return lowp_smem_for(h->lp_ts, h->A); }
 
@@ -269,6 +297,19 @@ static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
     h->launches++;
     MDP_CUDA(cudaGetLastError());
     MDP_CUDA(cudaMemsetAsync(h->lp_rows, 0, sizeof(unsigned long long), st));
+    if (h->col16) {
+      MDP_TRY(alloc((void**)&h->P16col, (size_t)std::max<int64_t>(1, h->P.nstored) * sizeof(int16_t),
+                    "16-bit column offsets"));
+      MDP_TRY(alloc((void**)&h->P16base, (size_t)h->R * sizeof(int32_t), "row base columns"));
+      const int rg = vec_grid(h, h->R);
+      if (h->P.uniform)
+        lowp_col16_kernel<true><<<rg, 256, 0, st>>>(h->P.col, h->P.off, h->P.len, h->P.kmax, h->R, h->P16col,
+                                                    h->P16base);
+      else
+        lowp_col16_kernel<false><<<rg, 256, 0, st>>>(h->P.col, h->P.off, h->P.len, 0, h->R, h->P16col, h->P16base);
+      h->launches++;
+      MDP_CUDA(cudaGetLastError());
+    }
   }
   // the tile mdp_tune chose for this sweep, else the binary64 sweep's, halved until
   // its 10 B per row fit in shared memory
@@ -278,11 +319,16 @@ static mdp_status ensure_lowp(mdp_s* h, cudaStream_t st) {
     h->lp_ts = ts;
     const size_t smem = lowp_smem(h);
     if (smem > 227 * 1024) return fail(MDP_ERR_INVALID_ARG, "low-precision sweep tile does not fit on an SM");
-    const void* kern[4] = {(const void*)bellman_lowp_kernel<true, __half>, (const void*)bellman_lowp_kernel<false, __half>,
-                           (const void*)bellman_lowp_kernel<true, __nv_bfloat16>,
-                           (const void*)bellman_lowp_kernel<false, __nv_bfloat16>};
+    const void* kern[8] = {(const void*)bellman_lowp_kernel<true, __half, int32_t>,
+                           (const void*)bellman_lowp_kernel<false, __half, int32_t>,
+                           (const void*)bellman_lowp_kernel<true, __nv_bfloat16, int32_t>,
+                           (const void*)bellman_lowp_kernel<false, __nv_bfloat16, int32_t>,
+                           (const void*)bellman_lowp_kernel<true, __half, int16_t>,
+                           (const void*)bellman_lowp_kernel<false, __half, int16_t>,
+                           (const void*)bellman_lowp_kernel<true, __nv_bfloat16, int16_t>,
+                           (const void*)bellman_lowp_kernel<false, __nv_bfloat16, int16_t>};
     for (const void* f : kern) MDP_TRY(raise_dyn_smem(f, smem));
-    const int which = (h->pstore == kStoreBF16 ? 2 : 0) + (h->P.uniform ? 0 : 1);
+    const int which = (h->P16col ? 4 : 0) + (h->pstore == kStoreBF16 ? 2 : 0) + (h->P.uniform ? 0 : 1);
     int per_sm = 0;
     MDP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[which], kBellThreads, smem));
     if (per_sm < 1) return fail(MDP_ERR_INVALID_ARG, "low-precision sweep tile does not fit on an SM");
@@ -304,15 +350,23 @@ mdp_status launch_bellman_lowp(mdp_s* h, double gamma, const double* V, double* 
   const Sell& P = h->P;
   const float gf = static_cast<float>(gamma);  // round to nearest, as on the device
   const int k = P.uniform ? P.kmax : 0;
-#define MDP_LOWP_LAUNCH(U, TP)                                                                              \
-  bellman_lowp_kernel<U, TP><<<h->lp_blocks, kBellThreads, smem, st>>>(                                      \
-      reinterpret_cast<const TP*>(h->P16), P.col, P.off, P.len, k, h->g32, h->g, h->vf32, V, h->S, h->A,     \
+#define MDP_LOWP_LAUNCH(U, TP, TC, COL, BASE)                                                               \
+  bellman_lowp_kernel<U, TP, TC><<<h->lp_blocks, kBellThreads, smem, st>>>(                                  \
+      reinterpret_cast<const TP*>(h->P16), COL, BASE, P.off, P.len, k, h->g32, h->g, h->vf32, V, h->S, h->A, \
       h->lp_ts, gamma, gf, TV, pi, h->resmax, h->lp_rows)
+#define MDP_LOWP_COLS(U, TP)                                                                                \
+  do {                                                                                                      \
+    if (h->P16col)                                                                                          \
+      MDP_LOWP_LAUNCH(U, TP, int16_t, (const int16_t*)h->P16col, (const int32_t*)h->P16base);               \
+    else                                                                                                    \
+      MDP_LOWP_LAUNCH(U, TP, int32_t, (const int32_t*)P.col, (const int32_t*)nullptr);                      \
+  } while (0)
   if (h->pstore == kStoreBF16) {
-    if (P.uniform) MDP_LOWP_LAUNCH(true, __nv_bfloat16); else MDP_LOWP_LAUNCH(false, __nv_bfloat16);
+    if (P.uniform) MDP_LOWP_COLS(true, __nv_bfloat16); else MDP_LOWP_COLS(false, __nv_bfloat16);
   } else {
-    if (P.uniform) MDP_LOWP_LAUNCH(true, __half); else MDP_LOWP_LAUNCH(false, __half);
+    if (P.uniform) MDP_LOWP_COLS(true, __half); else MDP_LOWP_COLS(false, __half);
   }
+#undef MDP_LOWP_COLS
 #undef MDP_LOWP_LAUNCH
   h->launches++;
   MDP_CUDA(cudaGetLastError());

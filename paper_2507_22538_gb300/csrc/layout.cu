@@ -322,6 +322,8 @@ static void destroy_handle(mdp_s* h) {
   dfree(st, h->sc);
   dfree(st, h->resmax);
   dfree(st, h->P16);
+  dfree(st, h->P16col);
+  dfree(st, h->P16base);
   dfree(st, h->g32);
   dfree(st, h->vf32);
   dfree(st, h->lp_rows);

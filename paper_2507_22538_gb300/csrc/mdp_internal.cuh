@@ -167,6 +167,8 @@ struct mdp_s {
   // certified low-precision sweep (bellman_lowp.cu), set up on first use when the
   // probabilities are exact in binary16 / bfloat16
   uint16_t* P16 = nullptr;               // [P.nstored] 16-bit copy of P.val (same sliced layout)
+  int16_t* P16col = nullptr;             // [P.nstored] with col16: column - P16base[row] as int16
+  int32_t* P16base = nullptr;            // [R] with col16: each row's first column
   float* g32 = nullptr;                  // [R] binary32 costs
   float* vf32 = nullptr;                 // [S] binary32 copy of the sweep's V
   unsigned long long* lp_rows = nullptr; // rows re-evaluated in binary64 (running count)
