@@ -152,7 +152,11 @@ void mdp_default_opts(mdp_solve_opts* opts);
  *                values (MDP_ERR_INVALID_ARG for any other val_type).
  *  g             double[S*A] stage costs, finite.
  *  inputs_on_device  nonzero: the four arrays are device pointers; zero: host pointers
- *                (pinned host memory gives the fastest upload).
+ *                (pinned host memory gives the fastest upload).  Host entries go up
+ *                in row-aligned chunks of at most 2^25 entries on an internal copy
+ *                stream, each converted to the device layout while later chunks are
+ *                in flight; besides the handle, creation holds at most four chunks
+ *                and the row pointers on the device.
  *  stream        stream for the upload and the layout kernels; the call returns
  *                after they complete.
  *  out           receives the handle (NULL on failure).

@@ -60,45 +60,25 @@ __device__ __forceinline__ double widen(float v) { return (double)v; }
 __device__ __forceinline__ double widen(__half v) { return (double)__half2float(v); }
 __device__ __forceinline__ double widen(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
-// One thread per row of Eq. 5: check the CSR invariants, record the row length and
-// whether every probability is exact in binary16 / bfloat16 (the narrowest exact
-// storage for the mixed solver's copies of the policy rows).  Values of type TV are
-// widened to binary64 first.
-template <typename TV>
-__global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                     const TV* __restrict__ val, const double* __restrict__ g, int64_t R,
-                                     int64_t S, int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
-                                     int* __restrict__ kmin, int* __restrict__ kmax, int* __restrict__ f16_ok,
-                                     int* __restrict__ bf16_ok, int A, int* __restrict__ near_ok) {
+// One thread per row of Eq. 5: check the row pointers and the stage cost, record
+// the row length and the shortest and longest row.  Entries are read only after
+// these checks have passed on every row (sell_rows_kernel).
+__global__ void row_struct_kernel(const int64_t* __restrict__ rp, const double* __restrict__ g, int64_t R,
+                                  int64_t nnz, int32_t* __restrict__ len, int* __restrict__ flags,
+                                  int* __restrict__ kmin, int* __restrict__ kmax) {
   int bad = 0;
   int lmin = 0x7fffffff, lmax = 0;
-  bool a16 = true, b16 = true, near = true;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = rp[r], hi = rp[r + 1];
+    const int64_t lo = rp[r], hi = rp[r + 1];
     int l = 0;
-    if (lo < 0 || hi < lo || hi > nnz) {
+    if (lo < 0 || hi < lo || hi > nnz)
       bad |= kBadPtr;
-    } else if (hi == lo) {
+    else if (hi == lo)
       bad |= kEmptyRow;
-    } else if (hi - lo > (1 << 30)) {
+    else if (hi - lo > (1 << 30))
       bad |= kLongRow;
-    } else {
+    else
       l = (int)(hi - lo);
-      double sum = 0.0;
-      const int c0 = col[lo];  // the row's first column: the base of its 16-bit offsets
-      for (int64_t j = lo; j < hi; ++j) {
-        int c = col[j];
-        double v = widen(val[j]);
-        if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
-        near &= ((int64_t)c - c0 >= -32768 && (int64_t)c - c0 <= 32767);
-        if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
-        const uint64_t bits = (uint64_t)__double_as_longlong(v);
-        a16 &= exact_in(bits, 10, -14, 15);
-        b16 &= exact_in(bits, 7, -126, 127);
-        sum += v;
-      }
-      if (!(fabs(sum - 1.0) <= 1e-12)) bad |= kRowSum;
-    }
     if (!isfinite(g[r])) bad |= kBadCost;
     len[r] = l;
     lmin = min(lmin, l);
@@ -107,9 +87,6 @@ __global__ void validate_rows_kernel(const int64_t* __restrict__ rp, const int32
   if (bad) atomicOr(flags, bad);
   atomicMin(kmin, lmin);
   atomicMax(kmax, lmax);
-  if (!__all_sync(0xffffffffu, a16) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
-  if (!__all_sync(0xffffffffu, b16) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
-  if (!__all_sync(0xffffffffu, near) && (threadIdx.x & 31) == 0) atomicAnd(near_ok, 0);
 }
 
 // Width of each slice of `rows` rows: the longest row among its 32.
@@ -134,29 +111,58 @@ __global__ void state_maxlen_kernel(const int32_t* __restrict__ len, int64_t S, 
   }
 }
 
-// CSR -> sliced ELL: one thread per row copies its entries (widened to binary64)
-// into their chunked slice positions.
+// CSR -> sliced ELL for rows [r0, r1) of Eq. 5, one thread per row: copy the row's
+// entries (values of type TV widened exactly to binary64) into their chunked slice
+// positions and zero-fill the slice width beyond the row, and check the entries on
+// the way: columns in [0, S), probabilities finite and >= 0 summing to 1 within
+// 1e-12, whether every probability is exact in binary16 / bfloat16 (the narrowest
+// exact storage for the mixed solver's copies of the policy rows) and whether every
+// column lies within 32767 of its row's first one (16-bit column offsets).
+// col and val hold the entries from index ebase on: the whole arrays (ebase 0) or
+// one uploaded chunk that covers the rows' entries.  Row pointers were checked by
+// row_struct_kernel.
 template <typename TV>
-__global__ void csr_to_sell_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                   const TV* __restrict__ val, int64_t R, const int64_t* __restrict__ off,
-                                   int uniform_k, double* __restrict__ sval, int32_t* __restrict__ scol) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-    int64_t q = r / kSlice;
-    int lane = (int)(r % kSlice);
-    int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
-    int64_t width = uniform_k ? uniform_k : (off[q + 1] - off[q]) / kSlice;
-    int64_t lo = rp[r], n = rp[r + 1] - lo;
-    for (int j = 0; j < (int)width; ++j) {
-      const int64_t d = sell_at(base, (int)width, lane, j);
+__global__ void sell_rows_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                 const TV* __restrict__ val, int64_t r0, int64_t r1, int64_t ebase, int64_t S,
+                                 const int64_t* __restrict__ off, int uniform_k, double* __restrict__ sval,
+                                 int32_t* __restrict__ scol, int* __restrict__ flags, int* __restrict__ f16_ok,
+                                 int* __restrict__ bf16_ok, int* __restrict__ near_ok) {
+  int bad = 0;
+  bool a16 = true, b16 = true, near = true;
+  for (int64_t r = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < r1; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = r / kSlice;
+    const int lane = (int)(r % kSlice);
+    const int64_t base = uniform_k ? q * kSlice * (int64_t)uniform_k : off[q];
+    const int width = uniform_k ? uniform_k : (int)((off[q + 1] - off[q]) / kSlice);
+    const int64_t lo = rp[r] - ebase;
+    const int n = (int)(rp[r + 1] - rp[r]);
+    const int c0 = col[lo];  // the row's first column: the base of its 16-bit offsets
+    double sum = 0.0;
+    for (int j = 0; j < width; ++j) {
+      const int64_t d = sell_at(base, width, lane, j);
       if (j < n) {
-        sval[d] = widen(val[lo + j]);
-        scol[d] = col[lo + j];
+        const int c = col[lo + j];
+        const double v = widen(val[lo + j]);
+        if (c < 0 || (int64_t)c >= S) bad |= kBadCol;
+        near &= ((int64_t)c - c0 >= -32768 && (int64_t)c - c0 <= 32767);
+        if (!(v >= 0.0) || isinf(v)) bad |= kBadVal;
+        const uint64_t bits = (uint64_t)__double_as_longlong(v);
+        a16 &= exact_in(bits, 10, -14, 15);
+        b16 &= exact_in(bits, 7, -126, 127);
+        sum += v;
+        sval[d] = v;
+        scol[d] = c;
       } else {
         sval[d] = 0.0;
         scol[d] = 0;
       }
     }
+    if (!(fabs(sum - 1.0) <= 1e-12)) bad |= kRowSum;
   }
+  if (bad) atomicOr(flags, bad);
+  if (!__all_sync(0xffffffffu, a16) && (threadIdx.x & 31) == 0) atomicAnd(f16_ok, 0);
+  if (!__all_sync(0xffffffffu, b16) && (threadIdx.x & 31) == 0) atomicAnd(bf16_ok, 0);
+  if (!__all_sync(0xffffffffu, near) && (threadIdx.x & 31) == 0) atomicAnd(near_ok, 0);
 }
 
 // Algorithm 1 step 4 on one problem (body in layout_dev.cuh).
@@ -412,6 +418,75 @@ static mdp_status retain_pool(int device) {
   return MDP_OK;
 }
 
+// Entries of a host CSR: uploaded in row-aligned chunks of at most 2^25 entries (or
+// one longest row) through a ring of four device buffers on a copy stream; each chunk
+// is converted and checked on the creation stream as soon as it has arrived, so the
+// copies of later chunks overlap the conversion of earlier ones, and device memory
+// holds a few chunks instead of the whole CSR.  (Host-to-device copies from pinned
+// memory run at the same rate from one stream as from two or four.)  The row pointers have been checked
+// on the device beforehand, so the chunk boundaries found here by binary search on
+// the host's row pointers are valid.
+template <typename Convert>
+static mdp_status upload_rows(mdp_s* h, const int64_t* row_ptr, const int32_t* col, const void* val, size_t vbytes,
+                              int64_t R, int kmax, cudaStream_t st, Convert& convert) {
+  constexpr int kRing = 4;
+  const int64_t cap = std::min<int64_t>(row_ptr[R] - row_ptr[0], std::max<int64_t>(int64_t(1) << 25, kmax));
+  std::vector<int64_t> cut{0};
+  for (int64_t r0 = 0; r0 < R;) {
+    int64_t r1 = std::upper_bound(row_ptr + r0 + 1, row_ptr + R + 1, row_ptr[r0] + cap) - row_ptr - 1;
+    if (r1 <= r0 || row_ptr[r1] - row_ptr[r0] > cap)
+      return fail(MDP_ERR_INVALID_ARG, "row_ptr changed during mdp_create");
+    cut.push_back(r1);
+    r0 = r1;
+  }
+  const int chunks = (int)cut.size() - 1;
+  const int nb = std::min(kRing, chunks);
+  struct Ring {
+    cudaStream_t st;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr, copied[kRing] = {}, used[kRing] = {};
+    int32_t* c[kRing] = {};
+    uint16_t* v[kRing] = {};
+    ~Ring() {  // copies still in flight (an error part-way) end before their buffers are freed
+      if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+      }
+      for (cudaEvent_t e : copied)
+        if (e) cudaEventDestroy(e);
+      for (cudaEvent_t e : used)
+        if (e) cudaEventDestroy(e);
+      if (ready) cudaEventDestroy(ready);
+      for (int b = 0; b < kRing; ++b) {
+        dfree(st, c[b]);
+        dfree(st, v[b]);
+      }
+    }
+  } ring{st};
+  for (int b = 0; b < nb; ++b) {
+    MDP_TRY(dalloc(h, &ring.c[b], (size_t)cap, "column chunk"));
+    MDP_TRY(dalloc(h, &ring.v[b], (size_t)cap * (vbytes / 2), "value chunk"));
+    MDP_CUDA(cudaEventCreateWithFlags(&ring.copied[b], cudaEventDisableTiming));
+    MDP_CUDA(cudaEventCreateWithFlags(&ring.used[b], cudaEventDisableTiming));
+  }
+  MDP_CUDA(cudaEventCreateWithFlags(&ring.ready, cudaEventDisableTiming));
+  MDP_CUDA(cudaStreamCreateWithFlags(&ring.cs, cudaStreamNonBlocking));
+  MDP_CUDA(cudaEventRecord(ring.ready, st));  // the ring buffers are allocated on st
+  for (int i = 0; i < chunks; ++i) {
+    const int b = i % nb;
+    cudaStream_t cs = ring.cs;
+    const int64_t r0 = cut[i], r1 = cut[i + 1], e0 = row_ptr[r0], n = row_ptr[r1] - e0;
+    MDP_CUDA(cudaStreamWaitEvent(cs, i < nb ? ring.ready : ring.used[b], 0));
+    MDP_CUDA(cudaMemcpyAsync(ring.c[b], col + e0, n * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+    MDP_CUDA(cudaMemcpyAsync(ring.v[b], (const char*)val + e0 * vbytes, n * vbytes, cudaMemcpyHostToDevice, cs));
+    MDP_CUDA(cudaEventRecord(ring.copied[b], cs));
+    MDP_CUDA(cudaStreamWaitEvent(st, ring.copied[b], 0));
+    MDP_TRY(convert(ring.c[b], ring.v[b], r0, r1, e0));
+    MDP_CUDA(cudaEventRecord(ring.used[b], st));
+  }
+  return MDP_OK;
+}
+
 static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
                               mdp_dtype val_type, const double* g, int32_t on_device, cudaStream_t st,
                               mdp_s* h) {
@@ -435,34 +510,21 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
     return fail(MDP_ERR_NOT_STOCHASTIC, "row_ptr[S*A] must be between S*A (no empty rows) and 2^40");
   h->nnz = nnz;
 
-  // device views of the CSR input (temporary copies when it lives on the host; the
-  // values keep the caller's type, so a narrow type also uploads fewer bytes)
+  // Row pointers and stage costs first: the row structure is checked on every row
+  // before any entry is read, and it fixes the sliced layout.
   const size_t vbytes = val_type == MDP_F64 ? 8 : val_type == MDP_F32 ? 4 : 2;
   const int64_t* drp = row_ptr;
-  const int32_t* dcol = col;
-  const void* dval = val;
-  int64_t* trp = nullptr;
-  int32_t* tcol = nullptr;
-  uint16_t* tval = nullptr;  // nnz * vbytes bytes
-  struct Temps {
-    cudaStream_t st; int64_t** a; int32_t** b; uint16_t** c;
-    ~Temps() { dfree(st, *a); dfree(st, *b); dfree(st, *c); }
-  } temps{st, &trp, &tcol, &tval};
+  int64_t* trp = nullptr;  // device copy of host row pointers
+  struct FreeRp { cudaStream_t st; int64_t** p; ~FreeRp() { dfree(st, *p); } } free_rp{st, &trp};
   if (!on_device) {
     MDP_TRY(dalloc(h, &trp, R + 1, "row pointers"));
-    MDP_TRY(dalloc(h, &tcol, nnz, "columns"));
-    MDP_TRY(dalloc(h, &tval, nnz * (vbytes / 2), "values"));
     MDP_CUDA(cudaMemcpyAsync(trp, row_ptr, (R + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    MDP_CUDA(cudaMemcpyAsync(tcol, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    MDP_CUDA(cudaMemcpyAsync(tval, val, nnz * vbytes, cudaMemcpyHostToDevice, st));
     drp = trp;
-    dcol = tcol;
-    dval = tval;
   }
   MDP_TRY(dalloc(h, &h->g, R, "stage costs"));
   MDP_CUDA(cudaMemcpyAsync(h->g, g, R * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
 
-  // validation (flags, kmin, kmax live in the scalar area)
+  // validation flags, kmin, kmax and the exactness / offset flags live in the scalar area
   MDP_TRY(dalloc(h, &h->sc, kScalarSlots, "scalars"));
   MDP_TRY(dalloc(h, &h->resmax, 1, "residual"));
   int32_t* dlen = nullptr;
@@ -471,48 +533,62 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   int* dflags = (int*)h->sc;
   int init[6] = {0, 0x7fffffff, 0, 1, 1, 1};
   MDP_CUDA(cudaMemcpyAsync(dflags, init, sizeof(init), cudaMemcpyHostToDevice, st));
-  {
-    const int vb = grid_for(R, 256, h->sm_count);
-    switch (val_type) {
-      case MDP_F32:
-        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const float*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
-                                                 dflags + 5);
-        break;
-      case MDP_F16:
-        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __half*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
-                                                 dflags + 5);
-        break;
-      case MDP_BF16:
-        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const __nv_bfloat16*)dval, h->g, R, S, nnz, dlen,
-                                                 dflags, dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
-                                                 dflags + 5);
-        break;
-      default:
-        validate_rows_kernel<<<vb, 256, 0, st>>>(drp, dcol, (const double*)dval, h->g, R, S, nnz, dlen, dflags,
-                                                 dflags + 1, dflags + 2, dflags + 3, dflags + 4, A,
-                                                 dflags + 5);
-    }
-  }
+  row_struct_kernel<<<grid_for(R, 256, h->sm_count), 256, 0, st>>>(drp, h->g, R, nnz, dlen, dflags, dflags + 1,
+                                                                     dflags + 2);
   h->launches++;
   MDP_CUDA(cudaGetLastError());
   int res[6];
   MDP_CUDA(cudaMemcpyAsync(res, dflags, sizeof(res), cudaMemcpyDeviceToHost, st));
   MDP_CUDA(cudaStreamSynchronize(st));
-  if (res[0]) {
+  auto invalid = [](int f) {
     std::string m = "invalid MDP:";
-    if (res[0] & kBadPtr) m += " row_ptr not monotone or out of [0, nnz];";
-    if (res[0] & kEmptyRow) m += " empty row;";
-    if (res[0] & kLongRow) m += " row longer than 2^30;";
-    if (res[0] & kBadCol) m += " column outside [0, S);";
-    if (res[0] & kBadVal) m += " negative or non-finite probability;";
-    if (res[0] & kRowSum) m += " row does not sum to 1 within 1e-12;";
-    if (res[0] & kBadCost) m += " non-finite stage cost;";
-    return fail((res[0] & (kBadCost | kBadPtr)) && !(res[0] & (kEmptyRow | kBadCol | kBadVal | kRowSum))
+    if (f & kBadPtr) m += " row_ptr not monotone or out of [0, nnz];";
+    if (f & kEmptyRow) m += " empty row;";
+    if (f & kLongRow) m += " row longer than 2^30;";
+    if (f & kBadCol) m += " column outside [0, S);";
+    if (f & kBadVal) m += " negative or non-finite probability;";
+    if (f & kRowSum) m += " row does not sum to 1 within 1e-12;";
+    if (f & kBadCost) m += " non-finite stage cost;";
+    return fail((f & (kBadCost | kBadPtr)) && !(f & (kEmptyRow | kBadCol | kBadVal | kRowSum))
                     ? MDP_ERR_INVALID_ARG : MDP_ERR_NOT_STOCHASTIC, m);
-  }
+  };
+  if (res[0] & (kBadPtr | kEmptyRow | kLongRow)) return invalid(res[0]);
   const int kmin = res[1], kmax = res[2];
+
+  // stacked matrix in sliced layout: entries converted and checked row by row
+  MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));
+  const int uk = h->P.uniform ? kmax : 0;
+  auto convert_rows = [&](const int32_t* c, const void* v, int64_t r0, int64_t r1, int64_t ebase) -> mdp_status {
+    const int cb = grid_for(r1 - r0, 256, h->sm_count);
+    Sell& P = h->P;
+    switch (val_type) {
+      case MDP_F32:
+        sell_rows_kernel<<<cb, 256, 0, st>>>(drp, c, (const float*)v, r0, r1, ebase, S, P.off, uk, P.val, P.col,
+                                             dflags, dflags + 3, dflags + 4, dflags + 5);
+        break;
+      case MDP_F16:
+        sell_rows_kernel<<<cb, 256, 0, st>>>(drp, c, (const __half*)v, r0, r1, ebase, S, P.off, uk, P.val, P.col,
+                                             dflags, dflags + 3, dflags + 4, dflags + 5);
+        break;
+      case MDP_BF16:
+        sell_rows_kernel<<<cb, 256, 0, st>>>(drp, c, (const __nv_bfloat16*)v, r0, r1, ebase, S, P.off, uk, P.val,
+                                             P.col, dflags, dflags + 3, dflags + 4, dflags + 5);
+        break;
+      default:
+        sell_rows_kernel<<<cb, 256, 0, st>>>(drp, c, (const double*)v, r0, r1, ebase, S, P.off, uk, P.val, P.col,
+                                             dflags, dflags + 3, dflags + 4, dflags + 5);
+    }
+    h->launches++;
+    MDP_CUDA(cudaGetLastError());
+    return MDP_OK;
+  };
+  if (on_device)
+    MDP_TRY(convert_rows(col, val, 0, R, 0));
+  else
+    MDP_TRY(upload_rows(h, row_ptr, col, val, vbytes, R, kmax, st, convert_rows));
+  MDP_CUDA(cudaMemcpyAsync(res, dflags, sizeof(res), cudaMemcpyDeviceToHost, st));
+  MDP_CUDA(cudaStreamSynchronize(st));
+  if (res[0]) return invalid(res[0]);
 
   // narrowest exact storage for the mixed solver's copies of the policy rows
   h->pstore = res[3] ? kStoreF16 : (res[4] ? kStoreBF16 : kStoreF32);
@@ -520,29 +596,6 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   // and every MDP of at most 32,768 states): the mixed solver's copy of the policy
   // rows then stores 16-bit column offsets (2 B per entry instead of 4)
   h->col16 = res[5] != 0;
-
-  // stacked matrix in sliced layout
-  MDP_TRY(build_sell(h, &h->P, dlen, R, kmin, kmax, st));
-  {
-    const int cb = grid_for(R, 256, h->sm_count);
-    const int uk = h->P.uniform ? kmax : 0;
-    switch (val_type) {
-      case MDP_F32:
-        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const float*)dval, R, h->P.off, uk, h->P.val, h->P.col);
-        break;
-      case MDP_F16:
-        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const __half*)dval, R, h->P.off, uk, h->P.val, h->P.col);
-        break;
-      case MDP_BF16:
-        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const __nv_bfloat16*)dval, R, h->P.off, uk, h->P.val,
-                                               h->P.col);
-        break;
-      default:
-        csr_to_sell_kernel<<<cb, 256, 0, st>>>(drp, dcol, (const double*)dval, R, h->P.off, uk, h->P.val, h->P.col);
-    }
-  }
-  h->launches++;
-  MDP_CUDA(cudaGetLastError());
   if (!h->P.uniform)
     MDP_CUDA(cudaMemcpyAsync(h->P.len, dlen, R * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
 

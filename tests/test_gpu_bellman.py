@@ -79,6 +79,57 @@ def test_host_upload_matches_device_upload():
         assert torch.equal(x, y)  # same layout, same kernel: bitwise equal
 
 
+def _two_chunk_mdp():
+    """A banded MDP of 35.2e6 entries (host uploads go in chunks of at most 2^25 entries,
+    so this one takes two, with a chunk boundary inside the band) whose rows have 9 or 8
+    entries: every fifth row moves the mass of its last entry onto its first one."""
+    from mdpgen import banded_birth_death
+    m = banded_birth_death(400000, 10, 4, 0.99, quant_bits=11)
+    R = m.S * m.A
+    col, val = m.col.reshape(R, 9), m.val.reshape(R, 9).copy()
+    short = np.arange(R) % 5 == 0
+    val[short, 0] += val[short, 8]  # multiples of 2^-11: exact
+    keep = np.ones((R, 9), dtype=bool)
+    keep[short, 8] = False
+    rp = np.zeros(R + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(9 - short.astype(np.int64))
+    assert rp[-1] > 2 ** 25
+    return m, rp, np.ascontiguousarray(col[keep]), np.ascontiguousarray(val[keep])
+
+
+def test_chunked_host_upload_matches_device_upload():
+    import torch
+    from paper_2507_22538_gb300 import mdp
+    m, rp, col, val = _two_chunk_mdp()
+    V = torch.from_numpy(random_value_vector(m.S, 4, 100.0)).cuda()
+    host16 = torch.from_numpy(val).to(torch.float16)
+    assert torch.equal(host16.double(), torch.from_numpy(val))
+    with mdp.MDP(m.S, m.A, torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda(), torch.from_numpy(val).cuda(),
+                 torch.from_numpy(m.g).cuda()) as Md:
+        ref = Md.bellman(m.gamma, V)
+        for v in (val, torch.from_numpy(val).pin_memory(), host16.pin_memory()):
+            with mdp.MDP(m.S, m.A, rp, col, v, m.g) as Mh:
+                got = Mh.bellman(m.gamma, V)
+                torch.cuda.synchronize()
+                for x, y in zip(ref, got):
+                    assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("bad", ["negative_last", "column_last", "row_sum_first"])
+def test_chunked_host_upload_rejects_invalid_entries(bad):
+    from paper_2507_22538_gb300 import mdp
+    m, rp, col, val = _two_chunk_mdp()
+    if bad == "negative_last":  # an entry of the second chunk
+        val[-2] = -val[-2]
+    elif bad == "column_last":
+        col[-1] = m.S
+    else:
+        val[0] *= 1.5
+    st, h = mdp.mdp_create(m.S, m.A, rp, col, val, m.g, False, stream=0)
+    assert st == mdp.MDP_ERR_NOT_STOCHASTIC, (st, mdp.mdp_last_error())
+    assert not h.value
+
+
 def test_exact_ties_take_lowest_action():
     """g = 1/4 everywhere, gamma = 3/4, dyadic probabilities, V = 1: every Q is exactly 1."""
     import torch
