@@ -163,6 +163,9 @@ void mdp_default_opts(mdp_solve_opts* opts);
  * The caller keeps ownership of its arrays; the handle keeps its own copy in a
  * GPU-friendly layout.  Every row must be nonempty, have entries >= 0 that sum
  * to 1 within 1e-12, and columns in [0, S): otherwise MDP_ERR_NOT_STOCHASTIC.
+ * A row_ptr that does not start at 0, decreases or leaves [0, nnz] (with no
+ * empty row), or a non-finite cost with otherwise valid rows, gives
+ * MDP_ERR_INVALID_ARG.
  */
 mdp_status mdp_create(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
                       mdp_dtype val_type, const double* g, int32_t inputs_on_device, void* stream,

@@ -71,7 +71,7 @@ __global__ void row_struct_kernel(const int64_t* __restrict__ rp, const double* 
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t lo = rp[r], hi = rp[r + 1];
     int l = 0;
-    if (lo < 0 || hi < lo || hi > nnz)
+    if (lo < 0 || hi < lo || hi > nnz || (r == 0 && lo != 0))
       bad |= kBadPtr;
     else if (hi == lo)
       bad |= kEmptyRow;
@@ -542,7 +542,7 @@ static mdp_status create_impl(int64_t S, int32_t A, const int64_t* row_ptr, cons
   MDP_CUDA(cudaStreamSynchronize(st));
   auto invalid = [](int f) {
     std::string m = "invalid MDP:";
-    if (f & kBadPtr) m += " row_ptr not monotone or out of [0, nnz];";
+    if (f & kBadPtr) m += " row_ptr[0] not 0, or row_ptr not monotone or out of [0, nnz];";
     if (f & kEmptyRow) m += " empty row;";
     if (f & kLongRow) m += " row longer than 2^30;";
     if (f & kBadCol) m += " column outside [0, S);";

@@ -166,7 +166,7 @@ def test_deterministic_repeat():
             assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("bad", ["row_sum", "column", "negative", "empty_row", "nan_cost", "gamma"])
+@pytest.mark.parametrize("bad", ["row_sum", "column", "negative", "empty_row", "nan_cost", "row_ptr_start", "gamma"])
 def test_invalid_inputs_are_rejected(bad):
     import torch
     from paper_2507_22538_gb300 import mdp
@@ -183,6 +183,11 @@ def test_invalid_inputs_are_rejected(bad):
         rp[1] = 0  # row 0 empty (row 1 then holds two rows' entries)
     elif bad == "nan_cost":
         g[4] = np.nan
+        expect = mdp.MDP_ERR_INVALID_ARG
+    elif bad == "row_ptr_start":  # one unused entry in front: row_ptr[0] = 1, otherwise a valid CSR
+        rp = rp + 1
+        rp[0] = 1
+        col, val = np.concatenate([[0], col]).astype(np.int32), np.concatenate([[1.0], val])
         expect = mdp.MDP_ERR_INVALID_ARG
     if bad == "gamma":
         with mdp.MDP(m.S, m.A, rp, col, val, g) as M:
