@@ -237,6 +237,33 @@ def test_gmres_restarted_matches_dense(mid_mdp):
     np.testing.assert_allclose(out.x, exact, atol=1e-10)
 
 
+def test_gmres_minimises_the_residual_over_the_krylov_space():
+    """k steps of GMRES from x0 give the x in x0 + K_k(J, r0) with the least
+    ||b - J x||_2 (the defining property, Saad Sec. 6.5): compared with a least-squares
+    solve over an orthonormal basis of the Krylov space built here by repeated
+    products and numpy's QR, with no Arnoldi recurrence or Givens rotation; and the
+    residual never grows with k."""
+    m = random_sparse(30, 3, 6, 0.9, seed=8)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    pi = (np.arange(m.S) * 5) % m.A
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    J = np.eye(m.S) - m.gamma * Ppi.toarray()
+    x0 = random_value_vector(m.S, 9, 1.0)
+    r0 = gpi - J @ x0
+    cols, prev = [], np.inf
+    for k in range(1, 9):
+        v = r0 if not cols else J @ cols[-1]
+        cols.append(v / np.linalg.norm(v))
+        Q, _ = np.linalg.qr(np.array(cols).T)
+        c = np.linalg.lstsq(J @ Q, r0, rcond=None)[0]
+        best = float(np.linalg.norm(r0 - J @ Q @ c))
+        out = O.gmres(lambda x: O.apply_J(Ppi, m.gamma, x), gpi, x0, k, 0.0, k)
+        assert out.iters == k
+        assert abs(out.res2 - best) <= 1e-10 * np.linalg.norm(r0), (k, out.res2, best)
+        assert out.res2 <= prev * (1 + 1e-12)
+        prev = out.res2
+
+
 def test_beta_vi_and_opi_converge_to_optimum(mid_mdp):
     """beta-VI (Richardson scale beta, one step) and OPI(W) (W steps) reach V* (Table 2)."""
     m = mid_mdp
@@ -308,13 +335,17 @@ def _bellman_transposed(P, g, gamma, V, S, A):
 def _pins_hold():
     """Run a subset of the pins; True when all pass."""
     try:
+        # the direct Krylov pins first: a broken GMRES or TFQMR fails them at once,
+        # while the solves below would iterate to their caps with it
+        test_unrestarted_gmres_is_exact_in_n_steps()
+        test_gmres_minimises_the_residual_over_the_krylov_space()
+        test_tfqmr_terminates_in_2n_half_steps()
         test_golden_closed_form("two_state.json")
         test_golden_closed_form("three_state.json")
         test_constant_cost_closed_form()
         test_single_state_closed_form()
         for s in range(3):
             test_brute_force_tiny(s)
-        test_unrestarted_gmres_is_exact_in_n_steps()
         test_tfqmr_solves_policy_system()
         test_jacobi_diagonal_and_one_step_identity()
         test_action_gaps_hand_computed()
@@ -324,13 +355,38 @@ def _pins_hold():
     return True
 
 
+def _planted(fn, old, new):
+    """The oracle's function fn with one piece of its source replaced (a planted mistake)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(O, fn)))
+    assert src.count(old) == 1, old
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), "<planted>", "exec"), ns)
+    return ns[fn]
+
+
+SOURCE_MUTANTS = {
+    "gmres_rotated_rhs_sign": ("gmres", "e[j + 1] = -sn[j] * e[j]", "e[j + 1] = sn[j] * e[j]"),
+    "gmres_stale_rotations": ("gmres", "for i in range(j):  # previous rotations",
+                              "for i in range(0):  # previous rotations"),
+    "gmres_backsub_row": ("gmres", "float(np.dot(H[i, i + 1:jdone], y[i + 1:]))",
+                          "float(np.dot(H[i + 1, i + 1:jdone], y[i + 1:]))"),
+    "gmres_basis_unnormalised": ("gmres", "Vb[j + 1] = w / hn", "Vb[j + 1] = w"),
+    "tfqmr_step_length": ("tfqmr", "eta = c * c * alpha", "eta = c * alpha"),
+    "tfqmr_direction_weight": ("tfqmr", "d = yy + (theta * theta * eta / alpha) * d", "d = yy + (theta * eta / alpha) * d"),
+    "tfqmr_v_recurrence_sign": ("tfqmr", "v = u1 + beta * (u2 + beta * v)", "v = u1 + beta * (u2 - beta * v)"),
+    "tfqmr_tau_update": ("tfqmr", "tau = tau * theta * c", "tau = tau * c"),
+}
+
+
 def _q_without_cost(P, g, gamma, V, S, A):
     return gamma * (P @ np.asarray(V, dtype=np.float64)).reshape(S, A)
 
 
 MUTANTS = ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign", "policy_row_action_major",
            "J_gamma_squared", "evaluation_sign", "jacobi_diagonal_sign", "dropped_cost", "gaps_reversed",
-           "gaps_zero", "gaps_inf", "gaps_largest"]
+           "gaps_zero", "gaps_inf", "gaps_largest"] + sorted(SOURCE_MUTANTS)
 
 
 @pytest.mark.parametrize("mutant", MUTANTS)
@@ -339,7 +395,10 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
     tie-break, discount, layout or sign in the Bellman operator and in J_pi, the
     policy rows taken action-major (pi(s) S + s instead of s A + pi(s)), the policy
     evaluated with the wrong sign, the Jacobi diagonal with the wrong sign, the
-    stage cost dropped from Q."""
+    stage cost dropped from Q, and GMRES with a wrong sign in the rotated right-hand
+    side, the earlier rotations not applied to a new column, the back substitution
+    reading the wrong row of R, or an unnormalised Arnoldi vector, and TFQMR with a
+    wrong step length, direction weight, v recurrence or tau update."""
     assert _pins_hold()
     if mutant == "argmax_ties":
         monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
@@ -373,6 +432,9 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
         monkeypatch.setattr(O, "action_gaps", lambda Q: np.full(Q.shape[0], np.inf))
     elif mutant == "gaps_largest":
         monkeypatch.setattr(O, "action_gaps", lambda Q: Q.max(axis=1) - Q.min(axis=1))
+    elif mutant in SOURCE_MUTANTS:
+        fn = SOURCE_MUTANTS[mutant][0]
+        monkeypatch.setattr(O, fn, _planted(*SOURCE_MUTANTS[mutant]))
     assert not _pins_hold()
 
 
@@ -395,6 +457,26 @@ def test_tfqmr_solves_policy_system():
         assert O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, cap).iters == cap
     r10, r40 = (O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, c).res2 for c in (10, 40))
     assert r40 < 1e-3 * r10
+
+
+def test_tfqmr_terminates_in_2n_half_steps():
+    """On an n-state policy system TFQMR, like the BiCG process under it, ends at the
+    exact solution once the Krylov space is exhausted: after 2n half steps (n BiCG
+    steps, each two products by J) the iterate equals the dense solve to rounding
+    level, while two half steps fewer it does not yet (Freund 1993)."""
+    for seed in range(5):
+        m = random_sparse(6, 3, 4, 0.9, seed=seed)
+        P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+        pi = (np.arange(m.S) * 5) % m.A
+        Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+        exact = np.linalg.solve(np.eye(m.S) - m.gamma * Ppi.toarray(), gpi)
+        mv = lambda x: O.apply_J(Ppi, m.gamma, x)
+        scale = np.abs(exact).max()
+        full = O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, 2 * m.S)
+        assert full.iters == 2 * m.S
+        assert np.abs(full.x - exact).max() <= 1e-12 * scale, seed
+        short = O.tfqmr(mv, gpi, np.zeros(m.S), 0.0, 2 * m.S - 2)
+        assert np.abs(short.x - exact).max() > 1e-9 * scale, seed
 
 
 @pytest.mark.parametrize("seed", range(4))
