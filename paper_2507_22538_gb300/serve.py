@@ -66,20 +66,39 @@ class Result:
 
 def device_bytes(data, restart: int = 30, precision: int = mdp.MDP_PREC_F64) -> int:
     """Upper estimate of a request's device footprint: the stacked matrix in the
-    sliced layout (12 B per entry), its temporary CSR copy during upload, the
-    policy rows, costs, work vectors and the Krylov basis."""
+    sliced layout (12 B per entry), what mdp_create holds besides it, the policy
+    rows, costs, work vectors and the Krylov basis."""
     S, A = int(data.S), int(data.A)
     if hasattr(data, "device_arrays"):  # drawn on the device at admission: sizes known up front
         nnz, kmax = int(data.nnz), int(data.kmax)
-    else:
-        nnz = int(data.row_ptr[-1])
-        kmax = int(np.max(np.diff(data.row_ptr))) if S * A else 0
-    return _footprint(S, A, nnz, kmax, restart, precision)
+        return _footprint(S, A, nnz, kmax, restart, precision, host=False)
+    nnz = int(data.row_ptr[-1])
+    kmax = int(np.max(np.diff(data.row_ptr))) if S * A else 0
+    return _footprint(S, A, nnz, kmax, restart, precision, host=True)
 
 
-def _footprint(S, A, nnz, kmax, restart, precision) -> int:
+# mdp_create uploads host entries in row-aligned chunks of at most this many entries
+# (or one longest row), through at most four device buffers
+UPLOAD_CHUNK_ENTRIES = 1 << 25
+UPLOAD_BUFFERS = 4
+
+
+def _creation_bytes(S, A, nnz, kmax, host) -> int:
+    """Device memory mdp_create holds besides the handle: the row pointers and row
+    lengths, and either the upload's chunk buffers (host input: each chunk but the last
+    holds more than cap - kmax entries, so their number is bounded) or the request's
+    own device copy of the CSR (device input, until mdp_create returns)."""
+    rows = 8 * (S * A + 1) + 4 * S * A
+    if not host:
+        return rows + 12 * nnz
+    cap = min(nnz, max(UPLOAD_CHUNK_ENTRIES, kmax))
+    chunks = 1 if nnz <= cap else nnz // max(1, cap - kmax + 1) + 1
+    return rows + 12 * cap * min(UPLOAD_BUFFERS, chunks)
+
+
+def _footprint(S, A, nnz, kmax, restart, precision, host=True) -> int:
     stacked = 12 * nnz + 8 * S * A
-    upload = 12 * nnz + 8 * (S * A + 1)
+    upload = _creation_bytes(S, A, nnz, kmax, host)
     policy = 16 * S * kmax
     basis = 8 * (restart + 1) * S + (4 * (restart + 1) * S if precision == mdp.MDP_PREC_MIXED else 0)
     vectors = 16 * 8 * S
