@@ -400,7 +400,7 @@ mdp_status raise_dyn_smem(const void* func, size_t bytes) {
 
 // The stream-ordered pool that every device buffer of the library comes from
 // keeps up to a sixteenth of the device's memory across synchronisations (the
-// default returns all of it to the driver at each one), so handles created and
+// default returns all of it to the CUDA driver at each one), so handles created and
 // destroyed in turn reuse their buffers instead of mapping memory again.  This is
 // the process's default pool of the device: the setting ends with the process.
 static mdp_status retain_pool(int device) {
