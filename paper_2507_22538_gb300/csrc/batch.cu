@@ -505,6 +505,8 @@ mdp_status mdp_solve_batch(int32_t n, const mdp_handle* handles, const mdp_solve
   NvtxRange range("mdp_solve_batch");
   const auto t0 = std::chrono::steady_clock::now();
   if (n < 1 || !handles || !opts || !V || !pi || !status) return fail(MDP_ERR_INVALID_ARG, "null argument or n < 1");
+  for (int i = 0; i < n; ++i)  // argument errors are reported before any CUDA call
+    if (!handles[i] || !V[i] || !pi[i]) return fail(MDP_ERR_INVALID_ARG, "null handle or vector in the batch");
   cudaStream_t st = (cudaStream_t)stream;
   int device = -1;
   MDP_CUDA(cudaGetDevice(&device));

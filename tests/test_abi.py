@@ -101,3 +101,50 @@ def test_noalloc_rejects_overlapping_buffers(lib):
         a.update(bad)
         st = mdp.mdp_bellman_csr_noalloc(S, A, rp, 7, 7, g, 0.9, a["V"], a["TV"], a["pi"], a["res"], stream=0)
         assert st == mdp.MDP_ERR_INVALID_ARG and "overlap" in mdp.mdp_last_error(), bad
+
+
+@pytest.mark.parametrize("args,msg", [
+    (dict(S=0, A=4), "S >= 1"),
+    (dict(S=10, A=0), "A <= 8192"),
+    (dict(S=10, A=8193), "A <= 8192"),
+    (dict(S=1 << 31, A=1), "S must fit int32"),
+    (dict(S=1 << 30, A=128), "S*A must be below 2^36"),
+    (dict(S=10, A=4, row_ptr=0), "null input array"),
+    (dict(S=10, A=4, g=0), "null input array"),
+    (dict(S=10, A=4, val_type=7), "val_type"),
+], ids=["S0", "A0", "A_big", "S_big", "SA_big", "null_row_ptr", "null_g", "val_type"])
+def test_create_argument_checks(lib, args, msg):
+    """mdp_create refuses bad sizes, null arrays and unknown value types on the host,
+    before it touches the device (the addresses below are never dereferenced)."""
+    from paper_2507_22538_gb300 import mdp
+    a = dict(S=10, A=4, row_ptr=1 << 20, col=1 << 21, val=1 << 22, g=1 << 23, val_type=mdp.MDP_F64)
+    a.update(args)
+    st, h = mdp.mdp_create(a["S"], a["A"], a["row_ptr"], a["col"], a["val"], a["g"], False, stream=0,
+                           val_type=a["val_type"])
+    assert st == mdp.MDP_ERR_INVALID_ARG and not h.value
+    assert msg in mdp.mdp_last_error(), mdp.mdp_last_error()
+
+
+def test_null_handles_are_refused(lib):
+    """Every handle-taking entry point answers a null handle with MDP_ERR_INVALID_ARG
+    and a message, without touching the device."""
+    from paper_2507_22538_gb300 import mdp
+    o = mdp.mdp_default_opts()
+    o.gamma = 0.9
+    calls = {
+        "mdp_get_info": lambda: mdp.mdp_get_info(None)[0],
+        "mdp_bellman_lowp": lambda: mdp.mdp_bellman_lowp(None, 0.9, 1, 2, 3, stream=0),
+        "mdp_policy_apply": lambda: mdp.mdp_policy_apply(None, 0.9, 1, 2, 3, stream=0),
+        "mdp_policy_eval": lambda: mdp.mdp_policy_eval(None, 0.9, 1, 2, 3, stream=0)[0],
+        "mdp_solve": lambda: mdp.mdp_solve(None, o, 1, 2, stream=0)[0],
+        "mdp_tune": lambda: mdp.mdp_tune(None, 0.9, stream=0)[0],
+        "mdp_set_sweep_shape": lambda: mdp.mdp_set_sweep_shape(None, 64),
+        "mdp_get_sweep_shape": lambda: mdp.mdp_get_sweep_shape(None)[0],
+        "mdp_solve_batch": lambda: mdp.mdp_solve_batch([None], [o], [1], [2], stream=0)[0],
+        "mdp_solve_small_batch": lambda: mdp.mdp_solve_small_batch([None], [o], [1], [2], stream=0)[0],
+        "mdp_solve_batch_empty": lambda: mdp.mdp_solve_batch([], [], [], [], stream=0)[0],
+        "mdp_solve_small_batch_empty": lambda: mdp.mdp_solve_small_batch([], [], [], [], stream=0)[0],
+    }
+    for name, call in calls.items():
+        assert call() == mdp.MDP_ERR_INVALID_ARG, name
+        assert mdp.mdp_last_error(), name
