@@ -201,6 +201,35 @@ def test_richardson_one_step_is_value_iteration(mid_mdp):
     np.testing.assert_array_equal(a.pi, b.pi)
 
 
+def test_ipi_inner_solves_start_from_V_and_meet_the_forcing_term():
+    """Algorithm 1's inexactness rule: the evaluation at V_k starts from theta_0 = V_k
+    and stops once ||g_pi - J_pi theta||_2 < alpha ||T V_k - V_k||_inf, pi greedy for
+    V_k.  Checked on every outer step of a converged run (V_k taken from runs capped at
+    k evaluations), and, for the start, one GMRES step from V_0 against its closed form:
+    the least-squares step along r = g_pi - J V_0, V_1 = V_0 + (Jr.r / Jr.Jr) r."""
+    m = random_sparse(40, 3, 5, 0.95, seed=13)
+    P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
+    alpha = 0.1
+    full = O.ipi(*_args(m), tol=1e-10, alpha=alpha)
+    assert full.converged and full.outer_iters >= 3
+    prev = O.ipi(*_args(m), tol=1e-10, alpha=alpha, max_outer=0).V
+    for k in range(full.outer_iters):
+        nxt = O.ipi(*_args(m), tol=1e-10, alpha=alpha, max_outer=k + 1).V
+        _, pi, res = O.bellman(P, m.g, m.gamma, prev, m.S, m.A)
+        assert res == full.residuals[k]
+        Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+        assert np.linalg.norm(gpi - O.apply_J(Ppi, m.gamma, nxt)) < alpha * res, k
+        prev = nxt
+    V0 = random_value_vector(m.S, 4, 5.0)
+    one = O.ipi(*_args(m), V0=V0, tol=0.0, alpha=1e-12, max_outer=1, max_inner=1)
+    _, pi, _ = O.bellman(P, m.g, m.gamma, V0, m.S, m.A)
+    Ppi, gpi = O.policy_system(P, m.g, pi, m.A)
+    J = np.eye(m.S) - m.gamma * Ppi.toarray()
+    r = gpi - J @ V0
+    Jr = J @ r
+    np.testing.assert_allclose(one.V, V0 + (Jr @ r) / (Jr @ Jr) * r, rtol=0, atol=1e-12 * np.abs(V0).max())
+
+
 def test_one_richardson_step_is_policy_operator(mid_mdp):
     m = mid_mdp
     P = O.stacked_matrix(m.S, m.A, m.row_ptr, m.col, m.val)
@@ -340,6 +369,7 @@ def _pins_hold():
         test_unrestarted_gmres_is_exact_in_n_steps()
         test_gmres_minimises_the_residual_over_the_krylov_space()
         test_tfqmr_terminates_in_2n_half_steps()
+        test_ipi_inner_solves_start_from_V_and_meet_the_forcing_term()
         test_golden_closed_form("two_state.json")
         test_golden_closed_form("three_state.json")
         test_constant_cost_closed_form()
@@ -377,6 +407,10 @@ SOURCE_MUTANTS = {
     "tfqmr_direction_weight": ("tfqmr", "d = yy + (theta * theta * eta / alpha) * d", "d = yy + (theta * eta / alpha) * d"),
     "tfqmr_v_recurrence_sign": ("tfqmr", "v = u1 + beta * (u2 + beta * v)", "v = u1 + beta * (u2 - beta * v)"),
     "tfqmr_tau_update": ("tfqmr", "tau = tau * theta * c", "tau = tau * c"),
+    "ipi_fixed_forcing": ("ipi", "out = gmres(mv, gpi, V, restart, alpha * res, max_inner)",
+                          "out = gmres(mv, gpi, V, restart, alpha, max_inner)"),
+    "ipi_cold_start": ("ipi", "out = gmres(mv, gpi, V, restart, alpha * res, max_inner)",
+                       "out = gmres(mv, gpi, np.zeros(S), restart, alpha * res, max_inner)"),
 }
 
 
@@ -397,8 +431,10 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
     evaluated with the wrong sign, the Jacobi diagonal with the wrong sign, the
     stage cost dropped from Q, and GMRES with a wrong sign in the rotated right-hand
     side, the earlier rotations not applied to a new column, the back substitution
-    reading the wrong row of R, or an unnormalised Arnoldi vector, and TFQMR with a
-    wrong step length, direction weight, v recurrence or tau update."""
+    reading the wrong row of R, or an unnormalised Arnoldi vector, TFQMR with a
+    wrong step length, direction weight, v recurrence or tau update, and iPI with a
+    fixed inner tolerance instead of alpha times the Bellman residual, or with its
+    inner solve started from zero instead of V_k."""
     assert _pins_hold()
     if mutant == "argmax_ties":
         monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
