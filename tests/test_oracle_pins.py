@@ -411,6 +411,11 @@ SOURCE_MUTANTS = {
                           "out = gmres(mv, gpi, V, restart, alpha, max_inner)"),
     "ipi_cold_start": ("ipi", "out = gmres(mv, gpi, V, restart, alpha * res, max_inner)",
                        "out = gmres(mv, gpi, np.zeros(S), restart, alpha * res, max_inner)"),
+    "richardson_step_sign": ("richardson", "x = x + omega * r", "x = x - omega * r"),
+    "richardson_stale_residual": ("richardson", "        r = b - matvec(x)\n        rn = float(np.linalg.norm(r))\n    return",
+                                  "        rn = float(np.linalg.norm(r))\n    return"),
+    "jacobi_multiplies_by_diagonal": ("jacobi_richardson", "x = x + omega * r / diag", "x = x + omega * r * diag"),
+    "jacobi_ignores_diagonal": ("jacobi_richardson", "x = x + omega * r / diag", "x = x + omega * r"),
 }
 
 
@@ -434,7 +439,9 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
     reading the wrong row of R, or an unnormalised Arnoldi vector, TFQMR with a
     wrong step length, direction weight, v recurrence or tau update, and iPI with a
     fixed inner tolerance instead of alpha times the Bellman residual, or with its
-    inner solve started from zero instead of V_k."""
+    inner solve started from zero instead of V_k, Richardson stepping against the
+    residual or never refreshing it, and Jacobi-Richardson multiplying by the
+    diagonal or ignoring it."""
     assert _pins_hold()
     if mutant == "argmax_ties":
         monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
