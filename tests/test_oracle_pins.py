@@ -370,6 +370,7 @@ def _pins_hold():
         test_gmres_minimises_the_residual_over_the_krylov_space()
         test_tfqmr_terminates_in_2n_half_steps()
         test_ipi_inner_solves_start_from_V_and_meet_the_forcing_term()
+        test_bellman_states_matches_stacked(random_sparse(300, 5, 7, 0.93, seed=21))
         test_golden_closed_form("two_state.json")
         test_golden_closed_form("three_state.json")
         test_constant_cost_closed_form()
@@ -411,6 +412,8 @@ SOURCE_MUTANTS = {
                           "out = gmres(mv, gpi, V, restart, alpha, max_inner)"),
     "ipi_cold_start": ("ipi", "out = gmres(mv, gpi, V, restart, alpha * res, max_inner)",
                        "out = gmres(mv, gpi, np.zeros(S), restart, alpha * res, max_inner)"),
+    "sampled_states_action_major": ("bellman_states", "PV.reshape(n, A)", "PV.reshape(A, n).T"),
+    "sampled_states_argmax": ("bellman_states", "Q.argmin(axis=1)", "Q.argmax(axis=1)"),
     "richardson_step_sign": ("richardson", "x = x + omega * r", "x = x - omega * r"),
     "richardson_stale_residual": ("richardson", "        r = b - matvec(x)\n        rn = float(np.linalg.norm(r))\n    return",
                                   "        rn = float(np.linalg.norm(r))\n    return"),
@@ -440,8 +443,9 @@ def test_planted_mistakes_are_caught(monkeypatch, mutant):
     wrong step length, direction weight, v recurrence or tau update, and iPI with a
     fixed inner tolerance instead of alpha times the Bellman residual, or with its
     inner solve started from zero instead of V_k, Richardson stepping against the
-    residual or never refreshing it, and Jacobi-Richardson multiplying by the
-    diagonal or ignoring it."""
+    residual or never refreshing it, Jacobi-Richardson multiplying by the diagonal
+    or ignoring it, and the sampled-state Bellman step (the full-size checks' oracle)
+    with its rows taken action-major or its argmin turned into an argmax."""
     assert _pins_hold()
     if mutant == "argmax_ties":
         monkeypatch.setattr(O, "bellman", _bellman_argmax_ties)
