@@ -365,8 +365,11 @@ def policy_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, max_ite
 
     pi_0 is greedy for V = 0.  Each step evaluates V_pi exactly and switches
     pi(s) to the lowest minimiser of Q(s, .) only where it improves on
-    Q(s, pi(s)) by more than 1e-13 |Q(s, pi(s))| (so ties never cycle).  Stops
-    when no state changes; returns (V*, pi*, list of V_pi per step).
+    Q(s, pi(s)) by more than 1e-13 max(|Q(s, pi(s))|, ||V_pi||_inf): a strict
+    improvement at the scale of the values, so that the dense solve's rounding,
+    which leaves values of exact zero as +-1e-17, never makes tied actions
+    alternate.  Stops when no state changes; returns (V*, pi*, list of V_pi per
+    step).
     """
     P = stacked_matrix(S, A, row_ptr, col, val)
     _, pi, _ = bellman(P, g, gamma, np.zeros(S), S, A)
@@ -378,7 +381,7 @@ def policy_iteration(S: int, A: int, row_ptr, col, val, g, gamma: float, max_ite
         Q = q_values(P, g, gamma, V, S, A)
         best = Q.argmin(axis=1)
         cur = Q[np.arange(S), pi]
-        better = Q[np.arange(S), best] < cur - 1e-13 * np.abs(cur)
+        better = Q[np.arange(S), best] < cur - 1e-13 * np.maximum(np.abs(cur), np.abs(V).max())
         if not np.any(better):
             return V, pi.astype(np.int32), history
         pi = np.where(better, best, pi).astype(np.int32)
