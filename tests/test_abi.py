@@ -148,3 +148,11 @@ def test_null_handles_are_refused(lib):
     for name, call in calls.items():
         assert call() == mdp.MDP_ERR_INVALID_ARG, name
         assert mdp.mdp_last_error(), name
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without libmdp.so the binding raises: there is no other path to fall back on."""
+    from paper_2507_22538_gb300 import mdp
+    monkeypatch.setattr(mdp, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        mdp.load(str(tmp_path / "libmdp.so"))
