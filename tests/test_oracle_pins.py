@@ -431,6 +431,7 @@ MUTANTS = ["argmax_ties", "gamma_one", "action_major_layout", "inner_sign", "pol
            "gaps_zero", "gaps_inf", "gaps_largest"] + sorted(SOURCE_MUTANTS)
 
 
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")  # a planted mistake may overflow or divide by zero
 @pytest.mark.parametrize("mutant", MUTANTS)
 def test_planted_mistakes_are_caught(monkeypatch, mutant):
     """Plausible mistakes planted in the oracle make at least one pin fail: a wrong
