@@ -157,3 +157,26 @@ def test_request_header_ranges():
     assert {h[3] for h in hs} == {0.9, 0.99, 0.999, 0.9999}
     # log-uniform: about a third of the requests below 1e4
     assert 0.2 < np.mean(S < 10_000) < 0.45
+
+
+def test_quantize_rows_properties():
+    """Largest-remainder rounding (with hypothesis, where installed): every row sums to
+    exactly one, holds multiples of 2^-bits only (exact in binary16 for 11 bits and in
+    bfloat16 for 8), and moves no entry by a full unit 2^-bits."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @hyp.settings(max_examples=300, deadline=None, derandomize=True)
+    @hyp.given(st.lists(st.floats(1e-6, 1e6), min_size=1, max_size=70), st.sampled_from([8, 11]))
+    def check(w, bits):
+        w = np.array([w])
+        q = quantize_rows(w, bits)[0]
+        unit = 2.0 ** bits
+        assert q.sum() == 1.0
+        assert np.all(q >= 0) and np.all(q * unit == np.round(q * unit))
+        assert np.all(np.abs(q - w[0] / w[0].sum()) < 1 / unit)
+        import torch
+        narrow = torch.float16 if bits == 11 else torch.bfloat16
+        assert torch.equal(torch.from_numpy(q).to(narrow).double(), torch.from_numpy(q))
+
+    check()
